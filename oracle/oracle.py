@@ -1,0 +1,287 @@
+"""Python front end of the FP64 CPU oracle (oracle/crk_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the benchmark's CPU
+baseline import this module; the product library never does.  It shares no
+code with the CUDA path: it compiles and loads its own C file with gcc and
+passes FP64 numpy arrays through ctypes.
+
+Every function takes plain arrays (positions as f64[n, 3], vectors as
+f64[n, 3], tensors as f64[n, 9]) so that finite-difference checks can perturb
+positions in FP64.  ``from_box`` promotes a workload's FP32 arrays exactly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "crk_oracle.c")
+LIB = os.path.join(HERE, "liborc.so")
+
+_lock = threading.Lock()
+_lib = None
+
+_d = ctypes.POINTER(ctypes.c_double)
+_u8 = ctypes.POINTER(ctypes.c_uint8)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(LIB)
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_wendland.argtypes = [ctypes.c_int64, _d, _d, _d, _d]
+            L.orc_grav_g.argtypes = [ctypes.c_int64, _d, ctypes.c_double, _d, _d, _d]
+            L.orc_gravity.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double, _d,
+                                      _i64, ctypes.c_int64, ctypes.c_int, _d, _i64]
+            L.orc_gravity_adjoint.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, _d, _d, _i64, ctypes.c_int64, ctypes.c_int, _d, _d]
+            L.orc_geometry.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
+                                       ctypes.c_int, _d, _d, _i64]
+            L.orc_corrections.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
+                                          ctypes.c_int, _d, _d, _d, _d, _i64]
+            L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
+            L.orc_geometry_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, ctypes.c_double, _i64,
+                                               ctypes.c_int64, ctypes.c_int, _d, _d]
+            L.orc_leaves_mesh.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_double, ctypes.c_int, _i32, _i32]
+            L.orc_leaves_rcb.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_int, _i32, _i32, ctypes.c_int64, _i64]
+            L.orc_leaf_pairs.argtypes = [ctypes.c_int64, _i32, _i32, _d, _u8, _d, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, _i32, ctypes.c_int64, _i32, _i32, ctypes.c_int64, _i64]
+            for name in ("orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections", "orc_hydro",
+                         "orc_geometry_adjoint", "orc_leaves_mesh", "orc_leaves_rcb", "orc_leaf_pairs"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def set_threads(t: int) -> None:
+    lib().orc_set_threads(int(t))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+class Inputs:
+    """FP64 copy of one box: the oracle's view of the workload."""
+
+    def __init__(self, pos, species, m, h, u, v, L, r_cut, eps, poly):
+        self.pos = _f64(pos).reshape(-1, 3)
+        self.species = np.ascontiguousarray(species, dtype=np.uint8)
+        self.m = _f64(m)
+        self.h = _f64(h)
+        self.u = _f64(u)
+        self.v = _f64(v).reshape(-1, 3)
+        self.L = float(L)
+        self.r_cut = float(r_cut)
+        self.eps = float(eps)
+        self.poly = _f64(poly)
+        self.n = self.pos.shape[0]
+
+    def with_pos(self, pos):
+        c = Inputs(pos, self.species, self.m, self.h, self.u, self.v, self.L, self.r_cut, self.eps, self.poly)
+        return c
+
+    def with_m(self, m):
+        return Inputs(self.pos, self.species, m, self.h, self.u, self.v, self.L, self.r_cut, self.eps, self.poly)
+
+
+def from_box(box) -> Inputs:
+    pos = np.stack([box.x, box.y, box.z], axis=1).astype(np.float64)
+    v = np.stack([box.vx, box.vy, box.vz], axis=1).astype(np.float64)
+    return Inputs(pos, box.species, box.m, box.h, box.u, v, box.L, box.r_cut, box.eps,
+                  np.asarray(box.poly, dtype=np.float32).astype(np.float64))
+
+
+def _sub(sub):
+    if sub is None:
+        return None, 0
+    s = np.ascontiguousarray(sub, dtype=np.int64)
+    return s, s.size
+
+
+# ------------------------------------------------------------------ kernels
+
+def wendland(r, h):
+    r = _f64(r)
+    h = _f64(np.broadcast_to(h, r.shape))
+    W = np.empty_like(r)
+    dWr = np.empty_like(r)
+    lib().orc_wendland(r.size, _p(r, _d), _p(h, _d), _p(W, _d), _p(dWr, _d))
+    return W, dWr
+
+
+def grav_g(s, eps, poly):
+    s = _f64(s)
+    c = _f64(poly)
+    g = np.empty_like(s)
+    dg = np.empty_like(s)
+    lib().orc_grav_g(s.size, _p(s, _d), float(eps), _p(c, _d), _p(g, _d), _p(dg, _d))
+    return g, dg
+
+
+def gravity(I: Inputs, sub=None, brute=False):
+    """Short-range gravity accelerations f64[n, 3] and the ordered in-range pair count."""
+    acc = np.zeros((I.n, 3))
+    npairs = ctypes.c_int64(0)
+    s, ns = _sub(sub)
+    _check(lib().orc_gravity(I.n, _p(I.pos, _d), _p(I.m, _d), I.L, I.r_cut, I.eps, _p(I.poly, _d), _p(s, _i64), ns,
+                             int(brute), _p(acc, _d), ctypes.byref(npairs)), "gravity")
+    return acc, int(npairs.value)
+
+
+def gravity_adjoint(I: Inputs, abar, sub=None, brute=False):
+    abar = _f64(abar).reshape(-1, 3)
+    gx = np.zeros((I.n, 3))
+    gm = np.zeros(I.n)
+    s, ns = _sub(sub)
+    _check(lib().orc_gravity_adjoint(I.n, _p(I.pos, _d), _p(I.m, _d), I.L, I.r_cut, I.eps, _p(I.poly, _d),
+                                     _p(abar, _d), _p(s, _i64), ns, int(brute), _p(gx, _d), _p(gm, _d)),
+           "gravity_adjoint")
+    return gx, gm
+
+
+def geometry(I: Inputs, sub=None, brute=False):
+    """Gas volumes V and densities rho (dark-matter entries 0) and the hydro pair count."""
+    V = np.zeros(I.n)
+    rho = np.zeros(I.n)
+    npairs = ctypes.c_int64(0)
+    s, ns = _sub(sub)
+    _check(lib().orc_geometry(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d), I.L, _p(s, _i64),
+                              ns, int(brute), _p(V, _d), _p(rho, _d), ctypes.byref(npairs)), "geometry")
+    return V, rho, int(npairs.value)
+
+
+def corrections(I: Inputs, V, sub=None, brute=False):
+    """A f64[n], B f64[n,3], gradA f64[n,3], gradB f64[n,9] (gradB[i, 3g+a] = d_g B^a) and #singular."""
+    V = _f64(V)
+    A = np.zeros(I.n)
+    B = np.zeros((I.n, 3))
+    gA = np.zeros((I.n, 3))
+    gB = np.zeros((I.n, 9))
+    ns_ = ctypes.c_int64(0)
+    s, ns = _sub(sub)
+    _check(lib().orc_corrections(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(V, _d), I.L, _p(s, _i64),
+                                 ns, int(brute), _p(A, _d), _p(B, _d), _p(gA, _d), _p(gB, _d), ctypes.byref(ns_)),
+           "corrections")
+    return A, B, gA, gB, int(ns_.value)
+
+
+def hydro(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, sub=None, brute=False):
+    """dv/dt f64[n,3], du/dt f64[n] (gas only) and the hydro pair count."""
+    args = [_f64(a) for a in (V, rho, A, B, gA, gB)]
+    dv = np.zeros((I.n, 3))
+    du = np.zeros(I.n)
+    npairs = ctypes.c_int64(0)
+    s, ns = _sub(sub)
+    _check(lib().orc_hydro(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d), _p(I.v, _d),
+                           _p(I.u, _d), *[_p(a, _d) for a in args], I.L, float(gamma), float(alpha), float(beta),
+                           float(eta2), _p(s, _i64), ns, int(brute), _p(dv, _d), _p(du, _d), ctypes.byref(npairs)),
+           "hydro")
+    return dv, du, int(npairs.value)
+
+
+def geometry_adjoint(I: Inputs, rhobar, Vbar=None, sub=None, brute=False):
+    rb = _f64(rhobar)
+    vb = _f64(Vbar) if Vbar is not None else None
+    gx = np.zeros((I.n, 3))
+    gm = np.zeros(I.n)
+    s, ns = _sub(sub)
+    _check(lib().orc_geometry_adjoint(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d), _p(rb, _d),
+                                      _p(vb, _d), I.L, _p(s, _i64), ns, int(brute), _p(gx, _d), _p(gm, _d)),
+           "geometry_adjoint")
+    return gx, gm
+
+
+def conservation(I: Inputs, dv, du):
+    """FP64 global sums: total momentum rate (3) and total energy rate."""
+    gas = I.species == 0
+    mom = (I.m[gas, None] * dv[gas]).sum(axis=0)
+    ene = float((I.m[gas] * (np.sum(I.v[gas] * dv[gas], axis=1) + du[gas])).sum())
+    return np.array([mom[0], mom[1], mom[2], ene])
+
+
+def forward(I: Inputs, gamma, alpha, beta, eta2, brute=False):
+    """The whole forward chain geometry -> corrections -> hydro, plus gravity."""
+    V, rho, nh = geometry(I, brute=brute)
+    A, B, gA, gB, nsing = corrections(I, V, brute=brute)
+    dv, du, _ = hydro(I, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, brute=brute)
+    acc, ng = gravity(I, brute=brute)
+    return dict(V=V, rho=rho, A=A, B=B, gA=gA, gB=gB, dv=dv, du=du, acc=acc, pairs_hydro=nh, pairs_grav=ng,
+                singular=nsing)
+
+
+# ------------------------------------------------------------------- leaves
+
+def leaves_mesh(I: Inputs, nc: int):
+    perm = np.zeros(I.n, np.int32)
+    start = np.zeros(nc ** 3 + 1, np.int32)
+    _check(lib().orc_leaves_mesh(I.n, _p(I.pos, _d), _p(I.species, _u8), I.L, int(nc), _p(perm, _i32),
+                                 _p(start, _i32)), "leaves_mesh")
+    return perm, start
+
+
+def leaves_rcb(I: Inputs, max_leaf: int):
+    perm = np.zeros(max(I.n, 1), np.int32)
+    cap = max(1, 2 * (I.n // max(1, max_leaf // 2) + 2))
+    start = np.zeros(cap + 1, np.int32)
+    nl = ctypes.c_int64(0)
+    _check(lib().orc_leaves_rcb(I.n, _p(I.pos, _d), _p(I.species, _u8), int(max_leaf), _p(perm, _i32),
+                                _p(start, _i32), cap, ctypes.byref(nl)), "leaves_rcb")
+    return perm[:I.n], start[:nl.value + 1]
+
+
+def leaf_pairs(I: Inputs, perm, leaf_start, hydro: bool, asub=None):
+    """Canonical leaf-pair CSR (ptr, list) over all leaves or the subset asub."""
+    perm = np.ascontiguousarray(perm, np.int32)
+    start = np.ascontiguousarray(leaf_start, np.int32)
+    nl = start.size - 1
+    a = np.ascontiguousarray(asub, np.int32) if asub is not None else None
+    na = a.size if a is not None else nl
+    ptr = np.zeros(na + 1, np.int32)
+    cap = 64
+    while True:
+        lst = np.zeros(cap, np.int32)
+        tot = ctypes.c_int64(0)
+        rc = lib().orc_leaf_pairs(nl, _p(start, _i32), _p(perm, _i32), _p(I.pos, _d), _p(I.species, _u8),
+                                  _p(I.h, _d), I.L, int(hydro), I.r_cut, _p(a, _i32), na if a is not None else 0,
+                                  _p(ptr, _i32), _p(lst, _i32), cap, ctypes.byref(tot))
+        if rc == 0:
+            return ptr, lst[:tot.value]
+        if tot.value <= cap:
+            _check(rc, "leaf_pairs")
+        cap = int(tot.value)
