@@ -1,0 +1,183 @@
+/*
+ * crk.h -- C ABI of libcrk, the GB300 (sm_103a) library of CRK-HACC's
+ * short-range particle-pair kernels.
+ *
+ * The paper (arXiv 2310.16122) names the hot kernels of CRK-HACC's adiabatic
+ * solver and what each computes in one sentence (Sec. 5, opening paragraph):
+ * Geometry (gas-particle volumes), Corrections (reproducing-kernel
+ * coefficients), Acceleration (momentum derivative) and Energy (internal-
+ * energy derivative); Sec. 3.1 adds the short-range gravity solver (direct
+ * particle-particle force under a particle-mesh force split, polynomial order
+ * 5 per the appendix's HACC_CUDA_POLY_ORDER), the two species, and the RCB
+ * tree; Sec. 5.3 states that the kernels run over pairs of tree leaves.  The
+ * paper prints no equation for any of them; each entry point below states the
+ * reading it implements (conservative reproducing-kernel SPH, linear
+ * corrections, Wendland C4 kernel with support 2h, symmetric h_ij = (h_i+h_j)/2,
+ * periodic minimum image).
+ *
+ * Conventions for every call
+ *  - All particle arrays are DEVICE pointers owned by the caller, FP32
+ *    structure-of-arrays in the caller's original particle order, length n.
+ *    Vectors are packed component-major: v3[c*n + i], c = 0,1,2.
+ *  - Gas-only quantities (h, V, rho, u, A, B, ...) also have length n; their
+ *    dark-matter entries are ignored on input and written as 0 on output.
+ *  - Every compute call is asynchronous on the context's stream and does not
+ *    synchronise.  crk_build_leaves synchronises once (it reads back sizes).
+ *  - Every call returns CRK_OK (0) or a negative status; crk_last_error()
+ *    gives a message.  Device-side results that the host cannot see without a
+ *    synchronisation (singular moment matrices, pair counts) are written to
+ *    optional device outputs instead.
+ *  - Calls on one context must not run concurrently from several host threads.
+ */
+#ifndef CRK_H
+#define CRK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRK_OK 0
+#define CRK_EINVAL (-1)    /* bad argument (null pointer, negative size, bad mode) */
+#define CRK_ENOMEM (-2)    /* device allocation failed */
+#define CRK_ECUDA (-3)     /* a CUDA runtime call failed */
+#define CRK_EBOX (-4)      /* a cut (r_c or 2 h_max) is not below half the box, or positions outside [0, box) */
+#define CRK_ESTATE (-5)    /* leaves and arrays do not belong together */
+#define CRK_ETIMEOUT (-6)  /* a bounded device wait expired (batched work queue) */
+
+typedef struct crk_ctx crk_ctx;       /* opaque: device, stream, scratch arena, autotuner table */
+typedef struct crk_leaves crk_leaves; /* opaque: library-owned device buffers of one leaf build */
+
+/* One periodic box.  x, y, z in [0, box); species 0 = gas, 1 = dark matter. */
+typedef struct {
+    const float *x, *y, *z;
+    const uint8_t *species;
+    int64_t n;
+    float box;
+} crk_particles;
+
+/* Leaf decomposition (Sec. 3.1 RCB tree; Sec. 5.3 leaf pairs).
+ *  mode 0: fixed chaining mesh of cells_per_side^3 cells (a cell may hold at
+ *          most 1024 particles);
+ *  mode 1: recursive coordinate bisection down to leaves of <= max_leaf
+ *          particles (1 <= max_leaf <= 1024).
+ * r_cut_grav is the gravity cutoff used for the gravity leaf-pair list. */
+typedef struct {
+    int mode;
+    int cells_per_side;
+    int max_leaf;
+    float r_cut_grav;
+} crk_leaf_params;
+
+/* Short-range gravity: g(s) = (s + eps^2)^-3/2 - sum_k poly[k] s^k, s = r^2,
+ * zero for r >= r_cut (which must equal the leaves' r_cut_grav). */
+typedef struct {
+    float eps;
+    float r_cut;
+    float poly[6];
+} crk_grav_params;
+
+/* Ideal-gas index and Monaghan viscosity constants (alpha, beta, eta^2). */
+typedef struct {
+    float gamma;
+    float alpha;
+    float beta;
+    float eta2;
+} crk_hydro_params;
+
+/* Create a context on `device` that issues all work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The context owns a
+ * growable device scratch arena. */
+int crk_create(crk_ctx **out, int device, void *cuda_stream);
+void crk_destroy(crk_ctx *ctx);
+int crk_set_stream(crk_ctx *ctx, void *cuda_stream);
+const char *crk_last_error(const crk_ctx *ctx);
+/* Library version and build info, e.g. "libcrk 1 sm_103a". */
+const char *crk_version(void);
+/* Number of CUDA kernels this context has launched so far (host counter). */
+int crk_launch_count(const crk_ctx *ctx, int64_t *out);
+
+/* Build leaves (Sec. 3.1, 5.3).  Reads the positions and species, and the gas
+ * smoothing lengths h (device, length n; dark-matter entries ignored), which
+ * the leaves keep: every later call on these leaves uses this h.  Produces
+ * the leaf permutation and two lists of leaf pairs: gravity (periodic box
+ * gap < r_cut_grav) and hydro (both leaves hold gas, gap < 2 max h of the
+ * two leaves).  The box gap of two leaves is, per axis, the smallest over
+ * the periodic shifts {-box, 0, box} of the distance between their tight
+ * FP32 boxes, summed in squares in FP64.  Errors: CRK_EBOX if r_cut_grav or
+ * 2 max h is not below box/2 or a position lies outside [0, box).
+ * Synchronises the context stream once. */
+int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
+                     crk_leaves **out);
+
+/* info[0] = n, info[1] = number of leaves, info[2] = gravity leaf pairs,
+ * info[3] = hydro leaf pairs, info[4] = gravity image entries, info[5] = hydro
+ * image entries (a leaf pair with several periodic images near each other
+ * has one image entry per image). */
+int crk_leaves_info(const crk_leaves *lv, int64_t info[6]);
+
+/* Copy the canonical leaf structure to HOST arrays (synchronous; for checks):
+ * perm[n] (original index of the particle at leaf-order position p; inside a
+ * leaf gas comes first, then dark matter, each by original index),
+ * leaf_start[n_leaves + 1], and the two CSR lists (ptr[n_leaves + 1],
+ * list[pairs], j-leaves ascending, a = b included).  Any pointer may be NULL. */
+int crk_leaves_export(crk_ctx *ctx, const crk_leaves *lv, int32_t *perm, int32_t *leaf_start, int32_t *grav_ptr,
+                      int32_t *grav_list, int32_t *hydro_ptr, int32_t *hydro_list);
+void crk_leaves_free(crk_ctx *ctx, crk_leaves *lv);
+
+/* Geometry (Sec. 5: volumes of gas particles).
+ *   V_i = 1 / sum_{gas j, r_ij < 2 h_ij} W(r_ij, h_ij)  (j = i included),  rho_i = m_i / V_i.
+ * Inputs m[n]; outputs V[n], rho[n].  pair_count (device int64, may be NULL)
+ * receives the number of ordered in-range gas pairs with i != j. */
+int crk_geometry(crk_ctx *ctx, const crk_leaves *lv, const float *m, float *V, float *rho, int64_t *pair_count);
+
+/* Corrections (Sec. 5: reproducing-kernel coefficients), linear CRK.  With
+ * w = V_j W_ij and x = x_ij the moments m0, m1, m2 and their gradients in the
+ * evaluation point give B = -m2^-1 m1, A = 1/(m0 + B.m1),
+ * dA = -A^2 (dm0 + 2 B.dm1 + B^T dm2 B), dB = -m2^-1 (dm1 + dm2 B).
+ * Moment sums in FP32 (compensated for m0, m1, m2); the 3x3 inverse in FP64.
+ * Outputs A[n], B[3n], gradA[3n], gradB[9n] with gradB[(3g+a)n + i] =
+ * d B^a / d x^g.  A particle with det(m2) <= 1e-12 tr(m2)^3 gets NaN outputs
+ * and is counted in n_singular (device int32, may be NULL). */
+int crk_corrections(crk_ctx *ctx, const crk_leaves *lv, const float *V, float *A, float *B, float *gradA,
+                    float *gradB, int32_t *n_singular);
+
+/* Acceleration + Energy (Sec. 5: momentum and internal-energy derivatives),
+ * CRKSPH with an unlimited Monaghan viscosity and an equal energy split:
+ *   f_ij = -1/2 V_i V_j (P_i + P_j + Q_ij)(grad_i W^R_ij - grad_j W^R_ji),
+ *   m_i dv_i/dt = sum_j f_ij,  m_i du_i/dt = -1/2 sum_j (v_i - v_j).f_ij,
+ * P = (gamma-1) rho u, W^R_ij = A_i (1 + B_i.x_ij) W_ij.  Inputs m, v3, u, V,
+ * rho, A, B, gradA, gradB; outputs dvdt3[3n], dudt[n].  conservation (device
+ * double[4], may be NULL) receives sum m_i dv_i (3) and
+ * sum m_i (v_i.dv_i + du_i) accumulated in FP64. */
+int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+              const float *u, const float *V, const float *rho, const float *A, const float *B, const float *gradA,
+              const float *gradB, float *dvdt3, float *dudt, double *conservation, int64_t *pair_count);
+
+/* Short-range gravity (Sec. 3.1), G = 1, all species:
+ *   a_i = sum_{j != i, r < r_c} m_j (x_j - x_i) g(r^2).
+ * Input m[n]; output a3[3n]. */
+int grav_short(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m, float *a3,
+               int64_t *pair_count);
+
+/* Reverse mode of grav_short for a cotangent abar3 = dL/da (not in the paper):
+ *   gm_k = -sum_j abar_j . d_kj g(s_kj),
+ *   gx_k =  sum_j J(d_kj) (m_k abar_j - m_j abar_k),  J(d) = g I + 2 g'(s) d d^T,
+ * with d_kj = x_j - x_k; pair terms are recomputed, nothing per pair is stored.
+ * Outputs gx3[3n], gm[n] (overwritten). */
+int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m,
+                       const float *abar3, float *gx3, float *gm);
+
+/* Reverse mode of crk_geometry at fixed h (not in the paper).  With
+ * S_i = 1/V_i and cotangents rhobar (and Vbar, may be NULL):
+ *   Sbar_i = rhobar_i m_i - Vbar_i V_i^2,  gm_i = rhobar_i S_i,
+ *   gx_k = sum_j (Sbar_k + Sbar_j) grad_k W_kj.
+ * V is the forward output.  Outputs gx3[3n], gm[n] (overwritten; dark matter 0). */
+int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *V, const float *rhobar,
+                         const float *Vbar, float *gx3, float *gm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRK_H */

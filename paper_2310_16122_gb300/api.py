@@ -1,0 +1,234 @@
+"""PyTorch-facing wrappers of libcrk (device memory and streams from torch; compute in CUDA).
+
+Tensors are CUDA, contiguous, float32 (species uint8), in the caller's
+original particle order; vectors are component-major (3, n).  Every call is
+asynchronous on the context's stream (the torch stream given at creation).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import native as N
+
+
+def _f32(t: torch.Tensor, name: str, numel: int | None = None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+class Context:
+    """Owns a crk_ctx bound to one device and one torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        L = N.lib()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = L.crk_create(ctypes.byref(h), int(device), ctypes.c_void_p(self.stream.cuda_stream))
+        if st != N.CRK_OK:
+            raise N.CrkError(st, "crk_create failed")
+        self.handle = h
+
+    def check(self, status: int) -> None:
+        N.check(status, self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            N.lib().crk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, *shape, dtype=torch.float32):
+        return torch.empty(*shape, dtype=dtype, device=self.device)
+
+
+@dataclass
+class LeafParams:
+    mode: int = 1            # 0 chaining mesh, 1 RCB
+    cells_per_side: int = 0
+    max_leaf: int = 128
+    r_cut_grav: float = 3.0
+
+
+@dataclass
+class GravParams:
+    eps: float
+    r_cut: float
+    poly: tuple
+
+    def c(self) -> N.crk_grav_params:
+        g = N.crk_grav_params()
+        g.eps = self.eps
+        g.r_cut = self.r_cut
+        for k in range(6):
+            g.poly[k] = float(self.poly[k])
+        return g
+
+
+@dataclass
+class HydroParams:
+    gamma: float = 5.0 / 3.0
+    alpha: float = 1.0
+    beta: float = 2.0
+    eta2: float = 0.01
+
+    def c(self) -> N.crk_hydro_params:
+        return N.crk_hydro_params(self.gamma, self.alpha, self.beta, self.eta2)
+
+
+class Leaves:
+    """A leaf build (library-owned device buffers)."""
+
+    def __init__(self, ctx: Context, handle: ctypes.c_void_p, keep: tuple):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keep  # input tensors must outlive nothing after the build, kept for safety
+        info = (ctypes.c_int64 * 6)()
+        ctx.check(N.lib().crk_leaves_info(handle, info))
+        self.n, self.n_leaves, self.n_grav_pairs, self.n_hydro_pairs, self.n_grav_images, self.n_hydro_images = \
+            (int(v) for v in info)
+
+    def export(self) -> dict:
+        nl = self.n_leaves
+        out = dict(perm=np.zeros(max(self.n, 1), np.int32), leaf_start=np.zeros(nl + 1, np.int32),
+                   grav_ptr=np.zeros(nl + 1, np.int32), grav_list=np.zeros(max(self.n_grav_pairs, 1), np.int32),
+                   hydro_ptr=np.zeros(nl + 1, np.int32), hydro_list=np.zeros(max(self.n_hydro_pairs, 1), np.int32))
+        p = {k: v.ctypes.data_as(ctypes.c_void_p) for k, v in out.items()}
+        self.ctx.check(N.lib().crk_leaves_export(self.ctx.handle, self.handle, p["perm"], p["leaf_start"],
+                                                 p["grav_ptr"], p["grav_list"], p["hydro_ptr"], p["hydro_list"]))
+        out["perm"] = out["perm"][:self.n]
+        out["grav_list"] = out["grav_list"][:self.n_grav_pairs]
+        out["hydro_list"] = out["hydro_list"][:self.n_hydro_pairs]
+        return out
+
+    def free(self) -> None:
+        if self.handle:
+            N.lib().crk_leaves_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_leaves(ctx: Context, x, y, z, species, h, box: float, lp: LeafParams) -> Leaves:
+    n = x.numel()
+    p = N.crk_particles(_f32(x, "x", n) if n else 0, _f32(y, "y", n) if n else 0, _f32(z, "z", n) if n else 0,
+                        species.data_ptr() if n else 0, n, float(box))
+    if n and (species.dtype != torch.uint8 or not species.is_cuda or species.numel() != n):
+        raise TypeError("species must be a CUDA uint8 tensor of length n")
+    c = N.crk_leaf_params(int(lp.mode), int(lp.cells_per_side), int(lp.max_leaf), float(lp.r_cut_grav))
+    out = ctypes.c_void_p()
+    ctx.check(N.lib().crk_build_leaves(ctx.handle, ctypes.byref(p), _f32(h, "h", n) if n else None,
+                                       ctypes.byref(c), ctypes.byref(out)))
+    return Leaves(ctx, out, (x, y, z, species, h))
+
+
+def _count(ctx, want):
+    return torch.zeros(1, dtype=torch.int64, device=ctx.device) if want else None
+
+
+def geometry(ctx: Context, lv: Leaves, m, count=False):
+    n = lv.n
+    V, rho = ctx.empty(n), ctx.empty(n)
+    c = _count(ctx, count)
+    ctx.check(N.lib().crk_geometry(ctx.handle, lv.handle, _f32(m, "m", n), V.data_ptr(), rho.data_ptr(),
+                                   c.data_ptr() if c is not None else None))
+    return V, rho, c
+
+
+def corrections(ctx: Context, lv: Leaves, V):
+    n = lv.n
+    A, B, gA, gB = ctx.empty(n), ctx.empty(3, n), ctx.empty(3, n), ctx.empty(9, n)
+    ns = torch.zeros(1, dtype=torch.int32, device=ctx.device)
+    ctx.check(N.lib().crk_corrections(ctx.handle, lv.handle, _f32(V, "V", n), A.data_ptr(), B.data_ptr(),
+                                      gA.data_ptr(), gB.data_ptr(), ns.data_ptr()))
+    return A, B, gA, gB, ns
+
+
+def hydro(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A, B, gA, gB, count=False):
+    n = lv.n
+    dv, du = ctx.empty(3, n), ctx.empty(n)
+    cons = torch.zeros(4, dtype=torch.float64, device=ctx.device)
+    c = _count(ctx, count)
+    hpc = hp.c()
+    ctx.check(N.lib().crk_hydro(ctx.handle, lv.handle, ctypes.byref(hpc), _f32(m, "m", n), _f32(v3, "v3", 3 * n),
+                                _f32(u, "u", n), _f32(V, "V", n), _f32(rho, "rho", n), _f32(A, "A", n),
+                                _f32(B, "B", 3 * n), _f32(gA, "gradA", 3 * n), _f32(gB, "gradB", 9 * n),
+                                dv.data_ptr(), du.data_ptr(), cons.data_ptr(),
+                                c.data_ptr() if c is not None else None))
+    return dv, du, cons, c
+
+
+def grav_short(ctx: Context, lv: Leaves, gp: GravParams, m, count=False):
+    n = lv.n
+    a = ctx.empty(3, n)
+    c = _count(ctx, count)
+    g = gp.c()
+    ctx.check(N.lib().grav_short(ctx.handle, lv.handle, ctypes.byref(g), _f32(m, "m", n), a.data_ptr(),
+                                 c.data_ptr() if c is not None else None))
+    return a, c
+
+
+def grav_short_adjoint(ctx: Context, lv: Leaves, gp: GravParams, m, abar3):
+    n = lv.n
+    gx, gm = ctx.empty(3, n), ctx.empty(n)
+    g = gp.c()
+    ctx.check(N.lib().grav_short_adjoint(ctx.handle, lv.handle, ctypes.byref(g), _f32(m, "m", n),
+                                         _f32(abar3, "abar3", 3 * n), gx.data_ptr(), gm.data_ptr()))
+    return gx, gm
+
+
+def geometry_adjoint(ctx: Context, lv: Leaves, m, V, rhobar, Vbar=None):
+    n = lv.n
+    gx, gm = ctx.empty(3, n), ctx.empty(n)
+    ctx.check(N.lib().crk_geometry_adjoint(ctx.handle, lv.handle, _f32(m, "m", n), _f32(V, "V", n),
+                                           _f32(rhobar, "rhobar", n),
+                                           _f32(Vbar, "Vbar", n) if Vbar is not None else None,
+                                           gx.data_ptr(), gm.data_ptr()))
+    return gx, gm
+
+
+# ----------------------------------------------------------------- box helpers
+
+class DeviceBox:
+    """A workload box uploaded to the device (original order, SoA)."""
+
+    def __init__(self, box, device="cuda"):
+        t = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        self.L = float(box.L)
+        self.n = box.n
+        self.x, self.y, self.z = t(box.x), t(box.y), t(box.z)
+        self.species = t(box.species, torch.uint8)
+        self.m, self.h, self.u = t(box.m), t(box.h), t(box.u)
+        self.v3 = t(np.stack([box.vx, box.vy, box.vz]))
+        self.lp = LeafParams(box.leaf_mode, box.cells_per_side, box.max_leaf, float(box.r_cut))
+        self.gp = GravParams(float(box.eps), float(box.r_cut), tuple(float(c) for c in box.poly))
+        self.hp = HydroParams()
+
+
+def forward(ctx: Context, db: DeviceBox, count=False):
+    """Leaves, then geometry -> corrections -> hydro, then gravity; returns a dict of device tensors."""
+    lv = build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, rho, cg = geometry(ctx, lv, db.m, count)
+    A, B, gA, gB, ns = corrections(ctx, lv, V)
+    dv, du, cons, ch = hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, count)
+    a, ca = grav_short(ctx, lv, db.gp, db.m, count)
+    return dict(leaves=lv, V=V, rho=rho, A=A, B=B, gA=gA, gB=gB, n_singular=ns, dv=dv, du=du, cons=cons, acc=a,
+                count_geom=cg, count_hydro=ch, count_grav=ca)

@@ -1,0 +1,104 @@
+// Context, errors and device memory of libcrk.
+#include <cstdarg>
+#include <cstdio>
+
+#include "crk_internal.cuh"
+
+int crk_fail(crk_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return CRK_OK;
+    if (e == cudaErrorMemoryAllocation) return crk_fail(ctx, CRK_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return crk_fail(ctx, CRK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Growable per-slot scratch.  Growing frees the old buffer: cudaFree waits for
+// the device, so work still using it on the context stream has finished.
+void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes) {
+    if (slot < 0 || slot >= crk_ctx::kSlots) return nullptr;
+    if (bytes == 0) bytes = 16;
+    if (ctx->slot_bytes[slot] >= bytes) return ctx->slot[slot];
+    if (ctx->slot[slot]) cudaFree(ctx->slot[slot]);
+    ctx->slot[slot] = nullptr;
+    ctx->slot_bytes[slot] = 0;
+    size_t want = bytes + bytes / 8;  // headroom for slowly growing inputs
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        want = bytes;
+    }
+    ctx->slot[slot] = p;
+    ctx->slot_bytes[slot] = want;
+    return p;
+}
+
+void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes) {
+    (void)ctx;
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    lv->allocs.push_back(p);
+    return p;
+}
+
+extern "C" {
+
+int crk_create(crk_ctx **out, int device, void *cuda_stream) {
+    if (!out) return CRK_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return CRK_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return CRK_ECUDA;
+    crk_ctx *ctx = new crk_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    *out = ctx;
+    return CRK_OK;
+}
+
+void crk_destroy(crk_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int s = 0; s < crk_ctx::kSlots; ++s)
+        if (ctx->slot[s]) cudaFree(ctx->slot[s]);
+    delete ctx;
+}
+
+int crk_set_stream(crk_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return CRK_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return CRK_OK;
+}
+
+const char *crk_last_error(const crk_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+const char *crk_version(void) { return "libcrk 1 sm_103a"; }
+
+int crk_launch_count(const crk_ctx *ctx, int64_t *out) {
+    if (!ctx || !out) return CRK_EINVAL;
+    *out = ctx->launches;
+    return CRK_OK;
+}
+
+}  // extern "C"

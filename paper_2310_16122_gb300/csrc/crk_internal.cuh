@@ -1,0 +1,90 @@
+// Internal declarations of libcrk (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/crk.h"
+
+#define CRK_WARP 32
+#define CRK_FULL_MASK 0xffffffffu
+
+// One periodic image of a j-leaf as seen from an i-leaf: adding (sx, sy, sz)
+// to the j-leaf's leaf-relative coordinates expresses them in the i-leaf frame.
+struct crk_image {
+    int32_t b;
+    float sx, sy, sz;
+};
+
+struct crk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    // growable scratch arena: one buffer per slot
+    static const int kSlots = 16;
+    void *slot[kSlots] = {};
+    size_t slot_bytes[kSlots] = {};
+    int64_t launches = 0;  // kernels this context has launched
+};
+
+struct crk_leaves {
+    int64_t n = 0;
+    int64_t n_gas = 0;
+    int64_t n_leaves = 0;
+    float box = 0.f;
+    int mode = 1;
+    float r_cut_grav = 0.f;
+    float hmax_all = 0.f;
+    int max_leaf_size = 0;  // largest leaf population
+    // device arrays
+    int32_t *perm = nullptr;        // canonical order -> original index
+    int32_t *kperm = nullptr;       // kernel order -> original index
+    int32_t *leaf_start = nullptr;  // [n_leaves + 1]
+    int32_t *leaf_ngas = nullptr;   // [n_leaves]
+    float *bbox = nullptr;          // [n_leaves][6]: lo xyz, hi xyz
+    float *hmax = nullptr;          // [n_leaves]
+    float4 *pos = nullptr;          // [n] kernel order: leaf-relative x, y, z and h (gas) or 0
+    int32_t *gimg_ptr = nullptr;    // [n_leaves + 1]
+    crk_image *gimg = nullptr;
+    int32_t *himg_ptr = nullptr;
+    crk_image *himg = nullptr;
+    int32_t *gpair_ptr = nullptr, *gpair_list = nullptr;
+    int32_t *hpair_ptr = nullptr, *hpair_list = nullptr;
+    int64_t n_gimg = 0, n_himg = 0, n_gpairs = 0, n_hpairs = 0;
+    std::vector<void *> allocs;
+};
+
+// ---- host helpers (api.cu) ----
+int crk_fail(crk_ctx *ctx, int code, const char *fmt, ...);
+int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
+void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes);
+void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes);
+
+#define CRK_CUDA(ctx, call)                                          \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return crk_check_cuda(ctx, e_, #call); \
+    } while (0)
+
+#define CRK_LAUNCH_CHECK(ctx, what)                                           \
+    do {                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) return crk_check_cuda(ctx, e_, what);          \
+    } while (0)
+
+// ---- scan / sort primitives (scan.cu) ----
+// exclusive prefix sum of n int32 values (in may equal out); total (device int32) optional
+int crk_exclusive_scan_i32(crk_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *total);
+// stable LSD radix sort of (key, value) pairs by all 32 key bits
+int crk_radix_sort_u32(crk_ctx *ctx, uint32_t *keys, int32_t *vals, int64_t n, int key_bits);
+
+static inline int crk_grid(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 2147483647LL) g = 2147483647LL;
+    return (int)g;
+}

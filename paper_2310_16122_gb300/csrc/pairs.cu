@@ -1,0 +1,779 @@
+// Short-range pair kernels of CRK-HACC (Sec. 5: Geometry, Corrections,
+// Acceleration/Energy; Sec. 3.1: short-range gravity) and the two adjoints.
+//
+// Work decomposition (Sec. 5.3 runs the kernels over leaf pairs; the paper's
+// "half-warp" lane split is prior art, not reused): one block per i-leaf, one
+// warp per group of 32 consecutive i-particles of that leaf.  The warp walks
+// the leaf's periodic images of j-leaves; every j-particle whose distance to
+// the warp's i-box is below the cut is appended, already shifted into the
+// i-leaf frame, to a per-warp buffer in shared memory (ballot compaction).
+// Each full buffer is then swept by all 32 lanes, every lane accumulating the
+// pair terms of its own i-particle (one-sided: no atomics, deterministic).
+// Positions are FP32 relative to the i-leaf origin; sums are FP32 (Kahan-
+// compensated for the moment sums); the CRK 3x3 inverse and the conservation
+// reductions are FP64.
+#include <cmath>
+
+#include "crk_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kWarps = kThreads / 32;
+constexpr int kCap = 64;                     // per-warp candidate buffer
+constexpr float kSigmaW = 0.61548156588532f;  // 495 / (256 pi), Wendland C4 3-D normalisation
+
+struct LeafView {
+    const int32_t *leaf_start;
+    const int32_t *leaf_ngas;
+    const float *bbox;
+    const float *hmax;
+    const float4 *pos;
+    const int32_t *kperm;
+    const int32_t *img_ptr;
+    const crk_image *img;
+    int64_t n_leaves;
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Wendland C4 with support 2h: W and (dW/dr)/r at distance^2 r2, h = hij.
+__device__ __forceinline__ void wendland(float r2, float hij, float &W, float &dWr) {
+    float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    float ih = __fdividef(1.0f, hij);
+    float q = r * ih;
+    float t = fmaxf(1.0f - 0.5f * q, 0.0f);
+    float t2 = t * t;
+    float t5 = t2 * t2 * t;
+    float ih2 = ih * ih;
+    float ih3 = ih2 * ih;
+    float n3 = kSigmaW * ih3;
+    W = n3 * t5 * t * (1.0f + q * (3.0f + q * (35.0f / 12.0f)));
+    dWr = n3 * ih2 * t5 * (-14.0f / 3.0f) * (1.0f + 2.5f * q);
+}
+
+// ------------------------------------------------------------------ stages
+// Each stage defines Rec (one kernel-order record, also the shared-memory
+// entry), gather (build Rec of particle p), box_cut (pruning radius of a
+// candidate against the i-group box), I (per-lane state), init, interact and
+// finish.
+
+struct GravP {
+    const float *m;
+    float *a3;
+    float rc2, eps2;
+    float c[6];
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct GravStage {
+    static constexpr bool kGasOnly = false;
+    using P = GravP;
+    struct Rec {
+        float x, y, z, m;
+    };
+    struct I {
+        float ax, ay, az;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t orig, float4 ps) { return {ps.x, ps.y, ps.z, p.m[orig]}; }
+    static constexpr bool kCons = false;
+    __device__ static float box_cut(const P &p, float, const Rec &) { return sqrtf(p.rc2); }
+    __device__ static float leaf_cut(const P &p, float, float) { return sqrtf(p.rc2); }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &) { s.ax = s.ay = s.az = 0.f; s.cnt = 0; }
+    template <bool kCount>
+    __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
+        float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float rinv = rsqrtf(r2 + p.eps2);
+        float r3 = rinv * rinv * rinv;
+        float poly = fmaf(fmaf(fmaf(fmaf(fmaf(p.c[5], r2, p.c[4]), r2, p.c[3]), r2, p.c[2]), r2, p.c[1]), r2, p.c[0]);
+        bool in = r2 < p.rc2;
+        float f = in ? rj.m * (r3 - poly) : 0.0f;
+        s.ax = fmaf(f, dx, s.ax);
+        s.ay = fmaf(f, dy, s.ay);
+        s.az = fmaf(f, dz, s.az);
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t orig) {
+        p.a3[orig] = s.ax;
+        p.a3[p.n + orig] = s.ay;
+        p.a3[2 * p.n + orig] = s.az;
+    }
+    __device__ static void finish_other(const P &, int32_t) {}
+};
+
+struct GravAdjP {
+    const float *m, *abar;
+    float *gx3, *gm;
+    float rc2, eps2;
+    float c[6];
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct GravAdjStage {
+    static constexpr bool kGasOnly = false;
+    using P = GravAdjP;
+    struct __align__(16) Rec {
+        float x, y, z, m;
+        float bx, by, bz, pad;
+    };
+    struct I {
+        float gx, gy, gz, gm;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) {
+        return {ps.x, ps.y, ps.z, p.m[o], p.abar[o], p.abar[p.n + o], p.abar[2 * p.n + o], 0.f};
+    }
+    static constexpr bool kCons = false;
+    __device__ static float box_cut(const P &p, float, const Rec &) { return sqrtf(p.rc2); }
+    __device__ static float leaf_cut(const P &p, float, float) { return sqrtf(p.rc2); }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &) { s.gx = s.gy = s.gz = s.gm = 0.f; s.cnt = 0; }
+    template <bool kCount>
+    __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
+        float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;  // d_ij = x_j - x_i
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float rinv = rsqrtf(r2 + p.eps2);
+        float ri2 = rinv * rinv;
+        float r3 = ri2 * rinv;
+        float poly = fmaf(fmaf(fmaf(fmaf(fmaf(p.c[5], r2, p.c[4]), r2, p.c[3]), r2, p.c[2]), r2, p.c[1]), r2, p.c[0]);
+        float dpoly = fmaf(fmaf(fmaf(fmaf(5.0f * p.c[5], r2, 4.0f * p.c[4]), r2, 3.0f * p.c[3]), r2, 2.0f * p.c[2]),
+                           r2, p.c[1]);
+        bool in = r2 < p.rc2;
+        float g = in ? r3 - poly : 0.0f;
+        float dg2 = in ? 2.0f * fmaf(-1.5f * r3, ri2, -dpoly) : 0.0f;
+        float wx = ri.m * rj.bx - rj.m * ri.bx;
+        float wy = ri.m * rj.by - rj.m * ri.by;
+        float wz = ri.m * rj.bz - rj.m * ri.bz;
+        float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+        float k = dg2 * dw;
+        s.gx = fmaf(g, wx, fmaf(k, dx, s.gx));
+        s.gy = fmaf(g, wy, fmaf(k, dy, s.gy));
+        s.gz = fmaf(g, wz, fmaf(k, dz, s.gz));
+        s.gm = fmaf(-g, fmaf(rj.bx, dx, fmaf(rj.by, dy, rj.bz * dz)), s.gm);
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+        p.gx3[o] = s.gx;
+        p.gx3[p.n + o] = s.gy;
+        p.gx3[2 * p.n + o] = s.gz;
+        p.gm[o] = s.gm;
+    }
+    __device__ static void finish_other(const P &, int32_t) {}
+};
+
+struct GeomP {
+    const float *m;
+    float *V, *rho;
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct GeomStage {
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    using P = GeomP;
+    struct Rec {
+        float x, y, z, h;
+    };
+    struct I {
+        float s, c;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &, int32_t, float4 ps) { return {ps.x, ps.y, ps.z, ps.w}; }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &) { s.s = s.c = 0.f; s.cnt = 0; }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float W, dWr;
+        wendland(r2, 0.5f * hs, W, dWr);
+        kahan_add(s.s, s.c, in ? W : 0.0f);
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+        float sum = s.s - s.c;
+        float V = 1.0f / sum;
+        p.V[o] = V;
+        p.rho[o] = p.m[o] * sum;
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        p.V[o] = 0.f;
+        p.rho[o] = 0.f;
+    }
+};
+
+struct GeomAdjP {
+    const float *m, *V, *rhobar, *Vbar;
+    float *gx3, *gm;
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct GeomAdjStage {
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    using P = GeomAdjP;
+    struct __align__(16) Rec {
+        float x, y, z, h;
+        float sbar, pad0, pad1, pad2;
+    };
+    struct I {
+        float gx, gy, gz;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) {
+        float V = p.V[o];
+        float sb = p.rhobar[o] * p.m[o] - (p.Vbar ? p.Vbar[o] * V * V : 0.0f);
+        return {ps.x, ps.y, ps.z, ps.w, sb, 0.f, 0.f, 0.f};
+    }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &) { s.gx = s.gy = s.gz = 0.f; s.cnt = 0; }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;  // x_kj
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float W, dWr;
+        wendland(r2, 0.5f * hs, W, dWr);
+        float k = in ? (ri.sbar + rj.sbar) * dWr : 0.0f;
+        s.gx = fmaf(k, dx, s.gx);
+        s.gy = fmaf(k, dy, s.gy);
+        s.gz = fmaf(k, dz, s.gz);
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+        p.gx3[o] = s.gx;
+        p.gx3[p.n + o] = s.gy;
+        p.gx3[2 * p.n + o] = s.gz;
+        p.gm[o] = p.rhobar[o] / p.V[o];
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        p.gx3[o] = 0.f;
+        p.gx3[p.n + o] = 0.f;
+        p.gx3[2 * p.n + o] = 0.f;
+        p.gm[o] = 0.f;
+    }
+};
+
+struct CorrP {
+    const float *V;
+    float *A, *B, *gA, *gB;
+    int32_t *n_singular;
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct CorrStage {
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    using P = CorrP;
+    struct __align__(16) Rec {
+        float x, y, z, h;
+        float V, pad0, pad1, pad2;
+    };
+    struct I {
+        float m0, c0;
+        float m1[3], c1[3];
+        float m2[6], c2[6];  // xx xy xz yy yz zz
+        float dm0[3];
+        float dm1[9];   // [g][a]
+        float dm2[18];  // [g][ab]
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) { return {ps.x, ps.y, ps.z, ps.w, p.V[o], 0, 0, 0}; }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &) {
+        s.m0 = s.c0 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s.m1[a] = s.c1[a] = s.dm0[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) s.m2[a] = s.c2[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s.dm1[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 18; ++a) s.dm2[a] = 0.f;
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float x[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};  // x_ij
+        float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float W, dWr;
+        wendland(r2, 0.5f * hs, W, dWr);
+        float w = in ? rj.V * W : 0.0f;
+        float vd = in ? rj.V * dWr : 0.0f;
+        float wx[3] = {w * x[0], w * x[1], w * x[2]};
+        float dW[3] = {vd * x[0], vd * x[1], vd * x[2]};  // V_j d_g W
+        kahan_add(s.m0, s.c0, w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) kahan_add(s.m1[a], s.c1[a], wx[a]);
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+        float xx[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            xx[q] = x[ia[q]] * x[ib[q]];
+            kahan_add(s.m2[q], s.c2[q], wx[ia[q]] * x[ib[q]]);
+        }
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            s.dm0[g] += dW[g];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s.dm1[3 * g + a] = fmaf(x[a], dW[g], s.dm1[3 * g + a] + (a == g ? w : 0.0f));
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                float t = (ia[q] == g ? wx[ib[q]] : 0.0f) + (ib[q] == g ? wx[ia[q]] : 0.0f);
+                s.dm2[6 * g + q] = fmaf(xx[q], dW[g], s.dm2[6 * g + q] + t);
+            }
+        }
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+        double m0 = (double)s.m0 - (double)s.c0;
+        double m1[3], M[3][3];
+        for (int a = 0; a < 3; ++a) m1[a] = (double)s.m1[a] - (double)s.c1[a];
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+        for (int q = 0; q < 6; ++q) {
+            double v = (double)s.m2[q] - (double)s.c2[q];
+            M[ia[q]][ib[q]] = v;
+            M[ib[q]][ia[q]] = v;
+        }
+        double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                     M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                     M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        double tr = M[0][0] + M[1][1] + M[2][2];
+        const int64_t n = p.n;
+        if (!(det > 1e-12 * tr * tr * tr)) {
+            const float nan = __int_as_float(0x7fc00000);
+            p.A[o] = nan;
+            for (int a = 0; a < 3; ++a) { p.B[a * n + o] = nan; p.gA[a * n + o] = nan; }
+            for (int a = 0; a < 9; ++a) p.gB[a * n + o] = nan;
+            if (p.n_singular) atomicAdd(p.n_singular, 1);
+            return;
+        }
+        double Mi[3][3];
+        double id = 1.0 / det;
+        Mi[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) * id;
+        Mi[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) * id;
+        Mi[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) * id;
+        Mi[1][0] = Mi[0][1];
+        Mi[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) * id;
+        Mi[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) * id;
+        Mi[2][0] = Mi[0][2];
+        Mi[2][1] = Mi[1][2];
+        Mi[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) * id;
+        double B[3];
+        for (int a = 0; a < 3; ++a) B[a] = -(Mi[a][0] * m1[0] + Mi[a][1] * m1[1] + Mi[a][2] * m1[2]);
+        double A = 1.0 / (m0 + B[0] * m1[0] + B[1] * m1[1] + B[2] * m1[2]);
+        p.A[o] = (float)A;
+        for (int a = 0; a < 3; ++a) p.B[a * n + o] = (float)B[a];
+        for (int g = 0; g < 3; ++g) {
+            double dM[3][3];
+            for (int q = 0; q < 6; ++q) {
+                dM[ia[q]][ib[q]] = s.dm2[6 * g + q];
+                dM[ib[q]][ia[q]] = s.dm2[6 * g + q];
+            }
+            double t[3], BdMB = 0.0, Bdm1 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double dMB = dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2];
+                t[a] = (double)s.dm1[3 * g + a] + dMB;
+                BdMB += B[a] * dMB;
+                Bdm1 += B[a] * (double)s.dm1[3 * g + a];
+            }
+            p.gA[g * n + o] = (float)(-A * A * ((double)s.dm0[g] + 2.0 * Bdm1 + BdMB));
+            for (int a = 0; a < 3; ++a)
+                p.gB[(3 * g + a) * n + o] = (float)(-(Mi[a][0] * t[0] + Mi[a][1] * t[1] + Mi[a][2] * t[2]));
+        }
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        const int64_t n = p.n;
+        p.A[o] = 0.f;
+        for (int a = 0; a < 3; ++a) { p.B[a * n + o] = 0.f; p.gA[a * n + o] = 0.f; }
+        for (int a = 0; a < 9; ++a) p.gB[a * n + o] = 0.f;
+    }
+};
+
+struct HydroP {
+    const float *m, *v3, *u, *V, *rho, *A, *B, *gA, *gB;
+    float *dv3, *du;
+    double *cons;
+    float gamma, alpha, beta, eta2;
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct HydroStage {
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = true;
+    using P = HydroP;
+    struct __align__(16) Rec {
+        float x, y, z, h;
+        float vx, vy, vz, P;
+        float c, rho, V, A;
+        float B[3], gA0;
+        float gA1, gA2, gB0, gB1;
+        float gB[7];  // gB[2..8]
+        float pad;
+    };
+    struct I {
+        float fx, fy, fz, e;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) {
+        const int64_t n = p.n;
+        Rec r;
+        r.x = ps.x; r.y = ps.y; r.z = ps.z; r.h = ps.w;
+        r.vx = p.v3[o]; r.vy = p.v3[n + o]; r.vz = p.v3[2 * n + o];
+        float rho = p.rho[o], u = p.u[o];
+        r.P = (p.gamma - 1.0f) * rho * u;
+        r.c = sqrtf(p.gamma * (p.gamma - 1.0f) * u);
+        r.rho = rho;
+        r.V = p.V[o];
+        r.A = p.A[o];
+        r.B[0] = p.B[o]; r.B[1] = p.B[n + o]; r.B[2] = p.B[2 * n + o];
+        r.gA0 = p.gA[o]; r.gA1 = p.gA[n + o]; r.gA2 = p.gA[2 * n + o];
+        r.gB0 = p.gB[o]; r.gB1 = p.gB[n + o];
+        for (int k = 0; k < 7; ++k) r.gB[k] = p.gB[(2 + k) * n + o];
+        r.pad = 0.f;
+        return r;
+    }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &) { s.fx = s.fy = s.fz = s.e = 0.f; s.cnt = 0; }
+    // grad W^R of record r at separation x (x = x_r - x_other): gA (1 + B.x) W + A (gB.x + B) W + A (1 + B.x) dWr x
+    __device__ static void grad_wr(const Rec &r, const float x[3], float W, float dWr, float g[3]) {
+        float Bx = fmaf(r.B[0], x[0], fmaf(r.B[1], x[1], r.B[2] * x[2]));
+        float gb[9] = {r.gB0, r.gB1, r.gB[0], r.gB[1], r.gB[2], r.gB[3], r.gB[4], r.gB[5], r.gB[6]};
+        float gA[3] = {r.gA0, r.gA1, r.gA2};
+        float k1 = (1.0f + Bx) * W;
+        float k3 = r.A * (1.0f + Bx) * dWr;
+        float AW = r.A * W;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float gBx = fmaf(gb[3 * q], x[0], fmaf(gb[3 * q + 1], x[1], gb[3 * q + 2] * x[2]));
+            g[q] = fmaf(gA[q], k1, fmaf(AW, gBx + r.B[q], k3 * x[q]));
+        }
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
+        float x[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};  // x_ij
+        float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float hij = 0.5f * hs;
+        float W, dWr;
+        wendland(r2, hij, W, dWr);
+        float gi[3], gj[3];
+        grad_wr(ri, x, W, dWr, gi);
+        float xm[3] = {-x[0], -x[1], -x[2]};
+        grad_wr(rj, xm, W, dWr, gj);
+        float vij[3] = {ri.vx - rj.vx, ri.vy - rj.vy, ri.vz - rj.vz};
+        float vx = fmaf(vij[0], x[0], fmaf(vij[1], x[1], vij[2] * x[2]));
+        float mu = vx < 0.0f ? __fdividef(hij * vx, fmaf(p.eta2 * hij, hij, r2)) : 0.0f;
+        float Q = 0.5f * (ri.rho + rj.rho) * mu * fmaf(-p.alpha * 0.5f, ri.c + rj.c, p.beta * mu);
+        float pre = in ? -0.5f * ri.V * rj.V * (ri.P + rj.P + Q) : 0.0f;
+        float f[3] = {pre * (gi[0] - gj[0]), pre * (gi[1] - gj[1]), pre * (gi[2] - gj[2])};
+        s.fx += f[0];
+        s.fy += f[1];
+        s.fz += f[2];
+        s.e = fmaf(-0.5f, fmaf(vij[0], f[0], fmaf(vij[1], f[1], vij[2] * f[2])), s.e);
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &ri, int32_t o) {
+        float mi = p.m[o];
+        float dvx = s.fx / mi, dvy = s.fy / mi, dvz = s.fz / mi, du = s.e / mi;
+        p.dv3[o] = dvx;
+        p.dv3[p.n + o] = dvy;
+        p.dv3[2 * p.n + o] = dvz;
+        p.du[o] = du;
+    }
+    // FP64 conservation terms of one gas particle: m dv (3) and m (v.dv + du)
+    __device__ static void cons_terms(const P &p, const I &s, const Rec &ri, int32_t o, double c[4]) {
+        double mi = (double)p.m[o];
+        double dvx = (double)(s.fx / p.m[o]), dvy = (double)(s.fy / p.m[o]), dvz = (double)(s.fz / p.m[o]);
+        double du = (double)(s.e / p.m[o]);
+        c[0] = mi * dvx;
+        c[1] = mi * dvy;
+        c[2] = mi * dvz;
+        c[3] = mi * ((double)ri.vx * dvx + (double)ri.vy * dvy + (double)ri.vz * dvz + du);
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        p.dv3[o] = 0.f;
+        p.dv3[p.n + o] = 0.f;
+        p.dv3[2 * p.n + o] = 0.f;
+        p.du[o] = 0.f;
+    }
+};
+
+// --------------------------------------------------------------- framework
+template <class S>
+__global__ void gather_kernel(int64_t n, const float4 *__restrict__ pos, const int32_t *__restrict__ kperm,
+                              typename S::P p, typename S::Rec *__restrict__ rec) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    rec[q] = S::gather(p, kperm[q], pos[q]);
+}
+
+template <class S, bool kCount>
+__global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S::P p,
+                                                        const typename S::Rec *__restrict__ rec,
+                                                        double *__restrict__ cons_part) {
+    using Rec = typename S::Rec;
+    __shared__ Rec buf[kWarps][kCap];
+    __shared__ double cons_sh[kWarps][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = lanemask_lt();
+    double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t a = blockIdx.x; a < lv.n_leaves; a += gridDim.x) {
+        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
+        const int ib = lv.img_ptr[a], ie = lv.img_ptr[a + 1];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
+            const int i = g0 + lane;
+            const bool act = i < hi;
+            const Rec ri = rec[act ? i : g0];
+            typename S::I st;
+            S::init(p, st, ri);
+            // i-group box and largest h (inactive lanes repeat lane 0's particle)
+            float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
+            float hm = lv.pos[act ? i : g0].w;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bl0 = fminf(bl0, __shfl_xor_sync(CRK_FULL_MASK, bl0, o));
+                bl1 = fminf(bl1, __shfl_xor_sync(CRK_FULL_MASK, bl1, o));
+                bl2 = fminf(bl2, __shfl_xor_sync(CRK_FULL_MASK, bl2, o));
+                bh0 = fmaxf(bh0, __shfl_xor_sync(CRK_FULL_MASK, bh0, o));
+                bh1 = fmaxf(bh1, __shfl_xor_sync(CRK_FULL_MASK, bh1, o));
+                bh2 = fmaxf(bh2, __shfl_xor_sync(CRK_FULL_MASK, bh2, o));
+                hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
+            }
+            int cnt = 0;
+            for (int e = ib; e < ie; ++e) {
+                const crk_image im = lv.img[e];
+                const int jlo = lv.leaf_start[im.b];
+                const int jhi = S::kGasOnly ? jlo + lv.leaf_ngas[im.b] : lv.leaf_start[im.b + 1];
+                // whole j-leaf against the i-group box (warp-uniform)
+                {
+                    const float *bb = lv.bbox + 6 * (int64_t)im.b;
+                    float gx = fmaxf(fmaxf(im.sx - bh0, bl0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+                    float gy = fmaxf(fmaxf(im.sy - bh1, bl1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+                    float gz = fmaxf(fmaxf(im.sz - bh2, bl2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+                    float cut = S::leaf_cut(p, hm, lv.hmax[im.b]);
+                    if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+                }
+                for (int j0 = jlo; j0 < jhi; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool jv = j < jhi;
+                    Rec rj;
+                    bool keep = false;
+                    if (jv) {
+                        rj = rec[j];
+                        S::shift(rj, im.sx, im.sy, im.sz);
+                        float dx = fmaxf(fmaxf(bl0 - rj.x, rj.x - bh0), 0.f);
+                        float dy = fmaxf(fmaxf(bl1 - rj.y, rj.y - bh1), 0.f);
+                        float dz = fmaxf(fmaxf(bl2 - rj.z, rj.z - bh2), 0.f);
+                        float cut = S::box_cut(p, hm, rj);
+                        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
+                    }
+                    const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+                    if (keep) buf[warp][cnt + __popc(m & below)] = rj;
+                    cnt += __popc(m);
+                    if (cnt >= 32) {
+                        __syncwarp();
+                        for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[warp][k]);
+                        cnt = 0;
+                        __syncwarp();
+                    }
+                }
+            }
+            __syncwarp();
+            for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[warp][k]);
+            __syncwarp();
+            if (act) S::finish(p, st, ri, lv.kperm[i]);
+            if constexpr (S::kCons) {
+                double c[4] = {0.0, 0.0, 0.0, 0.0};
+                if (act) S::cons_terms(p, st, ri, lv.kperm[i], c);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(CRK_FULL_MASK, c[k], o);
+                    cons_acc[k] += c[k];
+                }
+            }
+            if (kCount) {
+                int c = act ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
+                if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+            }
+        }
+        if (S::kGasOnly)
+            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.kperm[q]);
+    }
+    if constexpr (S::kCons) {
+        // per-block partial in a fixed order; reduced by cons_reduce_kernel (deterministic)
+        if (cons_part) {
+            if (lane == 0)
+                for (int k = 0; k < 4; ++k) cons_sh[warp][k] = cons_acc[k];
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 4; ++k) {
+                    double t = 0.0;
+                    for (int w = 0; w < kWarps; ++w) t += cons_sh[w][k];
+                    cons_part[4 * (int64_t)blockIdx.x + k] = t;
+                }
+        }
+    }
+}
+
+__global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, double *__restrict__ out) {
+    __shared__ double sh[256];
+    for (int k = 0; k < 4; ++k) {
+        double t = 0.0;
+        for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) t += part[4 * b + k];
+        sh[threadIdx.x] = t;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sh[0];
+        __syncthreads();
+    }
+}
+
+template <class S>
+int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pairs, double *cons = nullptr) {
+    if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
+    const int64_t n = lv->n;
+    if (n == 0) return CRK_OK;
+    using Rec = typename S::Rec;
+    Rec *rec = (Rec *)crk_scratch(ctx, 4, sizeof(Rec) * (size_t)n);
+    if (!rec) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
+    int64_t grid = lv->n_leaves;
+    if (grid < 1) grid = 1;
+    if (grid > 2147483647LL) grid = 2147483647LL;
+    double *part = nullptr;
+    if (cons) {
+        part = (double *)crk_scratch(ctx, 5, sizeof(double) * 4 * (size_t)grid);
+        if (!part) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
+    }
+    gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
+               gas_pairs ? lv->himg_ptr : lv->gimg_ptr, gas_pairs ? lv->himg : lv->gimg, lv->n_leaves};
+    if (p.count) {
+        CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
+        pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+    } else {
+        pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+    }
+    if (cons) cons_reduce_kernel<<<1, 256, 0, ctx->stream>>>(part, grid, cons);
+    ctx->launches += 2 + (cons ? 1 : 0);
+    CRK_LAUNCH_CHECK(ctx, "pair kernel");
+    return CRK_OK;
+}
+
+}  // namespace
+
+int grav_short(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m, float *a3,
+               int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !gp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !a3)) return crk_fail(ctx, CRK_EINVAL, "null array");
+    if (gp->r_cut != lv->r_cut_grav) return crk_fail(ctx, CRK_ESTATE, "r_cut differs from the leaves' r_cut_grav");
+    GravP p{};
+    p.m = m;
+    p.a3 = a3;
+    p.rc2 = gp->r_cut * gp->r_cut;
+    p.eps2 = gp->eps * gp->eps;
+    for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
+    p.n = lv->n;
+    p.count = (unsigned long long *)pair_count;
+    return run_stage<GravStage>(ctx, lv, p, false);
+}
+
+int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m,
+                       const float *abar3, float *gx3, float *gm) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !gp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !abar3 || !gx3 || !gm)) return crk_fail(ctx, CRK_EINVAL, "null array");
+    if (gp->r_cut != lv->r_cut_grav) return crk_fail(ctx, CRK_ESTATE, "r_cut differs from the leaves' r_cut_grav");
+    GravAdjP p{};
+    p.m = m;
+    p.abar = abar3;
+    p.gx3 = gx3;
+    p.gm = gm;
+    p.rc2 = gp->r_cut * gp->r_cut;
+    p.eps2 = gp->eps * gp->eps;
+    for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
+    p.n = lv->n;
+    p.count = nullptr;
+    return run_stage<GravAdjStage>(ctx, lv, p, false);
+}
+
+int crk_geometry(crk_ctx *ctx, const crk_leaves *lv, const float *m, float *V, float *rho, int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
+    if (lv->n > 0 && (!m || !V || !rho)) return crk_fail(ctx, CRK_EINVAL, "null array");
+    GeomP p{m, V, rho, lv->n, (unsigned long long *)pair_count};
+    return run_stage<GeomStage>(ctx, lv, p, true);
+}
+
+int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *V, const float *rhobar,
+                         const float *Vbar, float *gx3, float *gm) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
+    if (lv->n > 0 && (!m || !V || !rhobar || !gx3 || !gm)) return crk_fail(ctx, CRK_EINVAL, "null array");
+    GeomAdjP p{m, V, rhobar, Vbar, gx3, gm, lv->n, nullptr};
+    return run_stage<GeomAdjStage>(ctx, lv, p, true);
+}
+
+int crk_corrections(crk_ctx *ctx, const crk_leaves *lv, const float *V, float *A, float *B, float *gradA,
+                    float *gradB, int32_t *n_singular) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
+    if (lv->n > 0 && (!V || !A || !B || !gradA || !gradB)) return crk_fail(ctx, CRK_EINVAL, "null array");
+    if (n_singular) CRK_CUDA(ctx, cudaMemsetAsync(n_singular, 0, sizeof(int32_t), ctx->stream));
+    CorrP p{V, A, B, gradA, gradB, n_singular, lv->n, nullptr};
+    return run_stage<CorrStage>(ctx, lv, p, true);
+}
+
+int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+              const float *u, const float *V, const float *rho, const float *A, const float *B, const float *gradA,
+              const float *gradB, float *dvdt3, float *dudt, double *conservation, int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !hp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !v3 || !u || !V || !rho || !A || !B || !gradA || !gradB || !dvdt3 || !dudt))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, dvdt3, dudt, conservation,
+             hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count};
+    return run_stage<HydroStage>(ctx, lv, p, true, conservation);
+}

@@ -1,0 +1,102 @@
+"""ctypes binding of libcrk's C ABI (include/crk.h): the same names, argument marshalling only.
+
+Every compute step runs in the CUDA library.  Loading fails loudly when
+libcrk.so has not been built (``python -c "import __graft_entry__ as g;
+g.build()"`` builds it); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libcrk.so")
+
+CRK_OK = 0
+CRK_EINVAL = -1
+CRK_ENOMEM = -2
+CRK_ECUDA = -3
+CRK_EBOX = -4
+CRK_ESTATE = -5
+CRK_ETIMEOUT = -6
+STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
+                -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT"}
+
+
+class CrkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class crk_particles(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("species", ctypes.c_void_p), ("n", ctypes.c_int64), ("box", ctypes.c_float)]
+
+
+class crk_leaf_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("cells_per_side", ctypes.c_int), ("max_leaf", ctypes.c_int),
+                ("r_cut_grav", ctypes.c_float)]
+
+
+class crk_grav_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("r_cut", ctypes.c_float), ("poly", ctypes.c_float * 6)]
+
+
+class crk_hydro_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_float), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("eta2", ctypes.c_float)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+# name -> argument types (all return int unless listed in _VOID / _STR)
+SIGNATURES = {
+    "crk_create": [ctypes.POINTER(_P), _I, _P],
+    "crk_destroy": [_P],
+    "crk_set_stream": [_P, _P],
+    "crk_last_error": [_P],
+    "crk_version": [],
+    "crk_launch_count": [_P, ctypes.POINTER(_I64)],
+    "crk_build_leaves": [_P, ctypes.POINTER(crk_particles), _P, ctypes.POINTER(crk_leaf_params), ctypes.POINTER(_P)],
+    "crk_leaves_info": [_P, ctypes.POINTER(_I64)],
+    "crk_leaves_export": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "crk_leaves_free": [_P, _P],
+    "crk_geometry": [_P, _P, _P, _P, _P, _P],
+    "crk_corrections": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "crk_hydro": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 13,
+    "grav_short": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P],
+    "grav_short_adjoint": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P, _P],
+    "crk_geometry_adjoint": [_P, _P, _P, _P, _P, _P, _P, _P],
+}
+_VOID = {"crk_destroy", "crk_leaves_free"}
+_STR = {"crk_last_error", "crk_version"}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcrk.so (once).  Raises if the library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcrk.so not found at {LIB_PATH}: build it with paper_2310_16122_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name in _VOID else (ctypes.c_char_p if name in _STR else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(SIGNATURES)
+
+
+def check(status: int, ctx=None) -> None:
+    if status != CRK_OK:
+        msg = lib().crk_last_error(ctx).decode() if ctx else ""
+        raise CrkError(status, msg)
