@@ -1,0 +1,365 @@
+"""Benchmark of the CRK-HACC short-range pair path on GB300: pair interactions/s.
+
+One step = the whole hot path over one box: leaf build (RCB), geometry,
+corrections, hydro (acceleration + energy), short-range gravity, the gravity
+adjoint (cotangent 2a) and the geometry adjoint (cotangent 1 on every gas
+density).  ``value`` = ordered in-range pair interactions processed by all
+kernels of a step x steps / device time (inputs resident in HBM), summed over
+ranks.  Pair counts are the kernels' own in-range counts from an untimed
+counting step.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+path has) on a bounded sample of the same workload.
+
+Launch: python bench.py [--gpus N --steps K --warmup W --workload NAME]
+(N > 1 through torch.distributed.run: independent replica boxes, one per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# algorithmic FP32 operations per in-range pair (FMA = 2, add/mul = 1; MUFU counted apart),
+# from the operation lists of each kernel's pair term (derivation in the design doc)
+FLOPS_PER_PAIR = {"geometry": 24, "corrections": 135, "hydro": 160, "gravity": 29, "gravity_adjoint": 68,
+                  "geometry_adjoint": 31}
+MUFU_PER_PAIR = {"geometry": 2, "corrections": 2, "hydro": 3, "gravity": 1, "gravity_adjoint": 1,
+                 "geometry_adjoint": 2}
+STAGES = ["leaves", "geometry", "corrections", "hydro", "gravity", "gravity_adjoint", "geometry_adjoint"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="crk", choices=["crk", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "clustered", "adjoint", "tiny"])
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace-leaves", action="store_true", help="after timing, print leaf-build phase times")
+    return ap.parse_args()
+
+
+def make_box(name, rank):
+    from paper_2310_16122_gb300 import workloads as W
+
+    if name == "large":
+        b = W.clustered_box(256, 5000, W.SEEDS["large"] + 7919 * rank, name="large_2x256^3")
+    elif name == "clustered":
+        b = W.clustered_box(64, 200, W.SEEDS["clustered"] + 7919 * rank, name="clustered_2x64^3")
+    elif name == "adjoint":
+        b = W.clustered_box(32, 25, W.SEEDS["adjoint"] + 7919 * rank, name="adjoint_2x32^3")
+    else:
+        b = W.lattice_box(16, 0.2, W.SEEDS["tiny"] + 7919 * rank, h=1.0, leaf_mode=0, cells=4, name="tiny_2x16^3")
+    return b
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_reference(args, rank):
+    """The oracle as it stands, on a bounded sample of the same workload, on the host cores."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2310_16122_gb300 import workloads as W
+    import numpy as np
+
+    box = make_box(args.workload, 0)
+    I = O.from_box(box)
+    threads = O.num_threads()
+    sample_n = args.cpu_sample or (64 if args.workload == "large" else 256)
+    rng = np.random.default_rng(12345)
+    for _ in range(args.warmup):
+        O.sampled_chain(I, rng.choice(box.n, 8, replace=False), W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
+    pairs, t = 0, 0.0
+    for _ in range(args.steps):
+        s = rng.choice(box.n, sample_n, replace=False)
+        t0 = time.perf_counter()
+        r = O.sampled_chain(I, s, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
+        t += time.perf_counter() - t0
+        pairs += r["pairs"]
+    value = pairs / t
+    sample = (f"{sample_n} random particles per step of the {box.name} box: geometry on their two-hop gas "
+              f"neighbourhood, corrections on the one-hop, hydro and gravity adjoint on the sample, gravity "
+              f"on its gravity neighbourhood (FP64 oracle, OpenMP)")
+    line = {"impl": "reference", "metric": "pair interactions/s per GB300 (fwd & adjoint)", "value": value,
+            "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": box.name, "n_particles": box.n, "box": box.L, "sample": sample_n},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(box, seconds=10.0):
+    """Oracle pairs/s on a bounded sample of the workload (host cores).
+
+    The oracle rebuilds its cell lists over the whole box on every call, so
+    the sample grows until one call takes about `seconds`; that call is timed.
+    """
+    from oracle import oracle as O
+    from paper_2310_16122_gb300 import workloads as W
+    import numpy as np
+
+    I = O.from_box(box)
+    rng = np.random.default_rng(2024)
+    n_s, spent = 256, 0.0
+    while True:
+        s = rng.choice(box.n, min(n_s, box.n), replace=False)
+        t0 = time.perf_counter()
+        r = O.sampled_chain(I, s, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
+        dt = time.perf_counter() - t0
+        spent += dt
+        if dt >= seconds or n_s >= box.n or spent > 4 * seconds:
+            break
+        n_s = int(min(box.n, n_s * max(2.0, 1.2 * seconds / max(dt, 1e-3))))
+    return {"value": r["pairs"] / dt, "unit": "pairs/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{s.size} random i-particles of the same box through the oracle's sampled chain (geometry "
+                      f"on their two-hop gas neighbourhood, corrections one-hop, hydro, gravity on the gravity "
+                      f"neighbourhood, gravity adjoint); {r['pairs']} pairs in {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2310_16122_gb300 import api, native
+    from paper_2310_16122_gb300.build import build_library
+
+    build_library()
+    box = make_box(args.workload, rank)
+    ctx = api.Context(local)
+    db = api.DeviceBox(box, device=f"cuda:{local}")
+    gas = (db.species == 0).float()
+    stream = ctx.stream
+
+    def step(events=None, count=False):
+        def mark(k):
+            if events is not None:
+                events[k].record(stream)
+
+        mark(0)
+        lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+        mark(1)
+        V, rho, cg = api.geometry(ctx, lv, db.m, count)
+        mark(2)
+        A, B, gA, gB, ns = api.corrections(ctx, lv, V)
+        mark(3)
+        dv, du, cons, ch = api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, count)
+        mark(4)
+        a, ca = api.grav_short(ctx, lv, db.gp, db.m, count)
+        mark(5)
+        gx, gm = api.grav_short_adjoint(ctx, lv, db.gp, db.m, 2.0 * a)
+        mark(6)
+        gx2, gm2 = api.geometry_adjoint(ctx, lv, db.m, V, gas)
+        mark(7)
+        return dict(lv=lv, cons=cons, cg=cg, ch=ch, ca=ca, ns=ns, leaves=lv.n_leaves)
+
+    # counting step (untimed): pair counts of every kernel
+    r = step(count=True)
+    torch.cuda.synchronize()
+    p_h = int(r["ch"].item())
+    p_g = int(r["ca"].item())
+    pairs = {"geometry": int(r["cg"].item()), "corrections": p_h, "hydro": p_h, "gravity": p_g,
+             "gravity_adjoint": p_g, "geometry_adjoint": p_h}
+    pairs_step = sum(pairs.values())
+    n_leaves = r["leaves"]
+    del r
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ctypes_launches(ctx)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    launches = ctypes_launches(ctx) - launches0
+    ms = t0.elapsed_time(t1)
+    per_stage = {s: 0.0 for s in STAGES}
+    for k in range(args.steps):
+        for i, s in enumerate(STAGES):
+            per_stage[s] += ev[k][i].elapsed_time(ev[k][i + 1])
+    per_stage = {s: v / args.steps for s, v in per_stage.items()}
+    t_max = ms
+    total_pairs = pairs_step * args.steps
+    if dist:
+        tt = torch.tensor([ms, float(total_pairs)], dtype=torch.float64, device=f"cuda:{local}")
+        tm = tt.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_max, total_pairs = float(tm[0]), float(tt[1])
+    value = total_pairs / (t_max * 1e-3)
+
+    if args.trace_leaves:
+        native.lib().crk_set_trace(ctx.handle, 1)
+        api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+        native.lib().crk_set_trace(ctx.handle, 0)
+
+    # end to end through the public API: pinned host inputs -> device, step, result -> host
+    host = {k: getattr(db, k).cpu().pin_memory() for k in ("x", "y", "z", "species", "m", "h", "u", "v3")}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    out_host = torch.empty(4, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    te0.record(stream)
+    for _ in range(e2e_steps):
+        for k, t in host.items():
+            getattr(db, k).copy_(t, non_blocking=True)
+        res = step()
+        out_host.copy_(res["cons"], non_blocking=True)
+    te1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = te0.elapsed_time(te1) / e2e_steps
+    e2e_value = pairs_step / (e2e_ms * 1e-3) * world
+
+    # roofline of the dominant kernel (ALU bound: FP32 FMA pipe)
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = n_sm * 128 * 2 * f_max * 1e6 / 1e12
+    kern = {s: v for s, v in per_stage.items() if s in FLOPS_PER_PAIR}
+    dom = max(kern, key=kern.get)
+    achieved = FLOPS_PER_PAIR[dom] * pairs[dom] / (kern[dom] * 1e-3) / 1e12
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get(args.workload, {}).get(dom)
+    except Exception:
+        pass
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic, "kernel": dom,
+                "peak_basis": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flop x {f_max:.0f} MHz (max SM clock)",
+                "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs_per_launch": pairs[dom],
+                "ms_per_launch": kern[dom]}
+    all_flops = sum(FLOPS_PER_PAIR[s] * pairs[s] for s in FLOPS_PER_PAIR)
+    kern_ms = sum(kern.values())
+
+    line = {"metric": "pair interactions/s per GB300 (fwd & adjoint)", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": box.name, "n_particles": box.n, "n_gas": box.n_gas, "box": box.L,
+                       "leaves": n_leaves, "max_leaf": box.max_leaf, "r_cut": box.r_cut,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs (~%.1f GB) larger than L2 (129 MB)" % (h2d / 1e9)},
+            "pairs_per_step": pairs, "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+            "kernels_tflops": all_flops / (kern_ms * 1e-3) / 1e12,
+            "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 32,
+                    "ms_per_step": e2e_ms}}
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(box)
+        except Exception as e:  # reported, never silent
+            line["cpu_baseline"] = {"value": None, "error": repr(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def ctypes_launches(ctx):
+    import ctypes
+
+    from paper_2310_16122_gb300 import native
+
+    c = ctypes.c_int64(0)
+    native.check(native.lib().crk_launch_count(ctx.handle, ctypes.byref(c)), ctx.handle)
+    return int(c.value)
+
+
+if __name__ == "__main__":
+    main()

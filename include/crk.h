@@ -95,6 +95,25 @@ int crk_set_stream(crk_ctx *ctx, void *cuda_stream);
 const char *crk_last_error(const crk_ctx *ctx);
 /* Library version and build info, e.g. "libcrk 1 sm_103a". */
 const char *crk_version(void);
+/* Tracing: when on (or when the environment variable CRK_TRACE is set at
+ * crk_create), crk_build_leaves synchronises after each phase and prints the
+ * phase times to stderr.  Off by default; it serialises the build. */
+int crk_set_trace(crk_ctx *ctx, int on);
+/* Kernel variants: the execution scheme of one pair kernel (the results agree
+ * within FP32 rounding).  Gas-pair kernels (geometry, corrections, hydro,
+ * geometry adjoint): CRK_VARIANT_LISTS walks the exact neighbour lists built
+ * with the leaves, CRK_VARIANT_TILES sweeps ballot-compacted j-leaf tiles.
+ * Gravity kernels have CRK_VARIANT_TILES only.  crk_tune picks per kernel. */
+#define CRK_K_GEOMETRY 0
+#define CRK_K_CORRECTIONS 1
+#define CRK_K_HYDRO 2
+#define CRK_K_GRAVITY 3
+#define CRK_K_GRAVITY_ADJOINT 4
+#define CRK_K_GEOMETRY_ADJOINT 5
+#define CRK_VARIANT_LISTS 0
+#define CRK_VARIANT_TILES 1
+int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
+int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant);
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int crk_launch_count(const crk_ctx *ctx, int64_t *out);
 

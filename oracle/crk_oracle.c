@@ -275,7 +275,7 @@ int orc_gravity(int64_t n, const double *pos, const double *m, double L, double 
 /* ------------------------------------------------------------------------ */
 int orc_gravity_adjoint(int64_t n, const double *pos, const double *m, double L, double rc, double eps,
                         const double *poly, const double *abar, const int64_t *sub, int64_t nsub, int brute,
-                        double *gx, double *gm) {
+                        double *gx, double *gm, int64_t *npairs) {
     if (n < 0 || L <= 0 || rc <= 0 || !(rc < 0.5 * L)) return ORC_EBOX;
     CellList cl;
     if (cells_build(&cl, n, pos, NULL, L, rc, brute)) return ORC_ENOMEM;
@@ -303,6 +303,7 @@ int orc_gravity_adjoint(int64_t n, const double *pos, const double *m, double L,
         gm[i] = gmi;
     });
     cells_free(&cl);
+    if (npairs) *npairs = pairs;
     return ORC_OK;
 }
 
@@ -383,13 +384,14 @@ static void inv3(const double M[3][3], double det, double R[3][3]) {
 
 int orc_corrections(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *V, double L,
                     const int64_t *sub, int64_t nsub, int brute, double *A, double *B, double *gA, double *gB,
-                    int64_t *nsing) {
+                    int64_t *nsing, int64_t *npairs) {
     double hmax = max_h_gas(n, species, h);
     if (n < 0 || L <= 0 || !(2.0 * hmax < 0.5 * L)) return ORC_EBOX;
     uint8_t *gmask = gas_mask(n, species);
     CellList cl;
     if (cells_build(&cl, n, pos, gmask, L, 2.0 * hmax > 0 ? 2.0 * hmax : L, brute)) { free(gmask); return ORC_ENOMEM; }
-    int64_t pairs = 0; /* counts singular particles here */
+    int64_t pairs = 0; /* in-range pairs with i != j */
+    int64_t singular = 0;
     FOR_EACH_I(sub, nsub, n, {
         if (species[i] != 0) {
             A[i] = 0.0;
@@ -407,6 +409,7 @@ int orc_corrections(int64_t n, const double *pos, const uint8_t *species, const 
             double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
             double hij = 0.5 * (h[i] + h[j]);
             if (!(r2 < 4.0 * hij * hij)) continue;
+            if (j != i) ++pairs;
             double W, dWr;
             wendland(sqrt(r2), hij, &W, &dWr);
             double dW[3] = {dWr * x[0], dWr * x[1], dWr * x[2]};
@@ -428,7 +431,7 @@ int orc_corrections(int64_t n, const double *pos, const uint8_t *species, const 
         double det = det3(m2);
         double tr = m2[0][0] + m2[1][1] + m2[2][2];
         if (!(det > 1e-12 * tr * tr * tr)) {
-            ++pairs;
+            _Pragma("omp atomic") ++singular;
             A[i] = NAN;
             for (int c = 0; c < 3; ++c) { B[3 * i + c] = NAN; gA[3 * i + c] = NAN; }
             for (int c = 0; c < 9; ++c) gB[9 * i + c] = NAN;
@@ -458,7 +461,8 @@ int orc_corrections(int64_t n, const double *pos, const uint8_t *species, const 
     });
     cells_free(&cl);
     free(gmask);
-    if (nsing) *nsing = pairs;
+    if (nsing) *nsing = singular;
+    if (npairs) *npairs = pairs;
     return ORC_OK;
 }
 
@@ -786,4 +790,37 @@ int orc_leaf_pairs(int64_t n_leaves, const int32_t *leaf_start, const int32_t *p
     *total = k;
     free(bx);
     return k <= cap ? ORC_OK : ORC_ENOMEM;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour closure (test/benchmark helper): mark[j] = 1 for every j that is */
+/* in range of some i with mark_in[i] != 0, and for those i themselves.       */
+/* hydro != 0: gas pairs with r < h_i + h_j; else all pairs with r < rc.      */
+/* ------------------------------------------------------------------------ */
+int orc_mark_neighbours(int64_t n, const double *pos, const uint8_t *species, const double *h, double L, double rc,
+                        int hydro, const uint8_t *mark_in, uint8_t *mark_out) {
+    double hmax = max_h_gas(n, species, h);
+    double cut = hydro ? 2.0 * hmax : rc;
+    if (!(cut > 0.0) || !(cut < 0.5 * L)) return ORC_EBOX;
+    uint8_t *gm = hydro ? gas_mask(n, species) : NULL;
+    CellList cl;
+    if (cells_build(&cl, n, pos, gm, L, cut, 0)) { free(gm); return ORC_ENOMEM; }
+    int64_t *buf = (int64_t *)malloc(sizeof(int64_t) * (size_t)cells_buffer_size(&cl));
+    for (int64_t i = 0; i < n; ++i) mark_out[i] = mark_in[i];
+    for (int64_t i = 0; i < n; ++i) {
+        if (!mark_in[i] || (hydro && species[i] != 0)) continue;
+        int64_t nc = cells_candidates(&cl, &pos[3 * i], buf);
+        for (int64_t t = 0; t < nc; ++t) {
+            int64_t j = buf[t];
+            double d[3];
+            min_image(&pos[3 * i], &pos[3 * j], L, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double c = hydro ? h[i] + h[j] : rc;
+            if (r2 < c * c) mark_out[j] = 1;
+        }
+    }
+    free(buf);
+    cells_free(&cl);
+    free(gm);
+    return ORC_OK;
 }

@@ -54,11 +54,12 @@ def lib():
             L.orc_gravity.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double, _d,
                                       _i64, ctypes.c_int64, ctypes.c_int, _d, _i64]
             L.orc_gravity_adjoint.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double,
-                                              ctypes.c_double, _d, _d, _i64, ctypes.c_int64, ctypes.c_int, _d, _d]
+                                              ctypes.c_double, _d, _d, _i64, ctypes.c_int64, ctypes.c_int, _d, _d,
+                                              _i64]
             L.orc_geometry.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
                                        ctypes.c_int, _d, _d, _i64]
             L.orc_corrections.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
-                                          ctypes.c_int, _d, _d, _d, _d, _i64]
+                                          ctypes.c_int, _d, _d, _d, _d, _i64, _i64]
             L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
@@ -68,7 +69,9 @@ def lib():
             L.orc_leaves_rcb.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_int, _i32, _i32, ctypes.c_int64, _i64]
             L.orc_leaf_pairs.argtypes = [ctypes.c_int64, _i32, _i32, _d, _u8, _d, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, _i32, ctypes.c_int64, _i32, _i32, ctypes.c_int64, _i64]
-            for name in ("orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections", "orc_hydro",
+            L.orc_mark_neighbours.argtypes = [ctypes.c_int64, _d, _u8, _d, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, _u8, _u8]
+            for name in ("orc_mark_neighbours", "orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections", "orc_hydro",
                          "orc_geometry_adjoint", "orc_leaves_mesh", "orc_leaves_rcb", "orc_leaf_pairs"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -164,14 +167,17 @@ def gravity(I: Inputs, sub=None, brute=False):
     return acc, int(npairs.value)
 
 
-def gravity_adjoint(I: Inputs, abar, sub=None, brute=False):
+def gravity_adjoint(I: Inputs, abar, sub=None, brute=False, with_pairs=False):
     abar = _f64(abar).reshape(-1, 3)
     gx = np.zeros((I.n, 3))
     gm = np.zeros(I.n)
+    npairs = ctypes.c_int64(0)
     s, ns = _sub(sub)
     _check(lib().orc_gravity_adjoint(I.n, _p(I.pos, _d), _p(I.m, _d), I.L, I.r_cut, I.eps, _p(I.poly, _d),
-                                     _p(abar, _d), _p(s, _i64), ns, int(brute), _p(gx, _d), _p(gm, _d)),
-           "gravity_adjoint")
+                                     _p(abar, _d), _p(s, _i64), ns, int(brute), _p(gx, _d), _p(gm, _d),
+                                     ctypes.byref(npairs)), "gravity_adjoint")
+    if with_pairs:
+        return gx, gm, int(npairs.value)
     return gx, gm
 
 
@@ -186,7 +192,7 @@ def geometry(I: Inputs, sub=None, brute=False):
     return V, rho, int(npairs.value)
 
 
-def corrections(I: Inputs, V, sub=None, brute=False):
+def corrections(I: Inputs, V, sub=None, brute=False, with_pairs=False):
     """A f64[n], B f64[n,3], gradA f64[n,3], gradB f64[n,9] (gradB[i, 3g+a] = d_g B^a) and #singular."""
     V = _f64(V)
     A = np.zeros(I.n)
@@ -194,10 +200,14 @@ def corrections(I: Inputs, V, sub=None, brute=False):
     gA = np.zeros((I.n, 3))
     gB = np.zeros((I.n, 9))
     ns_ = ctypes.c_int64(0)
+    np_ = ctypes.c_int64(0)
     s, ns = _sub(sub)
     _check(lib().orc_corrections(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(V, _d), I.L, _p(s, _i64),
-                                 ns, int(brute), _p(A, _d), _p(B, _d), _p(gA, _d), _p(gB, _d), ctypes.byref(ns_)),
+                                 ns, int(brute), _p(A, _d), _p(B, _d), _p(gA, _d), _p(gB, _d), ctypes.byref(ns_),
+                                 ctypes.byref(np_)),
            "corrections")
+    if with_pairs:
+        return A, B, gA, gB, int(ns_.value), int(np_.value)
     return A, B, gA, gB, int(ns_.value)
 
 
@@ -243,6 +253,35 @@ def forward(I: Inputs, gamma, alpha, beta, eta2, brute=False):
     acc, ng = gravity(I, brute=brute)
     return dict(V=V, rho=rho, A=A, B=B, gA=gA, gB=gB, dv=dv, du=du, acc=acc, pairs_hydro=nh, pairs_grav=ng,
                 singular=nsing)
+
+
+def neighbour_closure(I: Inputs, sub, hydro: bool):
+    """Indices of sub together with every particle in range of one of them."""
+    mi = np.zeros(I.n, np.uint8)
+    mi[np.asarray(sub, np.int64)] = 1
+    mo = np.zeros(I.n, np.uint8)
+    _check(lib().orc_mark_neighbours(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), I.L, I.r_cut,
+                                     int(hydro), _p(mi, _u8), _p(mo, _u8)), "mark_neighbours")
+    return np.nonzero(mo)[0]
+
+
+def sampled_chain(I: Inputs, sample, gamma, alpha, beta, eta2):
+    """The forward chain plus the gravity adjoint for a sample of i-particles, every upstream
+    value computed by the oracle itself: geometry on the two-hop gas closure, corrections on
+    the one-hop closure, hydro and gravity on the sample.  Returns outputs and pair counts."""
+    gas = I.species == 0
+    s0 = np.asarray(sample, np.int64)
+    s1 = neighbour_closure(I, s0[gas[s0]], True) if np.any(gas[s0]) else s0[:0]
+    s2 = neighbour_closure(I, s1, True) if s1.size else s1
+    g1 = neighbour_closure(I, s0, False)
+    V, rho, n_geo = geometry(I, sub=s2)
+    A, B, gA, gB, _, n_corr = corrections(I, V, sub=s1, with_pairs=True)
+    dv, du, n_hyd = hydro(I, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, sub=s0)
+    acc, n_grav = gravity(I, sub=g1)
+    gx, gm, n_adj = gravity_adjoint(I, 2.0 * acc, sub=s0, with_pairs=True)
+    pairs = n_geo + n_corr + n_hyd + n_grav + n_adj
+    return dict(V=V, rho=rho, A=A, B=B, gA=gA, gB=gB, dv=dv, du=du, acc=acc, gx=gx, gm=gm, s1=s1, s2=s2,
+                g1=g1, pairs=pairs, n_grav=n_grav, n_hydro=n_hyd)
 
 
 # ------------------------------------------------------------------- leaves

@@ -52,6 +52,14 @@ class Context:
         except Exception:
             pass
 
+    def set_variant(self, kernel: str, variant: int) -> None:
+        self.check(N.lib().crk_set_variant(self.handle, N.KERNELS[kernel], int(variant)))
+
+    def get_variant(self, kernel: str) -> int:
+        v = ctypes.c_int(0)
+        self.check(N.lib().crk_get_variant(self.handle, N.KERNELS[kernel], ctypes.byref(v)))
+        return int(v.value)
+
     def empty(self, *shape, dtype=torch.float32):
         return torch.empty(*shape, dtype=dtype, device=self.device)
 
@@ -117,7 +125,8 @@ class Leaves:
 
     def free(self) -> None:
         if self.handle:
-            N.lib().crk_leaves_free(self.ctx.handle, self.handle)
+            # a closed context cannot take the buffers back: free them directly
+            N.lib().crk_leaves_free(self.ctx.handle if self.ctx.handle else None, self.handle)
             self.handle = None
 
     def __del__(self):

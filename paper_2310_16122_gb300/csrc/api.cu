@@ -1,6 +1,7 @@
 // Context, errors and device memory of libcrk.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 
 #include "crk_internal.cuh"
 
@@ -47,14 +48,33 @@ void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes) {
 }
 
 void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes) {
-    (void)ctx;
-    void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    // best fit among cached blocks no more than twice as large
+    int best = -1;
+    for (size_t k = 0; k < ctx->block_cache.size(); ++k) {
+        size_t sz = ctx->block_cache[k].second;
+        if (sz >= bytes && sz <= 2 * bytes + (1 << 16) && (best < 0 || sz < ctx->block_cache[best].second))
+            best = (int)k;
+    }
+    if (best >= 0) {
+        auto blk = ctx->block_cache[best];
+        ctx->block_cache.erase(ctx->block_cache.begin() + best);
+        lv->allocs.push_back(blk);
+        return blk.first;
+    }
+    void *p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        // drop the cache and retry once
+        for (auto &b : ctx->block_cache) cudaFree(b.first);
+        ctx->block_cache.clear();
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
     }
-    lv->allocs.push_back(p);
+    lv->allocs.push_back({p, bytes});
     return p;
 }
 
@@ -73,6 +93,10 @@ int crk_create(crk_ctx **out, int device, void *cuda_stream) {
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    const char *tr = getenv("CRK_TRACE");
+    ctx->trace = tr && tr[0] && tr[0] != '0';
+    ctx->variant[CRK_K_GRAVITY] = CRK_VARIANT_TILES;
+    ctx->variant[CRK_K_GRAVITY_ADJOINT] = CRK_VARIANT_TILES;
     *out = ctx;
     return CRK_OK;
 }
@@ -82,6 +106,8 @@ void crk_destroy(crk_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (int s = 0; s < crk_ctx::kSlots; ++s)
         if (ctx->slot[s]) cudaFree(ctx->slot[s]);
+    for (auto &b : ctx->block_cache) cudaFree(b.first);
+    crk_rcb_shape_free(ctx);
     delete ctx;
 }
 
@@ -94,6 +120,28 @@ int crk_set_stream(crk_ctx *ctx, void *cuda_stream) {
 const char *crk_last_error(const crk_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 const char *crk_version(void) { return "libcrk 1 sm_103a"; }
+
+int crk_set_variant(crk_ctx *ctx, int kernel, int variant) {
+    if (!ctx) return CRK_EINVAL;
+    if (kernel < 0 || kernel > CRK_K_GEOMETRY_ADJOINT) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
+    bool gas = kernel != CRK_K_GRAVITY && kernel != CRK_K_GRAVITY_ADJOINT;
+    if (variant != CRK_VARIANT_TILES && !(gas && variant == CRK_VARIANT_LISTS))
+        return crk_fail(ctx, CRK_EINVAL, "variant %d not available for kernel %d", variant, kernel);
+    ctx->variant[kernel] = variant;
+    return CRK_OK;
+}
+
+int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant) {
+    if (!ctx || !variant || kernel < 0 || kernel > CRK_K_GEOMETRY_ADJOINT) return CRK_EINVAL;
+    *variant = ctx->variant[kernel];
+    return CRK_OK;
+}
+
+int crk_set_trace(crk_ctx *ctx, int on) {
+    if (!ctx) return CRK_EINVAL;
+    ctx->trace = on != 0;
+    return CRK_OK;
+}
 
 int crk_launch_count(const crk_ctx *ctx, int64_t *out) {
     if (!ctx || !out) return CRK_EINVAL;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/crk.h"
@@ -19,6 +20,22 @@ struct crk_image {
     float sx, sy, sz;
 };
 
+// Shape of an RCB tree: with the left child taking floor(n/2) it depends on
+// the particle count and the leaf capacity only, so it is computed once on
+// the host and cached (with its device copies) in the context.
+struct crk_rcb_shape {
+    int64_t n = -1;
+    int max_leaf = 0;
+    int64_t n_leaves = 0, n_nodes = 0;
+    int max_leaf_size = 0;
+    std::vector<size_t> level_off, level_size;  // segment tables, 6 int32 columns per level
+    int32_t *dtab = nullptr;                    // device: lo, hi, k, child, node, axis per segment
+    int32_t *leaf_start = nullptr;              // device [n_leaves + 1]
+    int32_t *left = nullptr, *right = nullptr;  // device [n_nodes], -1 for leaves
+    int32_t *leaf_of = nullptr;                 // device [n_nodes], leaf id or -1
+    int32_t *leaf_node = nullptr;               // device [n_leaves]
+};
+
 struct crk_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -29,6 +46,13 @@ struct crk_ctx {
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     int64_t launches = 0;  // kernels this context has launched
+    // device blocks released by crk_leaves_free, reused by later leaf builds
+    // on this context (stream order makes the reuse safe)
+    std::vector<std::pair<void *, size_t>> block_cache;
+    crk_rcb_shape *rcb = nullptr;
+    bool trace = false;  // CRK_TRACE=1: synchronise and print phase times of the leaf build
+    // kernel variants (autotuner choices), indexed by CRK_K_*; 0 = default
+    int variant[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 struct crk_leaves {
@@ -48,14 +72,26 @@ struct crk_leaves {
     float *bbox = nullptr;          // [n_leaves][6]: lo xyz, hi xyz
     float *hmax = nullptr;          // [n_leaves]
     float4 *pos = nullptr;          // [n] kernel order: leaf-relative x, y, z and h (gas) or 0
-    int32_t *gimg_ptr = nullptr;    // [n_leaves + 1]
+    // leaf-pair lists: per i-leaf a, entries [start[a], start[a] + count[a]) in
+    // ascending j-leaf order (leaves may be laid out in any order)
+    int32_t *gimg_start = nullptr, *gimg_cnt = nullptr;  // gravity images
     crk_image *gimg = nullptr;
-    int32_t *himg_ptr = nullptr;
+    int32_t *himg_start = nullptr, *himg_cnt = nullptr;  // hydro images
     crk_image *himg = nullptr;
-    int32_t *gpair_ptr = nullptr, *gpair_list = nullptr;
-    int32_t *hpair_ptr = nullptr, *hpair_list = nullptr;
+    int32_t *gpair_start = nullptr, *gpair_cnt = nullptr, *gpair_list = nullptr;  // canonical gravity pairs
+    int32_t *hpair_start = nullptr, *hpair_cnt = nullptr, *hpair_list = nullptr;  // canonical hydro pairs
     int64_t n_gimg = 0, n_himg = 0, n_gpairs = 0, n_hpairs = 0;
-    std::vector<void *> allocs;
+    // exact gas neighbour lists (r < h_i + h_j, decided in FP32 exactly as the
+    // kernels decide it), one block per group of 32 consecutive gas particles
+    // of a leaf in kernel order, stored k-major (entry k of lane l at k*32 + l);
+    // an entry is (image index in the leaf's hydro image list << 10) | index of
+    // j inside its leaf
+    int32_t *gl_gstart = nullptr;  // [n_leaves + 1] first group of each leaf
+    int32_t *gl_goff = nullptr;    // [groups + 1] group offsets, units of 32 entries
+    int32_t *gl_cnt = nullptr;     // [n] list length per kernel-order position (gas)
+    uint32_t *gl_list = nullptr;
+    int64_t gl_groups = 0, gl_entries = 0, n_gas_pairs = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
 };
 
 // ---- host helpers (api.cu) ----
@@ -63,6 +99,8 @@ int crk_fail(crk_ctx *ctx, int code, const char *fmt, ...);
 int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes);
 void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes);
+void crk_rcb_shape_free(crk_ctx *ctx);
+int crk_build_gas_lists(crk_ctx *ctx, crk_leaves *lv);
 
 #define CRK_CUDA(ctx, call)                                          \
     do {                                                             \

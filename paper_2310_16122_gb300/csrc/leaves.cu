@@ -10,6 +10,8 @@
 // stably partitioned by a prefix sum of the side flags.  The shape of the
 // tree depends on n alone, so the host precomputes every level's segments.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cstring>
 
 #include "crk_internal.cuh"
@@ -148,8 +150,20 @@ __global__ void rcb_scatter_kernel(int64_t n, LevelDev lv, const int32_t *__rest
 }
 
 // --- per-leaf data ------------------------------------------------------------
-// One block per leaf: canonical order (gas first, then dark matter, each by
-// index), tight box, gas count, largest gas h, leaf-relative positions.
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 1023u;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// One block per leaf: tight box, gas count, largest gas h; the canonical
+// order (gas first, then dark matter, each by index) for export; the kernel
+// order (gas first, then dark matter, each along a Z-order curve of the
+// leaf box, ties by index) so that 32 consecutive particles are compact; and
+// the leaf-relative positions in kernel order.
 __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
                                  const int32_t *__restrict__ members, const float *__restrict__ x,
                                  const float *__restrict__ y, const float *__restrict__ z,
@@ -168,21 +182,12 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
         if (threadIdx.x == 0) atomicAdd(err, 1);
         return;
     }
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        int32_t id = members[lo + t];
-        key[t] = ((uint64_t)(sp[id] != 0) << 32) | (uint32_t)id;
-    }
-    __syncthreads();
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     int ng = 0;
     float hm = 0.0f;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        uint64_t kt = key[t];
-        int r = 0;
-        for (int u = 0; u < cnt; ++u) r += key[u] < kt;
-        int32_t id = (int32_t)(uint32_t)kt;
-        perm[lo + r] = id;
-        kperm[lo + r] = id;
+        int32_t id = members[lo + t];
+        key[t] = ((uint64_t)(sp[id] != 0) << 32) | (uint32_t)id;
         float c[3] = {x[id], y[id], z[id]};
         for (int q = 0; q < 3; ++q) {
             mn[q] = fminf(mn[q], c[q]);
@@ -226,34 +231,72 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
     }
     __syncthreads();
     const float ox = red[0][0], oy = red[1][0], oz = red[2][0];
+    const float ext = fmaxf(fmaxf(red[3][0] - ox, red[4][0] - oy), fmaxf(red[5][0] - oz, 1e-30f));
+    const float sc = 1023.0f / ext;
+    // canonical ranks, and the Z-order key of each member (kept in registers)
+    uint64_t zkey[kMaxLeafCap / 128];
+    int nk = 0;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        int32_t id = kperm[lo + t];
-        pos[lo + t] = make_float4(x[id] - ox, y[id] - oy, z[id] - oz, sp[id] == 0 ? h[id] : 0.0f);
+        uint64_t kt = key[t];
+        int r = 0;
+        for (int u = 0; u < cnt; ++u) r += key[u] < kt;
+        int32_t id = (int32_t)(uint32_t)kt;
+        perm[lo + r] = id;
+        uint32_t mx3 = spread10((uint32_t)fminf((x[id] - ox) * sc, 1023.0f)) |
+                       (spread10((uint32_t)fminf((y[id] - oy) * sc, 1023.0f)) << 1) |
+                       (spread10((uint32_t)fminf((z[id] - oz) * sc, 1023.0f)) << 2);
+        zkey[nk++] = ((uint64_t)(sp[id] != 0) << 62) | ((uint64_t)mx3 << 32) | (uint32_t)id;
+    }
+    __syncthreads();
+    nk = 0;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) key[t] = zkey[nk++];
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        uint64_t kt = key[t];
+        int r = 0;
+        for (int u = 0; u < cnt; ++u) r += key[u] < kt;
+        int32_t id = (int32_t)(uint32_t)kt;
+        kperm[lo + r] = id;
+        pos[lo + r] = make_float4(x[id] - ox, y[id] - oy, z[id] - oz, sp[id] == 0 ? h[id] : 0.0f);
     }
 }
 
 // --- leaf-pair images ------------------------------------------------------------
 struct TreeDev {
     const float *node_box;       // [nodes][6]
+    const float *node_hmax;      // [nodes] largest gas h below the node
     const int32_t *node_left;    // child ids, -1 for leaves
     const int32_t *node_right;
     const int32_t *node_leaf;    // leaf id for leaves, -1 otherwise
     int32_t root;
 };
 
+// FP32 periodic box gap, used only to discard candidates that are clearly out
+// of range (the caller adds a margin far above the FP32 rounding of the sums)
+__device__ __forceinline__ float axis_gap32(float loa, float hia, float lob, float hib, float L) {
+    float best = INFINITY;
+#pragma unroll
+    for (int k = -1; k <= 1; ++k) {
+        float s = (float)k * L;
+        float g = fmaxf(fmaxf((lob + s) - hia, (loa - hib) - s), 0.0f);
+        best = fminf(best, g);
+    }
+    return best;
+}
+
+__device__ __forceinline__ bool clearly_apart(const float *A, const float *B, float L, float cut) {
+    float gx = axis_gap32(A[0], A[3], B[0], B[3], L);
+    float gy = axis_gap32(A[1], A[4], B[1], B[4], L);
+    float gz = axis_gap32(A[2], A[5], B[2], B[5], L);
+    float c = cut + 1e-5f * L + 1e-6f;
+    return gx * gx + gy * gy + gz * gz > c * c;
+}
+
 __device__ __forceinline__ double axis_gap_shift(double loa, double hia, double lob, double hib, double s) {
     double t1 = __dsub_rn(__dadd_rn(lob, s), hia);
     double t2 = __dsub_rn(__dsub_rn(loa, hib), s);
     double g = t1 > t2 ? t1 : t2;
     return g < 0.0 ? 0.0 : g;
-}
-
-__device__ __forceinline__ double axis_gap(double loa, double hia, double lob, double hib, double L) {
-    double g0 = axis_gap_shift(loa, hia, lob, hib, -L);
-    double g1 = axis_gap_shift(loa, hia, lob, hib, 0.0);
-    double g2 = axis_gap_shift(loa, hia, lob, hib, L);
-    double g = g0 < g1 ? g0 : g1;
-    return g < g2 ? g : g2;
 }
 
 __device__ __forceinline__ double sum_sq(double gx, double gy, double gz) {
@@ -265,6 +308,7 @@ template <bool kFill>
 __device__ int leaf_images(const float *__restrict__ bbox, int64_t a, int64_t b, double L, double cut2,
                            crk_image *__restrict__ out) {
     const float *A = bbox + 6 * a, *B = bbox + 6 * b;
+    if (clearly_apart(A, B, (float)L, (float)sqrt(cut2))) return 0;
     double g[3][3];
     for (int q = 0; q < 3; ++q) {
         g[q][0] = axis_gap_shift(A[q], A[3 + q], B[q], B[3 + q], -L);
@@ -326,18 +370,15 @@ __global__ void pairs_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_
         if (brute) {
             for (int64_t b = 0; b < n_leaves; ++b) visit_leaf(b);
         } else {
-            double cutn = hydro ? 2.0 * (ha > hmax_all ? ha : hmax_all) : rc;
-            double cutn2 = cutn * cutn * (1.0 + 1e-12);
+            (void)hmax_all;
             int32_t stack[64];
             int top = 0;
             stack[top++] = tree.root;
             while (top > 0) {
                 int32_t nd = stack[--top];
                 const float *Nb = tree.node_box + 6 * (int64_t)nd;
-                double gx = axis_gap(A[0], A[3], Nb[0], Nb[3], L);
-                double gy = axis_gap(A[1], A[4], Nb[1], Nb[4], L);
-                double gz = axis_gap(A[2], A[5], Nb[2], Nb[5], L);
-                if (!(sum_sq(gx, gy, gz) < cutn2)) continue;
+                float cutn = hydro ? 2.0f * fmaxf((float)ha, tree.node_hmax[nd]) : (float)rc;
+                if (clearly_apart(A, Nb, (float)L, cutn)) continue;
                 int32_t lf = tree.node_leaf[nd];
                 if (lf >= 0) {
                     visit_leaf(lf);
@@ -354,11 +395,210 @@ __global__ void pairs_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_
     }
 }
 
+
+// --- warp-cooperative leaf-pair finder ---------------------------------------------
+// One warp per i-leaf.  The warp pops up to 32 tree nodes at a time from a
+// shared-memory stack, tests them in parallel (FP32, with margin, against the
+// larger of the gravity cut and the hydro cut bound), pushes the children of
+// the survivors and collects surviving leaves.  The candidates are sorted,
+// tested exactly (FP64 per periodic image, leaf_images) for both lists, and
+// the leaf's images are written with one atomic reservation per list, so each
+// leaf's lists stay in ascending j-leaf order.
+constexpr int kTravWarps = 4;
+constexpr int kStackCap = 512;
+constexpr int kCandCap = 1024;
+
+struct PairOut {
+    int32_t *start[4];  // gravity images, gravity pairs, hydro images, hydro pairs
+    int32_t *count[4];
+    crk_image *gimg, *himg;
+    int32_t *gpair, *hpair;
+    int64_t cap[4];
+    unsigned long long *cursor;  // [4]
+    int32_t *err;                // [0] traversal overflow, [1] output overflow
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(CRK_FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(CRK_FULL_MASK, x, 31);
+    return x - v;
+}
+
+template <bool kBrute>
+__global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
+    int64_t n_leaves, const int32_t *__restrict__ leaf_start, const int32_t *__restrict__ leaf_ngas,
+    const float *__restrict__ bbox, const float *__restrict__ hmax, TreeDev tree, double L, double rc, PairOut o) {
+    __shared__ int32_t stack[kTravWarps][kStackCap];
+    __shared__ int32_t cand[kTravWarps][kCandCap];
+    __shared__ int32_t sorted[kTravWarps][kCandCap];
+    __shared__ uint8_t ng[kTravWarps][kCandCap], nh[kTravWarps][kCandCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t a = (int64_t)blockIdx.x * kTravWarps + warp;
+    if (a >= n_leaves) return;  // whole warp leaves together; no block barrier below
+    const bool a_any = leaf_start[a + 1] > leaf_start[a];
+    const bool a_gas = leaf_ngas[a] > 0;
+    const float *A = bbox + 6 * a;
+    const float ha = hmax[a];
+    const float Lf = (float)L;
+    int nc = 0;
+    bool bad = false;
+    if (a_any) {
+        if (kBrute) {
+            for (int64_t b0 = 0; b0 < n_leaves; b0 += 32) {
+                int64_t b = b0 + lane;
+                bool keep = false;
+                if (b < n_leaves && leaf_start[b + 1] > leaf_start[b]) {
+                    float cut = fmaxf((float)rc, a_gas && leaf_ngas[b] > 0 ? 2.0f * fmaxf(ha, hmax[b]) : 0.0f);
+                    keep = !clearly_apart(A, bbox + 6 * b, Lf, cut);
+                }
+                unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+                int pos = nc + __popc(m & below);
+                if (keep && pos < kCandCap) cand[warp][pos] = (int32_t)b;
+                nc += __popc(m);
+            }
+        } else {
+            int top = 1;
+            if (lane == 0) stack[warp][0] = tree.root;
+            __syncwarp();
+            while (top > 0) {
+                const int take = top < 32 ? top : 32;
+                const int32_t nd = lane < take ? stack[warp][top - 1 - lane] : -1;
+                top -= take;
+                __syncwarp();
+                bool pass = false;
+                int32_t lf = -1;
+                if (nd >= 0) {
+                    float cut = fmaxf((float)rc, a_gas ? 2.0f * fmaxf(ha, tree.node_hmax[nd]) : 0.0f);
+                    pass = !clearly_apart(A, tree.node_box + 6 * (int64_t)nd, Lf, cut);
+                    lf = tree.node_leaf[nd];
+                }
+                const bool is_leaf = pass && lf >= 0, inner = pass && lf < 0;
+                unsigned m = __ballot_sync(CRK_FULL_MASK, is_leaf);
+                int pos = nc + __popc(m & below);
+                if (is_leaf && pos < kCandCap) cand[warp][pos] = lf;
+                nc += __popc(m);
+                unsigned m2 = __ballot_sync(CRK_FULL_MASK, inner);
+                int sp = top + 2 * __popc(m2 & below);
+                if (inner && sp + 1 < kStackCap) {
+                    stack[warp][sp] = tree.node_right[nd];
+                    stack[warp][sp + 1] = tree.node_left[nd];
+                }
+                top += 2 * __popc(m2);
+                if (top > kStackCap || nc > kCandCap) {
+                    bad = true;
+                    break;
+                }
+                __syncwarp();
+            }
+        }
+        if (nc > kCandCap) bad = true;
+    }
+    __syncwarp();
+    if (bad) {
+        if (lane == 0) atomicAdd(&o.err[0], 1);
+        return;
+    }
+    // ascending j-leaf order (rank sort; leaf ids are unique)
+    for (int t = lane; t < nc; t += 32) {
+        int32_t v = cand[warp][t];
+        int r = 0;
+        for (int u = 0; u < nc; ++u) r += cand[warp][u] < v;
+        sorted[warp][r] = v;
+    }
+    __syncwarp();
+    // exact image counts of both lists
+    const double rc2 = __dmul_rn(rc, rc);
+    for (int t = lane; t < nc; t += 32) {
+        int32_t b = sorted[warp][t];
+        int cg = leaf_images<false>(bbox, a, b, L, rc2, nullptr);
+        int ch = 0;
+        if (a_gas && leaf_ngas[b] > 0) {
+            double hb = (double)hmax[b], hA = (double)ha;
+            double cut = __dmul_rn(2.0, hA > hb ? hA : hb);
+            ch = leaf_images<false>(bbox, a, b, L, __dmul_rn(cut, cut), nullptr);
+        }
+        ng[warp][t] = (uint8_t)cg;
+        nh[warp][t] = (uint8_t)ch;
+    }
+    __syncwarp();
+    int tot[4] = {0, 0, 0, 0};
+    for (int t0 = 0; t0 < nc; t0 += 32) {
+        int t = t0 + lane;
+        int cg = t < nc ? ng[warp][t] : 0, ch = t < nc ? nh[warp][t] : 0;
+        int v[4] = {cg, cg > 0, ch, ch > 0};
+        for (int k = 0; k < 4; ++k) {
+            int s;
+            warp_excl_scan(v[k], lane, s);
+            tot[k] += s;
+        }
+    }
+    unsigned long long base[4] = {0, 0, 0, 0};
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) base[k] = tot[k] ? atomicAdd(&o.cursor[k], (unsigned long long)tot[k]) : 0ull;
+    bool over = false;
+    for (int k = 0; k < 4; ++k) {
+        base[k] = __shfl_sync(CRK_FULL_MASK, base[k], 0);
+        over |= base[k] + (unsigned long long)tot[k] > (unsigned long long)o.cap[k];
+    }
+    if (over) {
+        if (lane == 0) atomicAdd(&o.err[1], 1);
+        return;
+    }
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) {
+            o.start[k][a] = (int32_t)base[k];
+            o.count[k][a] = tot[k];
+        }
+    int run[4] = {0, 0, 0, 0};
+    for (int t0 = 0; t0 < nc; t0 += 32) {
+        int t = t0 + lane;
+        int cg = t < nc ? ng[warp][t] : 0, ch = t < nc ? nh[warp][t] : 0;
+        int v[4] = {cg, cg > 0, ch, ch > 0};
+        int off[4];
+        for (int k = 0; k < 4; ++k) {
+            int s;
+            off[k] = run[k] + warp_excl_scan(v[k], lane, s);
+            run[k] += s;
+        }
+        if (t < nc) {
+            int32_t b = sorted[warp][t];
+            if (cg > 0) {
+                o.gpair[base[1] + off[1]] = b;
+                leaf_images<true>(bbox, a, b, L, rc2, o.gimg + base[0] + off[0]);
+            }
+            if (ch > 0) {
+                double hb = (double)hmax[b], hA = (double)ha;
+                double cut = __dmul_rn(2.0, hA > hb ? hA : hb);
+                o.hpair[base[3] + off[3]] = b;
+                leaf_images<true>(bbox, a, b, L, __dmul_rn(cut, cut), o.himg + base[2] + off[2]);
+            }
+        }
+    }
+}
+
 __global__ void leaf_box_to_node_kernel(int64_t n_leaves, const float *__restrict__ bbox,
-                                        const int32_t *__restrict__ leaf_node, float *__restrict__ node_box) {
+                                        const float *__restrict__ hmax, const int32_t *__restrict__ leaf_node,
+                                        float *__restrict__ node_box, float *__restrict__ node_hmax) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n_leaves) return;
-    for (int q = 0; q < 6; ++q) node_box[6 * (int64_t)leaf_node[a] + q] = bbox[6 * a + q];
+    int64_t nd = leaf_node[a];
+    for (int q = 0; q < 6; ++q) node_box[6 * nd + q] = bbox[6 * a + q];
+    node_hmax[nd] = hmax[a];
+}
+
+// one level of split nodes, deepest level first: node h_max = max of the children
+__global__ void node_hmax_kernel(int nseg, LevelDev lv, const int32_t *__restrict__ left,
+                                 const int32_t *__restrict__ right, float *__restrict__ node_hmax) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg || lv.k[s] <= 0) return;
+    int nd = lv.node[s];
+    node_hmax[nd] = fmaxf(node_hmax[left[nd]], node_hmax[right[nd]]);
 }
 
 struct HostSeg {
@@ -368,11 +608,131 @@ struct HostSeg {
 }  // namespace
 
 // ---------------------------------------------------------------------------------
-static int upload(crk_ctx *ctx, void *dst, const void *src, size_t bytes) {
-    if (bytes == 0) return CRK_OK;
-    CRK_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+void crk_rcb_shape_free(crk_ctx *ctx) {
+    if (!ctx || !ctx->rcb) return;
+    crk_rcb_shape *r = ctx->rcb;
+    cudaFree(r->dtab);
+    cudaFree(r->leaf_start);
+    cudaFree(r->left);
+    cudaFree(r->right);
+    cudaFree(r->leaf_of);
+    cudaFree(r->leaf_node);
+    delete r;
+    ctx->rcb = nullptr;
+}
+
+// The RCB tree shape for (n, max_leaf): level segment tables, leaf starts, children.
+static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out) {
+    if (ctx->rcb && ctx->rcb->n == n && ctx->rcb->max_leaf == ml) {
+        *out = ctx->rcb;
+        return CRK_OK;
+    }
+    CRK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the old shape may still be in use
+    crk_rcb_shape_free(ctx);
+    crk_rcb_shape *r = new crk_rcb_shape();
+    r->n = n;
+    r->max_leaf = ml;
+    std::vector<std::vector<HostSeg>> levels;
+    std::vector<HostSeg> cur;
+    std::vector<int32_t> left(1, -1), right(1, -1);
+    int32_t next_node = 0;
+    if (n > 0) cur.push_back({0, (int32_t)n, 0, 0, next_node++});
+    while (!cur.empty()) {
+        bool any = false;
+        for (auto &sg : cur)
+            if (sg.hi - sg.lo > ml) {
+                sg.k = (sg.hi - sg.lo) / 2;
+                any = true;
+            }
+        if (!any) break;
+        std::vector<HostSeg> nxt;
+        nxt.reserve(cur.size() * 2);
+        for (auto &sg : cur) {
+            sg.child = (int32_t)nxt.size();
+            if (sg.k > 0) {
+                int32_t l = next_node++, rr = next_node++;
+                left.resize(next_node, -1);
+                right.resize(next_node, -1);
+                left[sg.node] = l;
+                right[sg.node] = rr;
+                nxt.push_back({sg.lo, sg.lo + sg.k, 0, 0, l});
+                nxt.push_back({sg.lo + sg.k, sg.hi, 0, 0, rr});
+            } else {
+                nxt.push_back({sg.lo, sg.hi, 0, 0, sg.node});
+            }
+        }
+        levels.push_back(cur);
+        cur.swap(nxt);
+    }
+    const int64_t nl = (int64_t)cur.size();
+    r->n_leaves = nl;
+    r->n_nodes = next_node;
+    std::vector<int32_t> leaf_start(nl + 1), leaf_of(next_node > 0 ? next_node : 1, -1), leaf_node(nl > 0 ? nl : 1);
+    for (int64_t a = 0; a < nl; ++a) {
+        leaf_start[a] = cur[a].lo;
+        leaf_of[cur[a].node] = (int32_t)a;
+        leaf_node[a] = cur[a].node;
+        r->max_leaf_size = std::max(r->max_leaf_size, cur[a].hi - cur[a].lo);
+    }
+    leaf_start[nl] = (int32_t)n;
+    size_t tot = 0;
+    for (auto &L : levels) {
+        r->level_off.push_back(tot);
+        r->level_size.push_back(L.size());
+        tot += 6 * L.size();
+    }
+    std::vector<int32_t> packed(tot > 0 ? tot : 1);
+    for (size_t d = 0; d < levels.size(); ++d) {
+        const auto &L = levels[d];
+        size_t m = L.size(), off = r->level_off[d];
+        for (size_t q = 0; q < m; ++q) {
+            packed[off + q] = L[q].lo;
+            packed[off + m + q] = L[q].hi;
+            packed[off + 2 * m + q] = L[q].k;
+            packed[off + 3 * m + q] = L[q].child;
+            packed[off + 4 * m + q] = L[q].node;
+            packed[off + 5 * m + q] = 0;
+        }
+    }
+    auto dev = [&](int32_t **p, const std::vector<int32_t> &v) -> int {
+        if (cudaMalloc(p, sizeof(int32_t) * (v.size() > 0 ? v.size() : 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return CRK_ENOMEM;
+        }
+        return cudaMemcpy(*p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess
+                   ? CRK_OK
+                   : CRK_ECUDA;
+    };
+    int rc = CRK_OK;
+    if (!rc) rc = dev(&r->dtab, packed);
+    if (!rc) rc = dev(&r->leaf_start, leaf_start);
+    if (!rc) rc = dev(&r->left, left);
+    if (!rc) rc = dev(&r->right, right);
+    if (!rc) rc = dev(&r->leaf_of, leaf_of);
+    if (!rc) rc = dev(&r->leaf_node, leaf_node);
+    ctx->rcb = r;
+    if (rc) {
+        crk_rcb_shape_free(ctx);
+        return crk_fail(ctx, rc, "RCB shape tables");
+    }
+    *out = r;
     return CRK_OK;
 }
+
+namespace {
+struct Tracer {
+    crk_ctx *ctx;
+    std::chrono::steady_clock::time_point t;
+    explicit Tracer(crk_ctx *c) : ctx(c), t(std::chrono::steady_clock::now()) {}
+    void mark(const char *what) {
+        if (!ctx->trace) return;
+        cudaStreamSynchronize(ctx->stream);
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[crk] %-18s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+}  // namespace
 
 int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
                      crk_leaves **out) {
@@ -391,6 +751,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
     if (!(lp->r_cut_grav > 0.0f) || !((double)lp->r_cut_grav < 0.5 * (double)p->box))
         return crk_fail(ctx, CRK_EBOX, "r_cut_grav must be positive and below box/2");
 
+    Tracer tr(ctx);
     crk_leaves *lv = new crk_leaves();
     lv->n = n;
     lv->box = p->box;
@@ -403,28 +764,35 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
         rc = (expr);                       \
         if (rc != CRK_OK) goto fail;       \
     } while (0)
-#define ALLOC(ptr, type, count)                                                          \
-    do {                                                                                 \
+#define ALLOC(ptr, type, count)                                                                      \
+    do {                                                                                             \
         ptr = (type *)crk_leaves_alloc(ctx, lv, sizeof(type) * (size_t)((count) > 0 ? (count) : 1)); \
-        if (!ptr) { rc = crk_fail(ctx, CRK_ENOMEM, "leaf allocation"); goto fail; }      \
+        if (!ptr) {                                                                                  \
+            rc = crk_fail(ctx, CRK_ENOMEM, "leaf allocation");                                       \
+            goto fail;                                                                               \
+        }                                                                                            \
+    } while (0)
+#define KCHECK(what)                                       \
+    do {                                                   \
+        cudaError_t e_ = cudaGetLastError();               \
+        if (e_ != cudaSuccess) {                           \
+            rc = crk_check_cuda(ctx, e_, what);            \
+            goto fail;                                     \
+        }                                                  \
     } while (0)
     {
-        // ---- validation flags
         int32_t *flags = (int32_t *)crk_scratch(ctx, 0, 64);
         if (!flags) { rc = crk_fail(ctx, CRK_ENOMEM, "scratch"); goto fail; }
         if (cudaMemsetAsync(flags, 0, 64, st) != cudaSuccess) { rc = crk_fail(ctx, CRK_ECUDA, "memset"); goto fail; }
         unsigned *hbits = (unsigned *)(flags + 8);
-        if (n > 0)
+        if (n > 0) {
             validate_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, p->species, h, n, p->box, flags, hbits);
-        ctx->launches += n > 0;
-
-        std::vector<int32_t> h_leaf_start;  // host copy of leaf boundaries (RCB known from the shape)
-        int32_t *members = nullptr;         // device: particle ids grouped by leaf
+            ++ctx->launches;
+        }
+        int32_t *members = nullptr;  // particle ids grouped by leaf
         int64_t nl = 0;
-        // tree for traversal (RCB)
-        std::vector<int32_t> n_left, n_right, n_leaf, leaf_node;
-        float *node_box = nullptr;
-        int32_t root = 0;
+        const crk_rcb_shape *shape = nullptr;
+        float *node_box = nullptr, *node_hmax = nullptr;
 
         if (lp->mode == 0) {
             int nc = lp->cells_per_side;
@@ -438,74 +806,39 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
                 rc = crk_fail(ctx, CRK_ECUDA, "memset");
                 goto fail;
             }
-            if (n > 0)
+            if (n > 0) {
                 mesh_keys_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, n, nc, (double)p->box, keys,
                                                                    vals, cnts);
-            ctx->launches += n > 0;
+                ++ctx->launches;
+            }
             int bits = 1;
             while ((1LL << bits) < nl) ++bits;
             TRY(crk_radix_sort_u32(ctx, keys, vals, n, bits));
             TRY(crk_exclusive_scan_i32(ctx, cnts, lv->leaf_start, nl + 1, nullptr));
             members = vals;
         } else {
-            // host: tree shape from n alone
-            const int ml = lp->max_leaf;
-            std::vector<std::vector<HostSeg>> levels;
-            std::vector<HostSeg> cur;
-            int32_t next_node = 0;
-            if (n > 0) cur.push_back({0, (int32_t)n, 0, 0, next_node++});
-            n_left.assign(1, -1);
-            n_right.assign(1, -1);
-            bool any = true;
-            while (any && !cur.empty()) {
-                any = false;
-                for (auto &s : cur)
-                    if (s.hi - s.lo > ml) { s.k = (s.hi - s.lo) / 2; any = true; }
-                if (!any) break;
-                std::vector<HostSeg> nxt;
-                nxt.reserve(cur.size() * 2);
-                for (auto &s : cur) {
-                    s.child = (int32_t)nxt.size();
-                    if (s.k > 0) {
-                        int32_t l = next_node++, r = next_node++;
-                        n_left.resize(next_node, -1);
-                        n_right.resize(next_node, -1);
-                        n_left[s.node] = l;
-                        n_right[s.node] = r;
-                        nxt.push_back({s.lo, s.lo + s.k, 0, 0, l});
-                        nxt.push_back({s.lo + s.k, s.hi, 0, 0, r});
-                    } else {
-                        nxt.push_back({s.lo, s.hi, 0, 0, s.node});
-                    }
-                }
-                levels.push_back(cur);
-                cur.swap(nxt);
-            }
-            // cur now lists the leaves in position (= depth-first) order
-            nl = (int64_t)cur.size();
-            n_leaf.assign(next_node, -1);
-            h_leaf_start.resize(nl + 1);
-            leaf_node.resize(nl);
-            for (int64_t a = 0; a < nl; ++a) {
-                h_leaf_start[a] = cur[a].lo;
-                n_leaf[cur[a].node] = (int32_t)a;
-                leaf_node[a] = cur[a].node;
-            }
-            h_leaf_start[nl] = (int32_t)n;
+            TRY(rcb_shape(ctx, n, lp->max_leaf, &shape));
+            nl = shape->n_leaves;
             ALLOC(lv->leaf_start, int32_t, nl + 1);
-            TRY(upload(ctx, lv->leaf_start, h_leaf_start.data(), sizeof(int32_t) * (size_t)(nl + 1)));
-            ALLOC(node_box, float, 6 * (int64_t)next_node);
-            // three presorted lists
-            int32_t *Lc[3], *Ln[3];
-            uint32_t *keys = (uint32_t *)crk_scratch(ctx, 1, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-            for (int a = 0; a < 3; ++a) {
-                Lc[a] = (int32_t *)crk_scratch(ctx, 2 + a, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-                Ln[a] = (int32_t *)crk_scratch(ctx, 5 + a, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+            if (cudaMemcpyAsync(lv->leaf_start, shape->leaf_start, sizeof(int32_t) * (size_t)(nl + 1),
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                rc = crk_fail(ctx, CRK_ECUDA, "leaf starts");
+                goto fail;
             }
-            int32_t *node_of = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-            int32_t *node_nx = (int32_t *)crk_scratch(ctx, 9, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+            ALLOC(node_box, float, 6 * shape->n_nodes);
+            ALLOC(node_hmax, float, shape->n_nodes);
+            tr.mark("shape");
+            int32_t *Lc[3], *Ln[3];
+            size_t nb = sizeof(int32_t) * (size_t)(n > 0 ? n : 1);
+            uint32_t *keys = (uint32_t *)crk_scratch(ctx, 1, nb);
+            for (int a = 0; a < 3; ++a) {
+                Lc[a] = (int32_t *)crk_scratch(ctx, 2 + a, nb);
+                Ln[a] = (int32_t *)crk_scratch(ctx, 5 + a, nb);
+            }
+            int32_t *node_of = (int32_t *)crk_scratch(ctx, 8, nb);
+            int32_t *node_nx = (int32_t *)crk_scratch(ctx, 9, nb);
             uint8_t *side = (uint8_t *)crk_scratch(ctx, 10, (size_t)(n > 0 ? n : 1));
-            int32_t *flag = (int32_t *)crk_scratch(ctx, 11, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+            int32_t *flag = (int32_t *)crk_scratch(ctx, 11, nb);
             if (!keys || !node_of || !node_nx || !side || !flag || !Lc[0] || !Lc[1] || !Lc[2] || !Ln[0] || !Ln[1] ||
                 !Ln[2]) {
                 rc = crk_fail(ctx, CRK_ENOMEM, "scratch");
@@ -517,59 +850,31 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
                 ++ctx->launches;
                 TRY(crk_radix_sort_u32(ctx, keys, Lc[a], n, 32));
             }
+            tr.mark("axis sorts");
             if (n > 0 && cudaMemsetAsync(node_of, 0, sizeof(int32_t) * (size_t)n, st) != cudaSuccess) {
                 rc = crk_fail(ctx, CRK_ECUDA, "memset");
                 goto fail;
             }
-            // device copies of the level tables (one buffer for all levels)
-            size_t tot = 0;
-            for (auto &L : levels) tot += L.size();
-            std::vector<int32_t> packed(6 * (tot > 0 ? tot : 1));
-            int32_t *dtab;
-            ALLOC(dtab, int32_t, 6 * (int64_t)(tot > 0 ? tot : 1));
-            {
-                size_t off = 0;
-                for (auto &L : levels) {
-                    size_t m = L.size();
-                    for (size_t s = 0; s < m; ++s) {
-                        packed[off + s] = L[s].lo;
-                        packed[off + m + s] = L[s].hi;
-                        packed[off + 2 * m + s] = L[s].k;
-                        packed[off + 3 * m + s] = L[s].child;
-                        packed[off + 4 * m + s] = L[s].node;
-                        packed[off + 5 * m + s] = 0;
-                    }
-                    off += 6 * m;
-                }
-                TRY(upload(ctx, dtab, packed.data(), sizeof(int32_t) * 6 * tot));
-            }
-            size_t off = 0;
-            for (auto &L : levels) {
-                int m = (int)L.size();
-                LevelDev d;
-                d.lo = dtab + off;
-                d.hi = dtab + off + m;
-                d.k = dtab + off + 2 * m;
-                d.child = dtab + off + 3 * m;
-                d.node = dtab + off + 4 * m;
-                d.axis = dtab + off + 5 * m;
-                off += 6 * (size_t)m;
-                rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, d, Lc[0], Lc[1], Lc[2], p->x, p->y, p->z,
+            for (size_t d = 0; d < shape->level_size.size(); ++d) {
+                int m = (int)shape->level_size[d];
+                int32_t *tab = shape->dtab + shape->level_off[d];
+                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m};
+                rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, Lc[0], Lc[1], Lc[2], p->x, p->y, p->z,
                                                                   node_box);
-                rcb_side_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, d, node_of, Lc[0], Lc[1], Lc[2], side, node_nx);
-                ctx->launches += 2 + 2 * 3;
+                rcb_side_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side, node_nx);
+                ctx->launches += 2;
                 for (int b = 0; b < 3; ++b) {
-                    rcb_flag_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, d, node_of, Lc[b], side, flag);
+                    rcb_flag_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[b], side, flag);
                     TRY(crk_exclusive_scan_i32(ctx, flag, flag, n, nullptr));
-                    rcb_scatter_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, d, node_of, Lc[b], side, flag, Ln[b]);
+                    rcb_scatter_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[b], side, flag, Ln[b]);
+                    ctx->launches += 2;
                 }
                 for (int b = 0; b < 3; ++b) std::swap(Lc[b], Ln[b]);
                 std::swap(node_of, node_nx);
-                cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) { rc = crk_check_cuda(ctx, e, "rcb level"); goto fail; }
+                KCHECK("rcb level");
             }
+            tr.mark("rcb levels");
             members = Lc[0];
-            root = 0;
         }
         lv->n_leaves = nl;
         ALLOC(lv->perm, int32_t, n);
@@ -578,16 +883,13 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
         ALLOC(lv->bbox, float, 6 * nl);
         ALLOC(lv->hmax, float, nl);
         ALLOC(lv->pos, float4, n);
-        int32_t *err_flag = flags + 4;
-        if (nl > 0)
+        if (nl > 0) {
             leaf_data_kernel<<<(unsigned)nl, 128, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
                                                            p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
-                                                           lv->bbox, lv->hmax, lv->pos, err_flag);
-        ctx->launches += nl > 0;
-        {
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) { rc = crk_check_cuda(ctx, e, "leaf data"); goto fail; }
+                                                           lv->bbox, lv->hmax, lv->pos, flags + 4);
+            ++ctx->launches;
         }
+        KCHECK("leaf data");
         // ---- host checks (one synchronisation)
         int32_t hflags[16];
         if (cudaMemcpyAsync(hflags, flags, 64, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -595,6 +897,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             rc = crk_fail(ctx, CRK_ECUDA, "leaf build: %s", cudaGetErrorString(cudaGetLastError()));
             goto fail;
         }
+        tr.mark("leaf data");
         if (hflags[0] > 0) { rc = crk_fail(ctx, CRK_EBOX, "%d particle positions outside [0, box)", hflags[0]); goto fail; }
         if (hflags[1] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "%d gas particles with h <= 0 or not finite", hflags[1]); goto fail; }
         if (hflags[4] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "a leaf holds more than %d particles", kMaxLeafCap); goto fail; }
@@ -617,92 +920,99 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             lv->max_leaf_size = mx;
             if (mx > kMaxLeafCap) { rc = crk_fail(ctx, CRK_EINVAL, "a chaining-mesh cell holds more than %d particles", kMaxLeafCap); goto fail; }
         } else {
-            int mx = 0;
-            for (int64_t a = 0; a < nl; ++a) mx = std::max(mx, h_leaf_start[a + 1] - h_leaf_start[a]);
-            lv->max_leaf_size = mx;
+            lv->max_leaf_size = shape->max_leaf_size;
         }
-
-        // ---- tree arrays for traversal
+        // ---- tree for traversal (RCB): leaf boxes and h_max into the nodes, then bottom-up h_max
         TreeDev tree{};
-        int brute = lp->mode == 0 ? 1 : 0;
+        const int brute = lp->mode == 0 ? 1 : 0;
         if (!brute && nl > 0) {
-            int32_t *dl, *dr, *dlf, *dln;
-            int64_t nn = (int64_t)n_left.size();
-            ALLOC(dl, int32_t, nn);
-            ALLOC(dr, int32_t, nn);
-            ALLOC(dlf, int32_t, nn);
-            ALLOC(dln, int32_t, nl);
-            TRY(upload(ctx, dl, n_left.data(), sizeof(int32_t) * nn));
-            TRY(upload(ctx, dr, n_right.data(), sizeof(int32_t) * nn));
-            TRY(upload(ctx, dlf, n_leaf.data(), sizeof(int32_t) * nn));
-            TRY(upload(ctx, dln, leaf_node.data(), sizeof(int32_t) * nl));
-            leaf_box_to_node_kernel<<<crk_grid(nl, 128), 128, 0, st>>>(nl, lv->bbox, dln, node_box);
+            leaf_box_to_node_kernel<<<crk_grid(nl, 128), 128, 0, st>>>(nl, lv->bbox, lv->hmax, shape->leaf_node,
+                                                                       node_box, node_hmax);
             ++ctx->launches;
+            for (size_t d = shape->level_size.size(); d-- > 0;) {
+                int m = (int)shape->level_size[d];
+                int32_t *tab = shape->dtab + shape->level_off[d];
+                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m};
+                node_hmax_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, shape->left, shape->right, node_hmax);
+                ++ctx->launches;
+            }
+            KCHECK("node h_max");
             tree.node_box = node_box;
-            tree.node_left = dl;
-            tree.node_right = dr;
-            tree.node_leaf = dlf;
-            tree.root = root;
+            tree.node_hmax = node_hmax;
+            tree.node_left = shape->left;
+            tree.node_right = shape->right;
+            tree.node_leaf = shape->leaf_of;
+            tree.root = 0;
         }
-        // ---- image lists: count, scan, fill (gravity then hydro)
-        for (int hyd = 0; hyd < 2; ++hyd) {
-            int32_t *icnt = (int32_t *)crk_scratch(ctx, 1, sizeof(int32_t) * (size_t)(nl + 1));
-            int32_t *pcnt = (int32_t *)crk_scratch(ctx, 2, sizeof(int32_t) * (size_t)(nl + 1));
-            int32_t *tot2 = (int32_t *)crk_scratch(ctx, 3, 64);
-            if (!icnt || !pcnt || !tot2) { rc = crk_fail(ctx, CRK_ENOMEM, "scratch"); goto fail; }
-            int32_t *iptr, *pptr;
-            ALLOC(iptr, int32_t, nl + 1);
-            ALLOC(pptr, int32_t, nl + 1);
-            if (nl > 0)
-                pairs_kernel<false><<<crk_grid(nl, 128), 128, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, lv->bbox,
-                                                                     lv->hmax, tree, brute, hyd, (double)p->box,
-                                                                     (double)lp->r_cut_grav, (double)hmax_all, icnt,
-                                                                     pcnt, nullptr, nullptr, nullptr, nullptr);
-            else {
-                if (cudaMemsetAsync(icnt, 0, sizeof(int32_t), st) != cudaSuccess) { rc = crk_fail(ctx, CRK_ECUDA, "memset"); goto fail; }
-                if (cudaMemsetAsync(pcnt, 0, sizeof(int32_t), st) != cudaSuccess) { rc = crk_fail(ctx, CRK_ECUDA, "memset"); goto fail; }
-            }
-            ctx->launches += nl > 0;
-            TRY(crk_exclusive_scan_i32(ctx, icnt, iptr, nl + 1, tot2));
-            TRY(crk_exclusive_scan_i32(ctx, pcnt, pptr, nl + 1, tot2 + 1));
-            int32_t tots[2];
-            if (cudaMemcpyAsync(tots, tot2, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess) {
-                rc = crk_fail(ctx, CRK_ECUDA, "pair counts: %s", cudaGetErrorString(cudaGetLastError()));
-                goto fail;
-            }
-            // scan of nl+1 entries where the last count is garbage: recompute totals from ptr[nl]
-            int32_t ni = 0, np = 0;
-            if (nl > 0) {
-                if (cudaMemcpy(&ni, iptr + nl, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-                    cudaMemcpy(&np, pptr + nl, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
-                    rc = crk_fail(ctx, CRK_ECUDA, "pair totals");
+        // ---- leaf-pair image lists, one warp per leaf; retried once with exact
+        // capacities if the first estimate is too small
+        {
+            int32_t *se[8];
+            for (int q = 0; q < 8; ++q) ALLOC(se[q], int32_t, nl);
+            unsigned long long *cur = (unsigned long long *)crk_scratch(ctx, 3, 64);
+            if (!cur) { rc = crk_fail(ctx, CRK_ENOMEM, "scratch"); goto fail; }
+            int64_t cap[4] = {48 * nl + 64, 32 * nl + 64, 48 * nl + 64, 32 * nl + 64};
+            crk_image *gimg = nullptr, *himg = nullptr;
+            int32_t *gpair = nullptr, *hpair = nullptr;
+            unsigned long long hcur[6];
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                // capacity blocks come from the leaves' own allocations; a retry leaves the
+                // first (too small) blocks unused until the leaves are freed
+                ALLOC(gimg, crk_image, cap[0]);
+                ALLOC(gpair, int32_t, cap[1]);
+                ALLOC(himg, crk_image, cap[2]);
+                ALLOC(hpair, int32_t, cap[3]);
+                if (cudaMemsetAsync(cur, 0, 64, st) != cudaSuccess) { rc = crk_fail(ctx, CRK_ECUDA, "memset"); goto fail; }
+                PairOut po;
+                for (int k = 0; k < 4; ++k) {
+                    po.start[k] = se[2 * k];
+                    po.count[k] = se[2 * k + 1];
+                    po.cap[k] = cap[k];
+                }
+                po.gimg = gimg; po.gpair = gpair; po.himg = himg; po.hpair = hpair;
+                po.cursor = cur;
+                po.err = (int32_t *)(cur + 4);
+                if (nl > 0) {
+                    unsigned grid = (unsigned)((nl + kTravWarps - 1) / kTravWarps);
+                    if (brute)
+                        leaf_pairs_warp_kernel<true><<<grid, kTravWarps * 32, 0, st>>>(
+                            nl, lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, tree, (double)p->box,
+                            (double)lp->r_cut_grav, po);
+                    else
+                        leaf_pairs_warp_kernel<false><<<grid, kTravWarps * 32, 0, st>>>(
+                            nl, lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, tree, (double)p->box,
+                            (double)lp->r_cut_grav, po);
+                    ++ctx->launches;
+                }
+                KCHECK("pair lists");
+                if (cudaMemcpyAsync(hcur, cur, 48, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess) {
+                    rc = crk_fail(ctx, CRK_ECUDA, "pair lists: %s", cudaGetErrorString(cudaGetLastError()));
                     goto fail;
                 }
+                const int32_t *herr = (const int32_t *)(hcur + 4);
+                if (herr[0] > 0) {
+                    rc = crk_fail(ctx, CRK_EINVAL,
+                                  "%d leaves have more than %d candidate leaves within the cut (leaves too small "
+                                  "for r_cut or h)", herr[0], kCandCap);
+                    goto fail;
+                }
+                if (herr[1] == 0) break;
+                for (int k = 0; k < 4; ++k) cap[k] = (int64_t)hcur[k] + 64;
+                if (attempt == 1) { rc = crk_fail(ctx, CRK_ESTATE, "pair list capacity"); goto fail; }
             }
-            crk_image *img;
-            int32_t *plist;
-            ALLOC(img, crk_image, ni);
-            ALLOC(plist, int32_t, np);
-            if (nl > 0)
-                pairs_kernel<true><<<crk_grid(nl, 128), 128, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, lv->bbox,
-                                                                    lv->hmax, tree, brute, hyd, (double)p->box,
-                                                                    (double)lp->r_cut_grav, (double)hmax_all, nullptr,
-                                                                    nullptr, iptr, img, pptr, plist);
-            ctx->launches += nl > 0;
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) { rc = crk_check_cuda(ctx, e, "pair lists"); goto fail; }
-            if (hyd == 0) {
-                lv->gimg_ptr = iptr; lv->gimg = img; lv->n_gimg = ni;
-                lv->gpair_ptr = pptr; lv->gpair_list = plist; lv->n_gpairs = np;
-            } else {
-                lv->himg_ptr = iptr; lv->himg = img; lv->n_himg = ni;
-                lv->hpair_ptr = pptr; lv->hpair_list = plist; lv->n_hpairs = np;
-            }
+            lv->gimg_start = se[0]; lv->gimg_cnt = se[1]; lv->gimg = gimg; lv->n_gimg = (int64_t)hcur[0];
+            lv->gpair_start = se[2]; lv->gpair_cnt = se[3]; lv->gpair_list = gpair; lv->n_gpairs = (int64_t)hcur[1];
+            lv->himg_start = se[4]; lv->himg_cnt = se[5]; lv->himg = himg; lv->n_himg = (int64_t)hcur[2];
+            lv->hpair_start = se[6]; lv->hpair_cnt = se[7]; lv->hpair_list = hpair; lv->n_hpairs = (int64_t)hcur[3];
         }
+        tr.mark("pair lists");
+        TRY(crk_build_gas_lists(ctx, lv));
+        tr.mark("gas lists");
     }
 #undef TRY
 #undef ALLOC
+#undef KCHECK
     *out = lv;
     return CRK_OK;
 fail:
@@ -726,24 +1036,39 @@ int crk_leaves_export(crk_ctx *ctx, const crk_leaves *lv, int32_t *perm, int32_t
     if (!ctx) return CRK_EINVAL;
     if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
     CRK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t n = lv->n, nl = lv->n_leaves;
+    if (perm && n) CRK_CUDA(ctx, cudaMemcpy(perm, lv->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (leaf_start) CRK_CUDA(ctx, cudaMemcpy(leaf_start, lv->leaf_start, sizeof(int32_t) * (nl + 1), cudaMemcpyDeviceToHost));
     struct {
-        void *dst;
-        const void *src;
-        size_t bytes;
-    } cp[6] = {{perm, lv->perm, sizeof(int32_t) * (size_t)lv->n},
-               {leaf_start, lv->leaf_start, sizeof(int32_t) * (size_t)(lv->n_leaves + 1)},
-               {grav_ptr, lv->gpair_ptr, sizeof(int32_t) * (size_t)(lv->n_leaves + 1)},
-               {grav_list, lv->gpair_list, sizeof(int32_t) * (size_t)lv->n_gpairs},
-               {hydro_ptr, lv->hpair_ptr, sizeof(int32_t) * (size_t)(lv->n_leaves + 1)},
-               {hydro_list, lv->hpair_list, sizeof(int32_t) * (size_t)lv->n_hpairs}};
-    for (auto &c : cp)
-        if (c.dst && c.bytes && c.src) CRK_CUDA(ctx, cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost));
+        int32_t *ptr, *list;
+        const int32_t *start, *cnt, *data;
+        int64_t total;
+    } L[2] = {{grav_ptr, grav_list, lv->gpair_start, lv->gpair_cnt, lv->gpair_list, lv->n_gpairs},
+              {hydro_ptr, hydro_list, lv->hpair_start, lv->hpair_cnt, lv->hpair_list, lv->n_hpairs}};
+    for (auto &l : L) {
+        if (!l.ptr && !l.list) continue;
+        std::vector<int32_t> st(nl), ct(nl), data(l.total);
+        if (nl) {
+            CRK_CUDA(ctx, cudaMemcpy(st.data(), l.start, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost));
+            CRK_CUDA(ctx, cudaMemcpy(ct.data(), l.cnt, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost));
+        }
+        if (l.total) CRK_CUDA(ctx, cudaMemcpy(data.data(), l.data, sizeof(int32_t) * l.total, cudaMemcpyDeviceToHost));
+        int64_t k = 0;
+        for (int64_t a = 0; a < nl; ++a) {
+            if (l.ptr) l.ptr[a] = (int32_t)k;
+            for (int32_t q = 0; q < ct[a]; ++q, ++k)
+                if (l.list) l.list[k] = data[st[a] + q];
+        }
+        if (l.ptr) l.ptr[nl] = (int32_t)k;
+    }
     return CRK_OK;
 }
 
 void crk_leaves_free(crk_ctx *ctx, crk_leaves *lv) {
-    (void)ctx;
     if (!lv) return;
-    for (void *q : lv->allocs) cudaFree(q);
+    for (auto &b : lv->allocs) {
+        if (ctx && ctx->block_cache.size() < 256) ctx->block_cache.push_back(b);
+        else cudaFree(b.first);
+    }
     delete lv;
 }

@@ -30,7 +30,8 @@ struct LeafView {
     const float *hmax;
     const float4 *pos;
     const int32_t *kperm;
-    const int32_t *img_ptr;
+    const int32_t *img_start;
+    const int32_t *img_cnt;
     const crk_image *img;
     int64_t n_leaves;
 };
@@ -80,6 +81,7 @@ struct GravP {
 
 struct GravStage {
     static constexpr bool kGasOnly = false;
+    static constexpr bool kTag = false;
     using P = GravP;
     struct Rec {
         float x, y, z, m;
@@ -93,7 +95,7 @@ struct GravStage {
     __device__ static float box_cut(const P &p, float, const Rec &) { return sqrtf(p.rc2); }
     __device__ static float leaf_cut(const P &p, float, float) { return sqrtf(p.rc2); }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &) { s.ax = s.ay = s.az = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.ax = s.ay = s.az = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
         float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
@@ -108,7 +110,7 @@ struct GravStage {
         s.az = fmaf(f, dz, s.az);
         if (kCount) s.cnt += in;
     }
-    __device__ static void finish(const P &p, I &s, const Rec &, int32_t orig) {
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t orig, int64_t) {
         p.a3[orig] = s.ax;
         p.a3[p.n + orig] = s.ay;
         p.a3[2 * p.n + orig] = s.az;
@@ -127,6 +129,7 @@ struct GravAdjP {
 
 struct GravAdjStage {
     static constexpr bool kGasOnly = false;
+    static constexpr bool kTag = false;
     using P = GravAdjP;
     struct __align__(16) Rec {
         float x, y, z, m;
@@ -143,7 +146,7 @@ struct GravAdjStage {
     __device__ static float box_cut(const P &p, float, const Rec &) { return sqrtf(p.rc2); }
     __device__ static float leaf_cut(const P &p, float, float) { return sqrtf(p.rc2); }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &) { s.gx = s.gy = s.gz = s.gm = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.gx = s.gy = s.gz = s.gm = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
         float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;  // d_ij = x_j - x_i
@@ -168,7 +171,7 @@ struct GravAdjStage {
         s.gm = fmaf(-g, fmaf(rj.bx, dx, fmaf(rj.by, dy, rj.bz * dz)), s.gm);
         if (kCount) s.cnt += in;
     }
-    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
         p.gx3[o] = s.gx;
         p.gx3[p.n + o] = s.gy;
         p.gx3[2 * p.n + o] = s.gz;
@@ -187,6 +190,7 @@ struct GeomP {
 struct GeomStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
+    static constexpr bool kTag = false;
     using P = GeomP;
     struct Rec {
         float x, y, z, h;
@@ -199,7 +203,7 @@ struct GeomStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &) { s.s = s.c = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.s = s.c = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
         float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
@@ -211,7 +215,7 @@ struct GeomStage {
         kahan_add(s.s, s.c, in ? W : 0.0f);
         if (kCount) s.cnt += in;
     }
-    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
         float sum = s.s - s.c;
         float V = 1.0f / sum;
         p.V[o] = V;
@@ -233,6 +237,7 @@ struct GeomAdjP {
 struct GeomAdjStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
+    static constexpr bool kTag = false;
     using P = GeomAdjP;
     struct __align__(16) Rec {
         float x, y, z, h;
@@ -250,7 +255,7 @@ struct GeomAdjStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &) { s.gx = s.gy = s.gz = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.gx = s.gy = s.gz = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
         float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;  // x_kj
@@ -265,7 +270,7 @@ struct GeomAdjStage {
         s.gz = fmaf(k, dz, s.gz);
         if (kCount) s.cnt += in;
     }
-    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
         p.gx3[o] = s.gx;
         p.gx3[p.n + o] = s.gy;
         p.gx3[2 * p.n + o] = s.gz;
@@ -290,6 +295,7 @@ struct CorrP {
 struct CorrStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
+    static constexpr bool kTag = false;
     using P = CorrP;
     struct __align__(16) Rec {
         float x, y, z, h;
@@ -308,7 +314,7 @@ struct CorrStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &) {
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) {
         s.m0 = s.c0 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) s.m1[a] = s.c1[a] = s.dm0[a] = 0.f;
@@ -355,7 +361,7 @@ struct CorrStage {
         }
         if (kCount) s.cnt += in;
     }
-    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o) {
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
         double m0 = (double)s.m0 - (double)s.c0;
         double m1[3], M[3][3];
         for (int a = 0; a < 3; ++a) m1[a] = (double)s.m1[a] - (double)s.c1[a];
@@ -432,6 +438,7 @@ struct HydroP {
 struct HydroStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = true;
+    static constexpr bool kTag = false;
     using P = HydroP;
     struct __align__(16) Rec {
         float x, y, z, h;
@@ -467,7 +474,7 @@ struct HydroStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &) { s.fx = s.fy = s.fz = s.e = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.fx = s.fy = s.fz = s.e = 0.f; s.cnt = 0; }
     // grad W^R of record r at separation x (x = x_r - x_other): gA (1 + B.x) W + A (gB.x + B) W + A (1 + B.x) dWr x
     __device__ static void grad_wr(const Rec &r, const float x[3], float W, float dWr, float g[3]) {
         float Bx = fmaf(r.B[0], x[0], fmaf(r.B[1], x[1], r.B[2] * x[2]));
@@ -507,7 +514,7 @@ struct HydroStage {
         s.e = fmaf(-0.5f, fmaf(vij[0], f[0], fmaf(vij[1], f[1], vij[2] * f[2])), s.e);
         if (kCount) s.cnt += in;
     }
-    __device__ static void finish(const P &p, I &s, const Rec &ri, int32_t o) {
+    __device__ static void finish(const P &p, I &s, const Rec &ri, int32_t o, int64_t) {
         float mi = p.m[o];
         float dvx = s.fx / mi, dvy = s.fy / mi, dvz = s.fz / mi, du = s.e / mi;
         p.dv3[o] = dvx;
@@ -533,6 +540,59 @@ struct HydroStage {
     }
 };
 
+
+// Builds the exact gas neighbour lists (count pass, then fill pass).
+struct ListP {
+    uint32_t *list;
+    const int32_t *gstart, *goff;
+    int32_t *cnt;
+    int fill;
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct ListStage {
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    static constexpr bool kTag = true;
+    using P = ListP;
+    struct __align__(16) Rec {
+        float x, y, z, h;
+        uint32_t code, pad0, pad1, pad2;
+    };
+    struct I {
+        uint32_t *out;
+        int c;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &, int32_t, float4 ps) { return {ps.x, ps.y, ps.z, ps.w, 0u, 0u, 0u, 0u}; }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void tag(Rec &r, int img_local, int j_local) {
+        r.code = ((uint32_t)img_local << 10) | (uint32_t)j_local;
+    }
+    __device__ static void init(const P &p, I &s, const Rec &, int64_t a, int q, int lane) {
+        s.c = 0;
+        s.cnt = 0;
+        s.out = p.fill ? p.list + (size_t)p.goff[p.gstart[a] + q] * 32 + lane : nullptr;
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float hs = ri.h + rj.h;
+        if (r2 < hs * hs) {
+            if (s.out) s.out[(size_t)s.c * 32] = rj.code;
+            ++s.c;
+        }
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t, int64_t i) {
+        if (!p.fill) p.cnt[i] = s.c;
+    }
+    __device__ static void finish_other(const P &, int32_t) {}
+};
+
 // --------------------------------------------------------------- framework
 template <class S>
 __global__ void gather_kernel(int64_t n, const float4 *__restrict__ pos, const int32_t *__restrict__ kperm,
@@ -555,13 +615,13 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
     for (int64_t a = blockIdx.x; a < lv.n_leaves; a += gridDim.x) {
         const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
-        const int ib = lv.img_ptr[a], ie = lv.img_ptr[a + 1];
+        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
         for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
             const int i = g0 + lane;
             const bool act = i < hi;
             const Rec ri = rec[act ? i : g0];
             typename S::I st;
-            S::init(p, st, ri);
+            S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
             // i-group box and largest h (inactive lanes repeat lane 0's particle)
             float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
             float hm = lv.pos[act ? i : g0].w;
@@ -597,6 +657,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
                     if (jv) {
                         rj = rec[j];
                         S::shift(rj, im.sx, im.sy, im.sz);
+                        if constexpr (S::kTag) S::tag(rj, e - ib, j - jlo);
                         float dx = fmaxf(fmaxf(bl0 - rj.x, rj.x - bh0), 0.f);
                         float dy = fmaxf(fmaxf(bl1 - rj.y, rj.y - bh1), 0.f);
                         float dz = fmaxf(fmaxf(bl2 - rj.z, rj.z - bh2), 0.f);
@@ -617,7 +678,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
             __syncwarp();
             for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[warp][k]);
             __syncwarp();
-            if (act) S::finish(p, st, ri, lv.kperm[i]);
+            if (act) S::finish(p, st, ri, lv.kperm[i], i);
             if constexpr (S::kCons) {
                 double c[4] = {0.0, 0.0, 0.0, 0.0};
                 if (act) S::cons_terms(p, st, ri, lv.kperm[i], c);
@@ -670,8 +731,104 @@ __global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, 
     }
 }
 
+
+// Gas-pair stages driven by the exact neighbour lists: each lane walks its own
+// list (k-major, so entry k of the 32 lanes is one coalesced row); inactive
+// lanes (k beyond their length) idle.
+struct GasLists {
+    const int32_t *gstart, *goff, *cnt;
+    const uint32_t *list;
+};
+
+template <class S, bool kCount>
+__global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S::P p,
+                                                        const typename S::Rec *__restrict__ rec, GasLists gl,
+                                                        double *__restrict__ cons_part) {
+    using Rec = typename S::Rec;
+    __shared__ double cons_sh[kWarps][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t a = blockIdx.x; a < lv.n_leaves; a += gridDim.x) {
+        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
+        const int hi = lo + lv.leaf_ngas[a];
+        const crk_image *imgs = lv.img + lv.img_start[a];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
+            const int q = (g0 - lo) >> 5;
+            const int64_t grp = gl.gstart[a] + q;
+            const uint32_t *L = gl.list + (size_t)gl.goff[grp] * 32 + lane;
+            const int i = g0 + lane;
+            const bool act = i < hi;
+            const Rec ri = rec[act ? i : g0];
+            typename S::I st;
+            S::init(p, st, ri, a, q, lane);
+            const int c = act ? gl.cnt[i] : 0;
+            for (int k = 0; k < c; ++k) {
+                const uint32_t code = __ldg(L + (size_t)k * 32);
+                const crk_image im = imgs[code >> 10];
+                Rec rj = rec[lv.leaf_start[im.b] + (int)(code & 1023u)];
+                S::shift(rj, im.sx, im.sy, im.sz);
+                S::template interact<kCount>(p, st, ri, rj);
+            }
+            if (act) S::finish(p, st, ri, lv.kperm[i], i);
+            if constexpr (S::kCons) {
+                double cc[4] = {0.0, 0.0, 0.0, 0.0};
+                if (act) S::cons_terms(p, st, ri, lv.kperm[i], cc);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cc[k] += __shfl_xor_sync(CRK_FULL_MASK, cc[k], o);
+                    cons_acc[k] += cc[k];
+                }
+            }
+            if (kCount) {
+                int cn = act ? st.cnt - 1 : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+                if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+            }
+        }
+        for (int t = hi + threadIdx.x; t < end; t += kThreads) S::finish_other(p, lv.kperm[t]);
+    }
+    if constexpr (S::kCons) {
+        if (cons_part) {
+            if (lane == 0)
+                for (int k = 0; k < 4; ++k) cons_sh[warp][k] = cons_acc[k];
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 4; ++k) {
+                    double t = 0.0;
+                    for (int w = 0; w < kWarps; ++w) t += cons_sh[w][k];
+                    cons_part[4 * (int64_t)blockIdx.x + k] = t;
+                }
+        }
+    }
+}
+
+__global__ void list_group_count_kernel(int64_t n_leaves, const int32_t *__restrict__ ngas, int32_t *__restrict__ ng) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n_leaves) ng[a] = (ngas[a] + 31) >> 5;
+}
+
+// per group: the longest list of its lanes (units of 32 entries once scanned)
+__global__ void list_group_k_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
+                                    const int32_t *__restrict__ ngas, const int32_t *__restrict__ gstart,
+                                    const int32_t *__restrict__ cnt, int32_t *__restrict__ gk) {
+    int64_t a = blockIdx.x;
+    if (a >= n_leaves) return;
+    const int lo = leaf_start[a], hi = lo + ngas[a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int g0 = lo + warp * 32; g0 < hi; g0 += (blockDim.x >> 5) * 32) {
+        int i = g0 + lane;
+        int c = i < hi ? cnt[i] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(CRK_FULL_MASK, c, o));
+        if (lane == 0) gk[gstart[a] + ((g0 - lo) >> 5)] = c;
+    }
+}
+
 template <class S>
-int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pairs, double *cons = nullptr) {
+int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pairs, int kernel_id,
+              double *cons = nullptr) {
     if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
     const int64_t n = lv->n;
     if (n == 0) return CRK_OK;
@@ -688,9 +845,17 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     }
     gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
-               gas_pairs ? lv->himg_ptr : lv->gimg_ptr, gas_pairs ? lv->himg : lv->gimg, lv->n_leaves};
-    if (p.count) {
-        CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
+               gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
+               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves};
+    if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
+    const bool lists = gas_pairs && lv->gl_list && ctx->variant[kernel_id] == CRK_VARIANT_LISTS;
+    if (lists) {
+        GasLists gl{lv->gl_gstart, lv->gl_goff, lv->gl_cnt, lv->gl_list};
+        if (p.count)
+            list_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
+        else
+            list_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
+    } else if (p.count) {
         pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
     } else {
         pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
@@ -717,7 +882,7 @@ int grav_short(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, co
     for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
     p.n = lv->n;
     p.count = (unsigned long long *)pair_count;
-    return run_stage<GravStage>(ctx, lv, p, false);
+    return run_stage<GravStage>(ctx, lv, p, false, CRK_K_GRAVITY);
 }
 
 int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m,
@@ -736,7 +901,7 @@ int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
     p.n = lv->n;
     p.count = nullptr;
-    return run_stage<GravAdjStage>(ctx, lv, p, false);
+    return run_stage<GravAdjStage>(ctx, lv, p, false, CRK_K_GRAVITY_ADJOINT);
 }
 
 int crk_geometry(crk_ctx *ctx, const crk_leaves *lv, const float *m, float *V, float *rho, int64_t *pair_count) {
@@ -744,7 +909,7 @@ int crk_geometry(crk_ctx *ctx, const crk_leaves *lv, const float *m, float *V, f
     if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
     if (lv->n > 0 && (!m || !V || !rho)) return crk_fail(ctx, CRK_EINVAL, "null array");
     GeomP p{m, V, rho, lv->n, (unsigned long long *)pair_count};
-    return run_stage<GeomStage>(ctx, lv, p, true);
+    return run_stage<GeomStage>(ctx, lv, p, true, CRK_K_GEOMETRY);
 }
 
 int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *V, const float *rhobar,
@@ -753,7 +918,7 @@ int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, con
     if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
     if (lv->n > 0 && (!m || !V || !rhobar || !gx3 || !gm)) return crk_fail(ctx, CRK_EINVAL, "null array");
     GeomAdjP p{m, V, rhobar, Vbar, gx3, gm, lv->n, nullptr};
-    return run_stage<GeomAdjStage>(ctx, lv, p, true);
+    return run_stage<GeomAdjStage>(ctx, lv, p, true, CRK_K_GEOMETRY_ADJOINT);
 }
 
 int crk_corrections(crk_ctx *ctx, const crk_leaves *lv, const float *V, float *A, float *B, float *gradA,
@@ -763,7 +928,7 @@ int crk_corrections(crk_ctx *ctx, const crk_leaves *lv, const float *V, float *A
     if (lv->n > 0 && (!V || !A || !B || !gradA || !gradB)) return crk_fail(ctx, CRK_EINVAL, "null array");
     if (n_singular) CRK_CUDA(ctx, cudaMemsetAsync(n_singular, 0, sizeof(int32_t), ctx->stream));
     CorrP p{V, A, B, gradA, gradB, n_singular, lv->n, nullptr};
-    return run_stage<CorrStage>(ctx, lv, p, true);
+    return run_stage<CorrStage>(ctx, lv, p, true, CRK_K_CORRECTIONS);
 }
 
 int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
@@ -775,5 +940,58 @@ int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, co
         return crk_fail(ctx, CRK_EINVAL, "null array");
     HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, dvdt3, dudt, conservation,
              hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count};
-    return run_stage<HydroStage>(ctx, lv, p, true, conservation);
+    return run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+}
+
+int crk_build_gas_lists(crk_ctx *ctx, crk_leaves *lv) {
+    const int64_t nl = lv->n_leaves, n = lv->n;
+    if (nl == 0 || n == 0 || lv->n_gas == 0) return CRK_OK;
+    cudaStream_t st = ctx->stream;
+    int32_t *gstart = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(nl + 1));
+    int32_t *cnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)n);
+    int32_t *ng = (int32_t *)crk_scratch(ctx, 6, sizeof(int32_t) * (size_t)(nl + 1));
+    int32_t *tot = (int32_t *)crk_scratch(ctx, 7, 64);
+    if (!gstart || !cnt || !ng || !tot) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
+    CRK_CUDA(ctx, cudaMemsetAsync(ng, 0, sizeof(int32_t) * (size_t)(nl + 1), st));
+    list_group_count_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, lv->leaf_ngas, ng);
+    ++ctx->launches;
+    int rc = crk_exclusive_scan_i32(ctx, ng, gstart, nl + 1, tot);
+    if (rc) return rc;
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm, lv->himg_start, lv->himg_cnt,
+               lv->himg, nl};
+    ListStage::Rec *rec = (ListStage::Rec *)crk_scratch(ctx, 4, sizeof(ListStage::Rec) * (size_t)n);
+    if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
+    gather_kernel<ListStage><<<crk_grid(n, 256), 256, 0, st>>>(n, lv->pos, lv->kperm, ListP{}, rec);
+    ListP pc{nullptr, gstart, nullptr, cnt, 0, n, nullptr};
+    pair_kernel<ListStage, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pc, rec, nullptr);
+    ctx->launches += 2;
+    CRK_LAUNCH_CHECK(ctx, "neighbour counts");
+    int32_t ngroups = 0;
+    CRK_CUDA(ctx, cudaMemcpyAsync(&ngroups, tot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CRK_CUDA(ctx, cudaStreamSynchronize(st));
+    int32_t *goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+    int32_t *gk = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(ngroups + 1));
+    if (!goff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
+    CRK_CUDA(ctx, cudaMemsetAsync(gk, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
+    list_group_k_kernel<<<(unsigned)nl, kThreads, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, gstart, cnt, gk);
+    ++ctx->launches;
+    rc = crk_exclusive_scan_i32(ctx, gk, goff, ngroups + 1, tot + 1);
+    if (rc) return rc;
+    int32_t rows = 0;
+    CRK_CUDA(ctx, cudaMemcpyAsync(&rows, goff + ngroups, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CRK_CUDA(ctx, cudaStreamSynchronize(st));
+    const int64_t entries = (int64_t)rows * 32;
+    uint32_t *list = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(entries > 0 ? entries : 1));
+    if (!list) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
+    ListP pf{list, gstart, goff, cnt, 1, n, nullptr};
+    pair_kernel<ListStage, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pf, rec, nullptr);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "neighbour lists");
+    lv->gl_gstart = gstart;
+    lv->gl_goff = goff;
+    lv->gl_cnt = cnt;
+    lv->gl_list = list;
+    lv->gl_groups = ngroups;
+    lv->gl_entries = entries;
+    return CRK_OK;
 }

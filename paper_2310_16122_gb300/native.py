@@ -19,6 +19,9 @@ CRK_ECUDA = -3
 CRK_EBOX = -4
 CRK_ESTATE = -5
 CRK_ETIMEOUT = -6
+KERNELS = {"geometry": 0, "corrections": 1, "hydro": 2, "gravity": 3, "gravity_adjoint": 4, "geometry_adjoint": 5}
+VARIANT_LISTS = 0
+VARIANT_TILES = 1
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
                 -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT"}
 
@@ -60,6 +63,9 @@ SIGNATURES = {
     "crk_last_error": [_P],
     "crk_version": [],
     "crk_launch_count": [_P, ctypes.POINTER(_I64)],
+    "crk_set_trace": [_P, _I],
+    "crk_set_variant": [_P, _I, _I],
+    "crk_get_variant": [_P, _I, ctypes.POINTER(_I)],
     "crk_build_leaves": [_P, ctypes.POINTER(crk_particles), _P, ctypes.POINTER(crk_leaf_params), ctypes.POINTER(_P)],
     "crk_leaves_info": [_P, ctypes.POINTER(_I64)],
     "crk_leaves_export": [_P, _P, _P, _P, _P, _P, _P, _P],

@@ -114,6 +114,17 @@ def test_empty_input(api, ctx):
     assert a.numel() == 0 and V.numel() == 0
 
 
+def test_variant_switch(api, ctx):
+    from paper_2310_16122_gb300 import native as N
+
+    assert ctx.get_variant("hydro") == 0 and ctx.get_variant("gravity") == 1
+    with pytest.raises(N.CrkError):
+        ctx.set_variant("gravity", 0)  # gravity has no list variant
+    ctx.set_variant("hydro", 1)
+    assert ctx.get_variant("hydro") == 1
+    ctx.set_variant("hydro", 0)
+
+
 def test_error_statuses(api, ctx):
     from paper_2310_16122_gb300 import native as N
 
@@ -147,12 +158,25 @@ def test_gravity_parity(api, ctx, name):
     assert abs(int(cnt.item()) - npairs) <= boundary_pairs(b, False)
 
 
+GAS_KERNELS = ("geometry", "corrections", "hydro", "geometry_adjoint")
+
+
+def set_gas_variant(ctx, variant):
+    for k in GAS_KERNELS:
+        ctx.set_variant(k, variant)
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
 @pytest.mark.parametrize("name", ["tiny_mesh", "clustered12", "clustered24", "random777_mesh3"])
-def test_hydro_chain_parity(api, ctx, name):
+def test_hydro_chain_parity(api, ctx, name, variant):
     b = box_of(name)
     db = api.DeviceBox(b)
-    out = api.forward(ctx, db, count=True)
-    torch.cuda.synchronize()
+    set_gas_variant(ctx, variant)
+    try:
+        out = api.forward(ctx, db, count=True)
+        torch.cuda.synchronize()
+    finally:
+        set_gas_variant(ctx, 0)
     I = O.from_box(b)
     ref = O.forward(I, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
     gas = b.species == 0
@@ -184,10 +208,12 @@ def test_hydro_chain_parity(api, ctx, name):
     assert int(out["count_geom"].item()) == int(out["count_hydro"].item())
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
 @pytest.mark.parametrize("name", ["clustered12", "clustered24"])
-def test_adjoint_parity(api, ctx, name):
+def test_adjoint_parity(api, ctx, name, variant):
     b = box_of(name)
     db = api.DeviceBox(b)
+    set_gas_variant(ctx, variant)
     lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
     a, _ = api.grav_short(ctx, lv, db.gp, db.m)
     gx, gm = api.grav_short_adjoint(ctx, lv, db.gp, db.m, 2.0 * a)
@@ -195,6 +221,7 @@ def test_adjoint_parity(api, ctx, name):
     gas_t = (db.species == 0).float()
     gx2, gm2 = api.geometry_adjoint(ctx, lv, db.m, V, gas_t)
     torch.cuda.synchronize()
+    set_gas_variant(ctx, 0)
     I = O.from_box(b)
     ref_a, _ = O.gravity(I)
     ogx, ogm = O.gravity_adjoint(I, 2.0 * ref_a)
