@@ -100,10 +100,13 @@ const char *crk_version(void);
  * phase times to stderr.  Off by default; it serialises the build. */
 int crk_set_trace(crk_ctx *ctx, int on);
 /* Kernel variants: the execution scheme of one pair kernel (the results agree
- * within FP32 rounding).  Gas-pair kernels (geometry, corrections, hydro,
- * geometry adjoint): CRK_VARIANT_LISTS walks the exact neighbour lists built
- * with the leaves, CRK_VARIANT_TILES sweeps ballot-compacted j-leaf tiles.
- * Gravity kernels have CRK_VARIANT_TILES only.  crk_tune picks per kernel. */
+ * within FP32 rounding).  CRK_VARIANT_LISTS walks exact per-particle neighbour
+ * lists (gas pairs for geometry, corrections, hydro and the geometry adjoint;
+ * gravity pairs for gravity and its adjoint) that crk_build_leaves builds when
+ * a kernel that uses them is set to LISTS at build time; CRK_VARIANT_TILES
+ * sweeps ballot-compacted j-leaf tiles and needs no lists.  A kernel set to
+ * LISTS on leaves built without its lists runs as TILES.  Defaults: LISTS for
+ * the gas-pair kernels, TILES for the gravity kernels. */
 #define CRK_K_GEOMETRY 0
 #define CRK_K_CORRECTIONS 1
 #define CRK_K_HYDRO 2

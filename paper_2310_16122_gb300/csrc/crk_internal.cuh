@@ -28,8 +28,8 @@ struct crk_rcb_shape {
     int max_leaf = 0;
     int64_t n_leaves = 0, n_nodes = 0;
     int max_leaf_size = 0;
-    std::vector<size_t> level_off, level_size;  // segment tables, 6 int32 columns per level
-    int32_t *dtab = nullptr;                    // device: lo, hi, k, child, node, axis per segment
+    std::vector<size_t> level_off, level_size;  // segment tables, 7 int32 columns per level
+    int32_t *dtab = nullptr;                    // device: lo, hi, k, child, node, axis, leftbase per segment
     int32_t *leaf_start = nullptr;              // device [n_leaves + 1]
     int32_t *left = nullptr, *right = nullptr;  // device [n_nodes], -1 for leaves
     int32_t *leaf_of = nullptr;                 // device [n_nodes], leaf id or -1
@@ -53,6 +53,14 @@ struct crk_ctx {
     bool trace = false;  // CRK_TRACE=1: synchronise and print phase times of the leaf build
     // kernel variants (autotuner choices), indexed by CRK_K_*; 0 = default
     int variant[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+struct crk_nlist {
+    int32_t *gstart = nullptr;  // [n_leaves + 1] first group of each leaf
+    int32_t *goff = nullptr;    // [groups + 1] group offsets, units of 32 entries
+    int32_t *cnt = nullptr;     // [n] list length per kernel-order position
+    uint32_t *list = nullptr;
+    int64_t groups = 0, entries = 0;
 };
 
 struct crk_leaves {
@@ -81,16 +89,13 @@ struct crk_leaves {
     int32_t *gpair_start = nullptr, *gpair_cnt = nullptr, *gpair_list = nullptr;  // canonical gravity pairs
     int32_t *hpair_start = nullptr, *hpair_cnt = nullptr, *hpair_list = nullptr;  // canonical hydro pairs
     int64_t n_gimg = 0, n_himg = 0, n_gpairs = 0, n_hpairs = 0;
-    // exact gas neighbour lists (r < h_i + h_j, decided in FP32 exactly as the
-    // kernels decide it), one block per group of 32 consecutive gas particles
-    // of a leaf in kernel order, stored k-major (entry k of lane l at k*32 + l);
-    // an entry is (image index in the leaf's hydro image list << 10) | index of
-    // j inside its leaf
-    int32_t *gl_gstart = nullptr;  // [n_leaves + 1] first group of each leaf
-    int32_t *gl_goff = nullptr;    // [groups + 1] group offsets, units of 32 entries
-    int32_t *gl_cnt = nullptr;     // [n] list length per kernel-order position (gas)
-    uint32_t *gl_list = nullptr;
-    int64_t gl_groups = 0, gl_entries = 0, n_gas_pairs = 0;
+    // exact neighbour lists (decided in FP32 exactly as the kernels decide the
+    // range): gas pairs r < h_i + h_j, and gravity pairs r < r_cut.  One block
+    // per group of 32 consecutive particles of a leaf in kernel order (gas
+    // prefix only for the gas lists), stored k-major (entry k of lane l at
+    // k*32 + l); an entry is (image index in the leaf's image list << 10) |
+    // index of j inside its leaf
+    crk_nlist gas_lists, grav_lists;
     std::vector<std::pair<void *, size_t>> allocs;
 };
 
@@ -100,7 +105,7 @@ int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes);
 void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes);
 void crk_rcb_shape_free(crk_ctx *ctx);
-int crk_build_gas_lists(crk_ctx *ctx, crk_leaves *lv);
+int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas);
 
 #define CRK_CUDA(ctx, call)                                          \
     do {                                                             \
@@ -125,4 +130,32 @@ static inline int crk_grid(int64_t n, int block) {
     if (g < 1) g = 1;
     if (g > 2147483647LL) g = 2147483647LL;
     return (int)g;
+}
+
+// Block-wide exclusive scan of one int32 per thread (all threads must call);
+// warp_tot needs blockDim/32 entries.  Returns the thread's exclusive prefix.
+__device__ __forceinline__ int32_t crk_block_scan(int32_t v, int32_t *warp_tot, int32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(CRK_FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(CRK_FULL_MASK, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    total = warp_tot[nw - 1];
+    int32_t r = (warp > 0 ? warp_tot[warp - 1] : 0) + x - v;
+    __syncthreads();
+    return r;
 }

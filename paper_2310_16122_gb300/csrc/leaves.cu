@@ -74,6 +74,7 @@ __global__ void mesh_keys_kernel(const float *__restrict__ x, const float *__res
 struct LevelDev {
     const int32_t *lo, *hi, *k, *child, *node;
     int32_t *axis;
+    const int32_t *leftbase;  // sum of k over the earlier segments of the level
 };
 
 __global__ void rcb_axis_kernel(int nseg, LevelDev lv, const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
@@ -122,31 +123,107 @@ __global__ void rcb_side_kernel(int64_t n, LevelDev lv, const int32_t *__restric
     node_of_next[p] = lv.child[s] + right;
 }
 
-__global__ void rcb_flag_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
-                                const int32_t *__restrict__ Lb, const uint8_t *__restrict__ side,
-                                int32_t *__restrict__ flag) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int s = node_of[p];
-    flag[p] = (lv.k[s] > 0 && side[Lb[p]] == 0) ? 1 : 0;
+// Fused stable partition of the three axis lists, one level at a time.  The
+// prefix count of left-going entries at a segment's start equals the sum of k
+// over the earlier split segments (every split segment sends exactly k
+// entries left in every list), so the prefix is never materialised: tiles
+// count, a 3-column scan orders the tiles, and the scatter re-derives the
+// tile-local prefixes.
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 8;
+constexpr int kPartTile = kPartThreads * kPartItems;
+
+__global__ void rcb_count3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
+                                  const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
+                                  const int32_t *__restrict__ L2, const uint8_t *__restrict__ side,
+                                  int32_t *__restrict__ bsum, int64_t nb) {
+    __shared__ int32_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kPartTile;
+    int32_t c[3] = {0, 0, 0};
+    for (int k = 0; k < kPartItems; ++k) {
+        int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
+        if (p >= n) break;
+        if (lv.k[node_of[p]] <= 0) continue;
+        c[0] += side[L0[p]] == 0;
+        c[1] += side[L1[p]] == 0;
+        c[2] += side[L2[p]] == 0;
+    }
+    for (int b = 0; b < 3; ++b) {
+        int32_t tot;
+        crk_block_scan(c[b], wt, tot);
+        if (threadIdx.x == 0) bsum[(int64_t)b * nb + blockIdx.x] = tot;
+    }
 }
 
-__global__ void rcb_scatter_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
-                                   const int32_t *__restrict__ Lb, const uint8_t *__restrict__ side,
-                                   const int32_t *__restrict__ scan, int32_t *__restrict__ out) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int s = node_of[p];
-    int k = lv.k[s];
-    int32_t id = Lb[p];
-    if (k <= 0) {
-        out[p] = id;
-        return;
+// single block: exclusive scan of the three columns of tile sums, in place
+__global__ void rcb_scan3_kernel(int32_t *__restrict__ bsum, int64_t nb) {
+    __shared__ int32_t wt[32];
+    for (int b = 0; b < 3; ++b) {
+        int32_t carry = 0;
+        int32_t *col = bsum + (int64_t)b * nb;
+        for (int64_t s0 = 0; s0 < nb; s0 += blockDim.x) {
+            int64_t i = s0 + threadIdx.x;
+            int32_t v = i < nb ? col[i] : 0;
+            int32_t tot;
+            int32_t e = crk_block_scan(v, wt, tot);
+            if (i < nb) col[i] = carry + e;
+            carry += tot;
+        }
     }
-    int lo = lv.lo[s];
-    int lb = scan[p] - scan[lo];
-    int np = side[id] == 0 ? lo + lb : lo + k + ((int)p - lo - lb);
-    out[np] = id;
+}
+
+__global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
+                                    const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
+                                    const int32_t *__restrict__ L2, const uint8_t *__restrict__ side,
+                                    const int32_t *__restrict__ bsum, int64_t nb, int32_t *__restrict__ O0,
+                                    int32_t *__restrict__ O1, int32_t *__restrict__ O2, int32_t *__restrict__ err) {
+    __shared__ int32_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;  // blocked
+    const int32_t *Ls[3] = {L0, L1, L2};
+    int32_t *Os[3] = {O0, O1, O2};
+    int32_t seg[kPartItems];
+    uint32_t flags = 0;  // bit 3k+b: entry k of list b goes left
+    int32_t c[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+        int64_t p = base + k;
+        seg[k] = p < n ? node_of[p] : -1;
+        if (seg[k] >= 0 && lv.k[seg[k]] > 0) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                bool left = side[Ls[b][p]] == 0;
+                flags |= (uint32_t)left << (3 * k + b);
+                c[b] += left;
+            }
+        }
+    }
+    int32_t pre[3];
+    for (int b = 0; b < 3; ++b) {
+        int32_t tot;
+        pre[b] = crk_block_scan(c[b], wt, tot) + bsum[(int64_t)b * nb + blockIdx.x];
+    }
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+        int64_t p = base + k;
+        if (seg[k] < 0) continue;
+        const int s = seg[k];
+        const int ks = lv.k[s];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            int32_t id = Ls[b][p];
+            if (ks <= 0) {
+                Os[b][p] = id;
+                continue;
+            }
+            const int lo = lv.lo[s];
+            const int lb = pre[b] - lv.leftbase[s];  // left-going entries before p in this segment
+            const bool left = (flags >> (3 * k + b)) & 1u;
+            const int np = left ? lo + lb : lo + ks + ((int)p - lo - lb);
+            if (np >= lo && np < lv.hi[s]) Os[b][np] = id;
+            else atomicAdd(err, 1);  // inconsistent partition: reported, never written out of the segment
+            pre[b] += left;
+        }
+    }
 }
 
 // --- per-leaf data ------------------------------------------------------------
@@ -679,12 +756,13 @@ static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out)
     for (auto &L : levels) {
         r->level_off.push_back(tot);
         r->level_size.push_back(L.size());
-        tot += 6 * L.size();
+        tot += 7 * L.size();
     }
     std::vector<int32_t> packed(tot > 0 ? tot : 1);
     for (size_t d = 0; d < levels.size(); ++d) {
         const auto &L = levels[d];
         size_t m = L.size(), off = r->level_off[d];
+        int64_t leftbase = 0;
         for (size_t q = 0; q < m; ++q) {
             packed[off + q] = L[q].lo;
             packed[off + m + q] = L[q].hi;
@@ -692,6 +770,8 @@ static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out)
             packed[off + 3 * m + q] = L[q].child;
             packed[off + 4 * m + q] = L[q].node;
             packed[off + 5 * m + q] = 0;
+            packed[off + 6 * m + q] = (int32_t)leftbase;
+            leftbase += L[q].k;
         }
     }
     auto dev = [&](int32_t **p, const std::vector<int32_t> &v) -> int {
@@ -838,7 +918,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             int32_t *node_of = (int32_t *)crk_scratch(ctx, 8, nb);
             int32_t *node_nx = (int32_t *)crk_scratch(ctx, 9, nb);
             uint8_t *side = (uint8_t *)crk_scratch(ctx, 10, (size_t)(n > 0 ? n : 1));
-            int32_t *flag = (int32_t *)crk_scratch(ctx, 11, nb);
+            int32_t *flag = (int32_t *)crk_scratch(ctx, 11, nb + 3 * sizeof(int32_t) * (size_t)(n / 2048 + 2));
             if (!keys || !node_of || !node_nx || !side || !flag || !Lc[0] || !Lc[1] || !Lc[2] || !Ln[0] || !Ln[1] ||
                 !Ln[2]) {
                 rc = crk_fail(ctx, CRK_ENOMEM, "scratch");
@@ -858,17 +938,17 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             for (size_t d = 0; d < shape->level_size.size(); ++d) {
                 int m = (int)shape->level_size[d];
                 int32_t *tab = shape->dtab + shape->level_off[d];
-                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m};
+                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m};
                 rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, Lc[0], Lc[1], Lc[2], p->x, p->y, p->z,
                                                                   node_box);
                 rcb_side_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side, node_nx);
-                ctx->launches += 2;
-                for (int b = 0; b < 3; ++b) {
-                    rcb_flag_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[b], side, flag);
-                    TRY(crk_exclusive_scan_i32(ctx, flag, flag, n, nullptr));
-                    rcb_scatter_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[b], side, flag, Ln[b]);
-                    ctx->launches += 2;
-                }
+                const int64_t nbt = (n + kPartTile - 1) / kPartTile;
+                rcb_count3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side,
+                                                                          flag, nbt);
+                rcb_scan3_kernel<<<1, 1024, 0, st>>>(flag, nbt);
+                rcb_scatter3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side,
+                                                                            flag, nbt, Ln[0], Ln[1], Ln[2], flags + 5);
+                ctx->launches += 5;
                 for (int b = 0; b < 3; ++b) std::swap(Lc[b], Ln[b]);
                 std::swap(node_of, node_nx);
                 KCHECK("rcb level");
@@ -901,6 +981,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
         if (hflags[0] > 0) { rc = crk_fail(ctx, CRK_EBOX, "%d particle positions outside [0, box)", hflags[0]); goto fail; }
         if (hflags[1] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "%d gas particles with h <= 0 or not finite", hflags[1]); goto fail; }
         if (hflags[4] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "a leaf holds more than %d particles", kMaxLeafCap); goto fail; }
+        if (hflags[5] > 0) { rc = crk_fail(ctx, CRK_ESTATE, "internal error: inconsistent RCB partition"); goto fail; }
         lv->n_gas = hflags[2];
         float hmax_all;
         std::memcpy(&hmax_all, &hflags[8], sizeof(float));
@@ -932,7 +1013,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             for (size_t d = shape->level_size.size(); d-- > 0;) {
                 int m = (int)shape->level_size[d];
                 int32_t *tab = shape->dtab + shape->level_off[d];
-                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m};
+                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m};
                 node_hmax_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, shape->left, shape->right, node_hmax);
                 ++ctx->launches;
             }
@@ -1007,8 +1088,13 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             lv->hpair_start = se[6]; lv->hpair_cnt = se[7]; lv->hpair_list = hpair; lv->n_hpairs = (int64_t)hcur[3];
         }
         tr.mark("pair lists");
-        TRY(crk_build_gas_lists(ctx, lv));
+        if (ctx->variant[CRK_K_GEOMETRY] == CRK_VARIANT_LISTS || ctx->variant[CRK_K_CORRECTIONS] == CRK_VARIANT_LISTS ||
+            ctx->variant[CRK_K_HYDRO] == CRK_VARIANT_LISTS || ctx->variant[CRK_K_GEOMETRY_ADJOINT] == CRK_VARIANT_LISTS)
+            TRY(crk_build_lists(ctx, lv, true));
         tr.mark("gas lists");
+        if (ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS || ctx->variant[CRK_K_GRAVITY_ADJOINT] == CRK_VARIANT_LISTS)
+            TRY(crk_build_lists(ctx, lv, false));
+        tr.mark("gravity lists");
     }
 #undef TRY
 #undef ALLOC

@@ -541,18 +541,21 @@ struct HydroStage {
 };
 
 
-// Builds the exact gas neighbour lists (count pass, then fill pass).
+// Builds the exact neighbour lists (count pass, then fill pass): gas pairs
+// (r < h_i + h_j) or gravity pairs (r < r_cut).
 struct ListP {
     uint32_t *list;
     const int32_t *gstart, *goff;
     int32_t *cnt;
     int fill;
+    float rc2;
     int64_t n;
     unsigned long long *count;
 };
 
+template <bool kGas>
 struct ListStage {
-    static constexpr bool kGasOnly = true;
+    static constexpr bool kGasOnly = kGas;
     static constexpr bool kCons = false;
     static constexpr bool kTag = true;
     using P = ListP;
@@ -566,8 +569,12 @@ struct ListStage {
         int cnt;
     };
     __device__ static Rec gather(const P &, int32_t, float4 ps) { return {ps.x, ps.y, ps.z, ps.w, 0u, 0u, 0u, 0u}; }
-    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
-    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static float box_cut(const P &p, float hmax_i, const Rec &rj) {
+        return kGas ? hmax_i + rj.h : sqrtf(p.rc2);
+    }
+    __device__ static float leaf_cut(const P &p, float hmax_i, float hmax_j) {
+        return kGas ? hmax_i + hmax_j : sqrtf(p.rc2);
+    }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
     __device__ static void tag(Rec &r, int img_local, int j_local) {
         r.code = ((uint32_t)img_local << 10) | (uint32_t)j_local;
@@ -578,11 +585,19 @@ struct ListStage {
         s.out = p.fill ? p.list + (size_t)p.goff[p.gstart[a] + q] * 32 + lane : nullptr;
     }
     template <bool kCount>
-    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
-        float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float hs = ri.h + rj.h;
-        if (r2 < hs * hs) {
+    __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
+        bool in;
+        if (kGas) {
+            float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float hs = ri.h + rj.h;
+            in = r2 < hs * hs;
+        } else {  // the gravity kernels take d = x_j - x_i
+            float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            in = r2 < p.rc2;
+        }
+        if (in) {
             if (s.out) s.out[(size_t)s.c * 32] = rj.code;
             ++s.c;
         }
@@ -750,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t a = blockIdx.x; a < lv.n_leaves; a += gridDim.x) {
         const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
-        const int hi = lo + lv.leaf_ngas[a];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
         const crk_image *imgs = lv.img + lv.img_start[a];
         for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
             const int q = (g0 - lo) >> 5;
@@ -787,7 +802,8 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
                 if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
             }
         }
-        for (int t = hi + threadIdx.x; t < end; t += kThreads) S::finish_other(p, lv.kperm[t]);
+        if (S::kGasOnly)
+            for (int t = hi + threadIdx.x; t < end; t += kThreads) S::finish_other(p, lv.kperm[t]);
     }
     if constexpr (S::kCons) {
         if (cons_part) {
@@ -804,18 +820,19 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
     }
 }
 
-__global__ void list_group_count_kernel(int64_t n_leaves, const int32_t *__restrict__ ngas, int32_t *__restrict__ ng) {
+__global__ void list_group_count_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
+                                        const int32_t *__restrict__ ngas, int gas, int32_t *__restrict__ ng) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < n_leaves) ng[a] = (ngas[a] + 31) >> 5;
+    if (a < n_leaves) ng[a] = ((gas ? ngas[a] : leaf_start[a + 1] - leaf_start[a]) + 31) >> 5;
 }
 
 // per group: the longest list of its lanes (units of 32 entries once scanned)
 __global__ void list_group_k_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
-                                    const int32_t *__restrict__ ngas, const int32_t *__restrict__ gstart,
+                                    const int32_t *__restrict__ ngas, int gas, const int32_t *__restrict__ gstart,
                                     const int32_t *__restrict__ cnt, int32_t *__restrict__ gk) {
     int64_t a = blockIdx.x;
     if (a >= n_leaves) return;
-    const int lo = leaf_start[a], hi = lo + ngas[a];
+    const int lo = leaf_start[a], hi = gas ? lo + ngas[a] : leaf_start[a + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int g0 = lo + warp * 32; g0 < hi; g0 += (blockDim.x >> 5) * 32) {
         int i = g0 + lane;
@@ -848,9 +865,10 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
                gas_pairs ? lv->himg : lv->gimg, lv->n_leaves};
     if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
-    const bool lists = gas_pairs && lv->gl_list && ctx->variant[kernel_id] == CRK_VARIANT_LISTS;
+    const crk_nlist &nls = gas_pairs ? lv->gas_lists : lv->grav_lists;
+    const bool lists = nls.list && ctx->variant[kernel_id] == CRK_VARIANT_LISTS;
     if (lists) {
-        GasLists gl{lv->gl_gstart, lv->gl_goff, lv->gl_cnt, lv->gl_list};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list};
         if (p.count)
             list_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
         else
@@ -943,27 +961,31 @@ int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, co
     return run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
 }
 
-int crk_build_gas_lists(crk_ctx *ctx, crk_leaves *lv) {
+template <bool kGas>
+static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     const int64_t nl = lv->n_leaves, n = lv->n;
-    if (nl == 0 || n == 0 || lv->n_gas == 0) return CRK_OK;
+    if (nl == 0 || n == 0 || (kGas && lv->n_gas == 0)) return CRK_OK;
     cudaStream_t st = ctx->stream;
+    using LS = ListStage<kGas>;
     int32_t *gstart = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(nl + 1));
     int32_t *cnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)n);
     int32_t *ng = (int32_t *)crk_scratch(ctx, 6, sizeof(int32_t) * (size_t)(nl + 1));
     int32_t *tot = (int32_t *)crk_scratch(ctx, 7, 64);
     if (!gstart || !cnt || !ng || !tot) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
     CRK_CUDA(ctx, cudaMemsetAsync(ng, 0, sizeof(int32_t) * (size_t)(nl + 1), st));
-    list_group_count_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, lv->leaf_ngas, ng);
+    list_group_count_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, kGas, ng);
     ++ctx->launches;
     int rc = crk_exclusive_scan_i32(ctx, ng, gstart, nl + 1, tot);
     if (rc) return rc;
-    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm, lv->himg_start, lv->himg_cnt,
-               lv->himg, nl};
-    ListStage::Rec *rec = (ListStage::Rec *)crk_scratch(ctx, 4, sizeof(ListStage::Rec) * (size_t)n);
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
+               kGas ? lv->himg_start : lv->gimg_start, kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg,
+               nl};
+    typename LS::Rec *rec = (typename LS::Rec *)crk_scratch(ctx, 4, sizeof(typename LS::Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
-    gather_kernel<ListStage><<<crk_grid(n, 256), 256, 0, st>>>(n, lv->pos, lv->kperm, ListP{}, rec);
-    ListP pc{nullptr, gstart, nullptr, cnt, 0, n, nullptr};
-    pair_kernel<ListStage, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pc, rec, nullptr);
+    const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
+    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, lv->pos, lv->kperm, ListP{}, rec);
+    ListP pc{nullptr, gstart, nullptr, cnt, 0, rc2, n, nullptr};
+    pair_kernel<LS, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pc, rec, nullptr);
     ctx->launches += 2;
     CRK_LAUNCH_CHECK(ctx, "neighbour counts");
     int32_t ngroups = 0;
@@ -973,7 +995,7 @@ int crk_build_gas_lists(crk_ctx *ctx, crk_leaves *lv) {
     int32_t *gk = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(ngroups + 1));
     if (!goff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
     CRK_CUDA(ctx, cudaMemsetAsync(gk, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
-    list_group_k_kernel<<<(unsigned)nl, kThreads, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, gstart, cnt, gk);
+    list_group_k_kernel<<<(unsigned)nl, kThreads, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, kGas, gstart, cnt, gk);
     ++ctx->launches;
     rc = crk_exclusive_scan_i32(ctx, gk, goff, ngroups + 1, tot + 1);
     if (rc) return rc;
@@ -983,15 +1005,19 @@ int crk_build_gas_lists(crk_ctx *ctx, crk_leaves *lv) {
     const int64_t entries = (int64_t)rows * 32;
     uint32_t *list = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(entries > 0 ? entries : 1));
     if (!list) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
-    ListP pf{list, gstart, goff, cnt, 1, n, nullptr};
-    pair_kernel<ListStage, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pf, rec, nullptr);
+    ListP pf{list, gstart, goff, cnt, 1, rc2, n, nullptr};
+    pair_kernel<LS, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pf, rec, nullptr);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "neighbour lists");
-    lv->gl_gstart = gstart;
-    lv->gl_goff = goff;
-    lv->gl_cnt = cnt;
-    lv->gl_list = list;
-    lv->gl_groups = ngroups;
-    lv->gl_entries = entries;
+    out.gstart = gstart;
+    out.goff = goff;
+    out.cnt = cnt;
+    out.list = list;
+    out.groups = ngroups;
+    out.entries = entries;
     return CRK_OK;
+}
+
+int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas) {
+    return gas ? build_lists<true>(ctx, lv, lv->gas_lists) : build_lists<false>(ctx, lv, lv->grav_lists);
 }

@@ -119,7 +119,7 @@ def test_variant_switch(api, ctx):
 
     assert ctx.get_variant("hydro") == 0 and ctx.get_variant("gravity") == 1
     with pytest.raises(N.CrkError):
-        ctx.set_variant("gravity", 0)  # gravity has no list variant
+        ctx.set_variant("gravity", 7)
     ctx.set_variant("hydro", 1)
     assert ctx.get_variant("hydro") == 1
     ctx.set_variant("hydro", 0)
@@ -145,12 +145,17 @@ def test_error_statuses(api, ctx):
     assert e.value.status == N.CRK_EBOX  # 2 h_max >= box/2
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
 @pytest.mark.parametrize("name", ["tiny_mesh", "clustered24", "random1000_leaf7", "random777_mesh3"])
-def test_gravity_parity(api, ctx, name):
+def test_gravity_parity(api, ctx, name, variant):
     b = box_of(name)
     db = api.DeviceBox(b)
-    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
-    a, cnt = api.grav_short(ctx, lv, db.gp, db.m, count=True)
+    ctx.set_variant("gravity", variant)
+    try:
+        lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+        a, cnt = api.grav_short(ctx, lv, db.gp, db.m, count=True)
+    finally:
+        ctx.set_variant("gravity", 1)
     I = O.from_box(b)
     ref, npairs = O.gravity(I)
     e = rel_l2(a.cpu().numpy().T, ref)
@@ -158,12 +163,13 @@ def test_gravity_parity(api, ctx, name):
     assert abs(int(cnt.item()) - npairs) <= boundary_pairs(b, False)
 
 
-GAS_KERNELS = ("geometry", "corrections", "hydro", "geometry_adjoint")
+GAS_KERNELS = ("geometry", "corrections", "hydro", "geometry_adjoint", "gravity", "gravity_adjoint")
 
 
 def set_gas_variant(ctx, variant):
+    """variant for every pair kernel; None restores the defaults (lists for gas, tiles for gravity)"""
     for k in GAS_KERNELS:
-        ctx.set_variant(k, variant)
+        ctx.set_variant(k, (1 if k.startswith("gravity") else 0) if variant is None else variant)
 
 
 @pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
@@ -176,7 +182,7 @@ def test_hydro_chain_parity(api, ctx, name, variant):
         out = api.forward(ctx, db, count=True)
         torch.cuda.synchronize()
     finally:
-        set_gas_variant(ctx, 0)
+        set_gas_variant(ctx, None)
     I = O.from_box(b)
     ref = O.forward(I, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
     gas = b.species == 0
@@ -221,7 +227,7 @@ def test_adjoint_parity(api, ctx, name, variant):
     gas_t = (db.species == 0).float()
     gx2, gm2 = api.geometry_adjoint(ctx, lv, db.m, V, gas_t)
     torch.cuda.synchronize()
-    set_gas_variant(ctx, 0)
+    set_gas_variant(ctx, None)
     I = O.from_box(b)
     ref_a, _ = O.gravity(I)
     ogx, ogm = O.gravity_adjoint(I, 2.0 * ref_a)
