@@ -45,6 +45,7 @@ extern "C" {
 #define CRK_EBOX (-4)      /* a cut (r_c or 2 h_max) is not below half the box, or positions outside [0, box) */
 #define CRK_ESTATE (-5)    /* leaves and arrays do not belong together */
 #define CRK_ETIMEOUT (-6)  /* a bounded device wait expired (batched work queue) */
+#define CRK_ETOOLARGE (-7) /* more particles than an allocation-free entry point can hold */
 
 typedef struct crk_ctx crk_ctx;       /* opaque: device, stream, scratch arena, autotuner table */
 typedef struct crk_leaves crk_leaves; /* opaque: library-owned device buffers of one leaf build */
@@ -198,6 +199,29 @@ int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
  * V is the forward output.  Outputs gx3[3n], gm[n] (overwritten; dark matter 0). */
 int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *V, const float *rhobar,
                          const float *Vbar, float *gx3, float *gm);
+
+/* Allocation-free short-range gravity.  The paper has no counterpart: this is
+ * for callers that cannot let a library allocate device memory, such as an
+ * application whose own memory pool already owns the GPU, or a step loop that
+ * must never pay the device synchronisation cudaMalloc/cudaFree can imply.
+ * It computes exactly what grav_short computes (same kernels, no pair count)
+ * and calls no cudaMalloc, cudaFree or other allocating routine: its only
+ * scratch, 16 bytes per particle, is a file-scope device array of
+ * CRK_NOALLOC_MAX_PARTICLES entries (32 MiB) that every GPU which loads the
+ * library holds until the process exits.  The caller passes the inputs (leaves
+ * built earlier, m) and the output a3 as for grav_short.
+ *  - n > CRK_NOALLOC_MAX_PARTICLES: returns CRK_ETOOLARGE and does nothing.
+ *  - The context's device must be the current device (else CRK_ESTATE).
+ *  - The first call on a device looks up the array's device address (a
+ *    runtime query, no allocation); make that first call before any stream
+ *    capture begins.
+ *  - All calls share the one array: calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race and give wrong results; issue
+ *    them in one stream order.  Nothing in the array needs clearing: every
+ *    call rewrites the entries it reads.
+ * Errors are reported by the status code only (crk_last_error is not set). */
+#define CRK_NOALLOC_MAX_PARTICLES (1 << 21)
+int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m, float *a3);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,7 @@
 // compensated for the moment sums); the CRK 3x3 inverse and the conservation
 // reductions are FP64.
 #include <cmath>
+#include <mutex>
 
 #include "crk_internal.cuh"
 
@@ -1020,4 +1021,74 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
 
 int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas) {
     return gas ? build_lists<true>(ctx, lv, lv->gas_lists) : build_lists<false>(ctx, lv, lv->grav_lists);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free short-range gravity (no counterpart in the paper).
+//
+// Some callers cannot let a library call cudaMalloc: an application whose own
+// pool already owns the device memory, or a time-stepping loop that must not
+// pay the device synchronisation that cudaMalloc/cudaFree can imply.  This
+// entry point runs the same gravity kernels as grav_short, but its only
+// scratch (the kernel-order particle records, 16 bytes per particle) lives in
+// the file-scope array below, which every GPU that loads libcrk holds until
+// the process exits: CRK_NOALLOC_MAX_PARTICLES x 16 bytes = 32 MiB.
+namespace {
+__device__ __align__(256) GravStage::Rec g_noalloc_rec[CRK_NOALLOC_MAX_PARTICLES];
+
+constexpr int kNoAllocMaxDevices = 64;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_rec, per device
+std::mutex g_noalloc_mu;
+}  // namespace
+
+int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const float *m, float *a3) {
+    if (!ctx || !lv || !gp) return CRK_EINVAL;
+    const int64_t n = lv->n;
+    if (n > CRK_NOALLOC_MAX_PARTICLES) return CRK_ETOOLARGE;
+    if (n > 0 && (!m || !a3)) return CRK_EINVAL;
+    if (gp->r_cut != lv->r_cut_grav) return CRK_ESTATE;
+    if (n == 0) return CRK_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return CRK_ESTATE;  // the context's device must be current
+    }
+    // set-up, once per device, with that device current: the host-side name of a
+    // __device__ array is not a device address, so ask the runtime for it
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_rec) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return CRK_ECUDA;
+            }
+            g_noalloc_ptr[dev] = ptr;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    GravStage::Rec *rec = (GravStage::Rec *)base;
+    GravP p{};
+    p.m = m;
+    p.a3 = a3;
+    p.rc2 = gp->r_cut * gp->r_cut;
+    p.eps2 = gp->eps * gp->eps;
+    for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
+    p.n = n;
+    p.count = nullptr;
+    // every record is rewritten before it is read, so nothing needs clearing
+    gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm, lv->gimg_start, lv->gimg_cnt,
+               lv->gimg, lv->n_leaves};
+    const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
+    const crk_nlist &nls = lv->grav_lists;
+    if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list};
+        list_kernel<GravStage, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, nullptr);
+    } else {
+        pair_kernel<GravStage, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, nullptr);
+    }
+    ctx->launches += 2;
+    return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }

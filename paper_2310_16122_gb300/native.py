@@ -19,11 +19,13 @@ CRK_ECUDA = -3
 CRK_EBOX = -4
 CRK_ESTATE = -5
 CRK_ETIMEOUT = -6
+CRK_ETOOLARGE = -7
+NOALLOC_MAX_PARTICLES = 1 << 21
 KERNELS = {"geometry": 0, "corrections": 1, "hydro": 2, "gravity": 3, "gravity_adjoint": 4, "geometry_adjoint": 5}
 VARIANT_LISTS = 0
 VARIANT_TILES = 1
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
-                -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT"}
+                -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT", -7: "CRK_ETOOLARGE"}
 
 
 class CrkError(RuntimeError):
@@ -76,6 +78,7 @@ SIGNATURES = {
     "grav_short": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P],
     "grav_short_adjoint": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P, _P],
     "crk_geometry_adjoint": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "grav_short_noalloc": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P],
 }
 _VOID = {"crk_destroy", "crk_leaves_free"}
 _STR = {"crk_last_error", "crk_version"}
