@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crk", choices=["crk", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "clustered", "adjoint", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "clustered", "adjoint", "tiny"])
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trace-leaves", action="store_true", help="after timing, print leaf-build phase times")
+    ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8)")
     return ap.parse_args()
 
 
@@ -57,6 +58,8 @@ def make_box(name, rank):
 
     if name == "large":
         b = W.clustered_box(256, 5000, W.SEEDS["large"] + 7919 * rank, name="large_2x256^3")
+    elif name == "medium":  # profiling case: 2x128^3, inputs larger than L2
+        b = W.clustered_box(128, 1600, W.SEEDS["large"] + 31 + 7919 * rank, name="medium_2x128^3")
     elif name == "clustered":
         b = W.clustered_box(64, 200, W.SEEDS["clustered"] + 7919 * rank, name="clustered_2x64^3")
     elif name == "adjoint":
@@ -205,6 +208,10 @@ def main():
     build_library()
     box = make_box(args.workload, rank)
     ctx = api.Context(local)
+    for kv in filter(None, args.variants.split(",")):
+        k, v = kv.split("=")
+        ctx.set_variant(k, int(v))
+    variants = {k: ctx.get_variant(k) for k in native.KERNELS}
     db = api.DeviceBox(box, device=f"cuda:{local}")
     gas = (db.species == 0).float()
     stream = ctx.stream
@@ -336,6 +343,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs (~%.1f GB) larger than L2 (129 MB)" % (h2d / 1e9)},
             "pairs_per_step": pairs, "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+            "variants": variants,
             "kernels_tflops": all_flops / (kern_ms * 1e-3) / 1e12,
             "roofline": roofline, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 32,

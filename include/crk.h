@@ -116,7 +116,13 @@ int crk_set_trace(crk_ctx *ctx, int on);
 #define CRK_K_GEOMETRY_ADJOINT 5
 #define CRK_VARIANT_LISTS 0
 #define CRK_VARIANT_TILES 1
+#define CRK_VARIANT_TILES16 2 /* tiles with two 16-particle i-groups per warp */
+#define CRK_VARIANT_TILES8 3  /* tiles with four 8-particle i-groups per warp */
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
+/* Launch mode of the pair kernels: 0 (default) one block per i-leaf; 1
+ * persistent: a grid of 4 blocks per SM whose blocks take i-leaves from an
+ * atomic work queue (no block ever waits on another).  Same results. */
+int crk_set_persistent(crk_ctx *ctx, int on);
 int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant);
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int crk_launch_count(const crk_ctx *ctx, int64_t *out);
@@ -133,6 +139,24 @@ int crk_launch_count(const crk_ctx *ctx, int64_t *out);
  * Synchronises the context stream once. */
 int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
                      crk_leaves **out);
+
+/* Leaves of many independent periodic boxes in one build (the batched form):
+ * the particles of box b are the consecutive range box_start[b] ..
+ * box_start[b+1] - 1 of the device arrays, in [0, box_side[b]) (host arrays
+ * box_start[nbox + 1], box_side[nbox]).  RCB leaves only (mode 1); every box
+ * gets its own tree, leaves are numbered box by box, and leaf pairs never
+ * cross boxes.  Every kernel then runs over all boxes in one launch.  Cuts
+ * are checked per box (CRK_EBOX). */
+typedef struct {
+    const float *x, *y, *z;
+    const uint8_t *species;
+    int64_t n;
+    int nbox;
+    const int64_t *box_start;
+    const float *box_side;
+} crk_batch;
+int crk_build_leaves_batch(crk_ctx *ctx, const crk_batch *b, const float *h, const crk_leaf_params *lp,
+                           crk_leaves **out);
 
 /* info[0] = n, info[1] = number of leaves, info[2] = gravity leaf pairs,
  * info[3] = hydro leaf pairs, info[4] = gravity image entries, info[5] = hydro
@@ -199,6 +223,51 @@ int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
  * V is the forward output.  Outputs gx3[3n], gm[n] (overwritten; dark matter 0). */
 int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *V, const float *rhobar,
                          const float *Vbar, float *gx3, float *gm);
+
+/* One whole step of the path on one set of leaves, in this order: geometry,
+ * corrections, hydro, gravity, gravity adjoint, geometry adjoint.  All arrays
+ * are caller-owned device arrays laid out as for the single calls.  The
+ * adjoint cotangents default to the loss sum |a|^2 + sum_gas rho: when abar3
+ * (rhobar) is NULL the step writes 2a into scratch3 (3n floats) and the gas
+ * indicator into scratch1 (n floats), which the caller then provides.
+ * pair_count (device int64[3], may be NULL) receives the geometry, hydro and
+ * gravity pair counts; n_singular and conservation as for the single calls. */
+typedef struct {
+    const float *m, *v3, *u;                /* inputs */
+    float *V, *rho, *A, *B, *gradA, *gradB; /* geometry, corrections */
+    float *dvdt3, *dudt;                    /* hydro */
+    double *conservation;                   /* double[4], may be NULL */
+    float *a3;                              /* gravity */
+    const float *abar3;                     /* gravity cotangent, NULL = 2 a */
+    float *gx3_grav, *gm_grav;              /* gravity adjoint */
+    const float *rhobar, *Vbar;             /* geometry cotangents; rhobar NULL = 1 on gas; Vbar may be NULL */
+    float *gx3_geom, *gm_geom;              /* geometry adjoint */
+    float *scratch3, *scratch1;             /* needed when abar3 / rhobar are NULL */
+    int32_t *n_singular;                    /* may be NULL */
+    int64_t *pair_count;                    /* int64[3], may be NULL */
+} crk_step_io;
+
+int crk_step(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+             const crk_step_io *io);
+
+/* CUDA graph of crk_step (the batched form: one graph launch replays every
+ * kernel of the step).  Creation runs one uncaptured step (sizing the scratch
+ * arena) and then captures one step on the context stream, which must not be
+ * the legacy default stream.  The graph bakes in the leaves, the arrays and
+ * the kernel variants current at creation; replay it only while they are
+ * alive and unchanged in shape (their contents may change). */
+typedef struct crk_graph crk_graph;
+int crk_step_graph_create(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+                          const crk_step_io *io, crk_graph **out);
+int crk_graph_launch(crk_graph *g);
+void crk_graph_destroy(crk_graph *g);
+
+/* Autotuner: times every variant of every kernel on these leaves (best of
+ * reps after a warm-up, CUDA events on the context stream), keeps the fastest
+ * in the context, and reports ms_out[6 * 4] (kernel-major; -1 = not available)
+ * and best_out[6] (host arrays, may be NULL).  Runs one crk_step first. */
+int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+             const crk_step_io *io, int reps, float *ms_out, int *best_out);
 
 /* Allocation-free short-range gravity.  The paper has no counterpart: this is
  * for callers that cannot let a library allocate device memory, such as an

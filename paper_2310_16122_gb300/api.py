@@ -55,6 +55,9 @@ class Context:
     def set_variant(self, kernel: str, variant: int) -> None:
         self.check(N.lib().crk_set_variant(self.handle, N.KERNELS[kernel], int(variant)))
 
+    def set_persistent(self, on: bool) -> None:
+        self.check(N.lib().crk_set_persistent(self.handle, int(bool(on))))
+
     def get_variant(self, kernel: str) -> int:
         v = ctypes.c_int(0)
         self.check(N.lib().crk_get_variant(self.handle, N.KERNELS[kernel], ctypes.byref(v)))
@@ -232,6 +235,42 @@ class DeviceBox:
         self.hp = HydroParams()
 
 
+class DeviceBatch:
+    """Several independent boxes uploaded as one concatenated particle set (box b = one range)."""
+
+    def __init__(self, boxes, device="cuda"):
+        cat = lambda f, dt=np.float32: torch.as_tensor(np.ascontiguousarray(np.concatenate([f(b) for b in boxes]))
+                                                       ).to(device=device, dtype=torch.float32 if dt is np.float32
+                                                            else dt)
+        self.boxes = boxes
+        self.n = int(sum(b.n for b in boxes))
+        self.box_start = np.concatenate([[0], np.cumsum([b.n for b in boxes])]).astype(np.int64)
+        self.box_side = np.array([b.L for b in boxes], np.float32)
+        self.x, self.y, self.z = cat(lambda b: b.x), cat(lambda b: b.y), cat(lambda b: b.z)
+        self.species = torch.as_tensor(np.concatenate([b.species for b in boxes])).to(device=device,
+                                                                                       dtype=torch.uint8)
+        self.m, self.h, self.u = cat(lambda b: b.m), cat(lambda b: b.h), cat(lambda b: b.u)
+        self.v3 = torch.stack([cat(lambda b: b.vx), cat(lambda b: b.vy), cat(lambda b: b.vz)]).contiguous()
+        b0 = boxes[0]
+        self.lp = LeafParams(1, 0, b0.max_leaf, float(b0.r_cut))
+        self.gp = GravParams(float(b0.eps), float(b0.r_cut), tuple(float(c) for c in b0.poly))
+        self.hp = HydroParams()
+
+
+def build_leaves_batch(ctx: Context, dbt: DeviceBatch) -> Leaves:
+    n = dbt.n
+    bs = np.ascontiguousarray(dbt.box_start, np.int64)
+    side = np.ascontiguousarray(dbt.box_side, np.float32)
+    c = N.crk_batch(_f32(dbt.x, "x", n), _f32(dbt.y, "y", n), _f32(dbt.z, "z", n), dbt.species.data_ptr(), n,
+                    len(side), bs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                    side.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    lp = N.crk_leaf_params(int(dbt.lp.mode), 0, int(dbt.lp.max_leaf), float(dbt.lp.r_cut_grav))
+    out = ctypes.c_void_p()
+    ctx.check(N.lib().crk_build_leaves_batch(ctx.handle, ctypes.byref(c), _f32(dbt.h, "h", n), ctypes.byref(lp),
+                                             ctypes.byref(out)))
+    return Leaves(ctx, out, (dbt.x, dbt.y, dbt.z, dbt.species, dbt.h))
+
+
 def forward(ctx: Context, db: DeviceBox, count=False):
     """Leaves, then geometry -> corrections -> hydro, then gravity; returns a dict of device tensors."""
     lv = build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
@@ -241,3 +280,72 @@ def forward(ctx: Context, db: DeviceBox, count=False):
     a, ca = grav_short(ctx, lv, db.gp, db.m, count)
     return dict(leaves=lv, V=V, rho=rho, A=A, B=B, gA=gA, gB=gB, n_singular=ns, dv=dv, du=du, cons=cons, acc=a,
                 count_geom=cg, count_hydro=ch, count_grav=ca)
+
+
+# ------------------------------------------------------------------- whole step
+
+class StepIO:
+    """Device arrays of one whole step (crk_step): inputs from a DeviceBox, outputs allocated here."""
+
+    def __init__(self, ctx: Context, db: "DeviceBox"):
+        n = db.n
+        e = ctx.empty
+        self.db = db
+        self.V, self.rho, self.A, self.B, self.gA, self.gB = e(n), e(n), e(n), e(3, n), e(3, n), e(9, n)
+        self.dv, self.du = e(3, n), e(n)
+        self.cons = torch.zeros(4, dtype=torch.float64, device=ctx.device)
+        self.acc = e(3, n)
+        self.gx_grav, self.gm_grav, self.gx_geom, self.gm_geom = e(3, n), e(n), e(3, n), e(n)
+        self.scratch3, self.scratch1 = e(3, n), e(n)
+        self.n_singular = torch.zeros(1, dtype=torch.int32, device=ctx.device)
+        self.pair_count = torch.zeros(3, dtype=torch.int64, device=ctx.device)
+
+    def c(self, count: bool = False) -> N.crk_step_io:
+        d, P = self.db, lambda t: t.data_ptr() if t is not None else None
+        return N.crk_step_io(P(d.m), P(d.v3), P(d.u), P(self.V), P(self.rho), P(self.A), P(self.B), P(self.gA),
+                             P(self.gB), P(self.dv), P(self.du), P(self.cons), P(self.acc), None, P(self.gx_grav),
+                             P(self.gm_grav), None, None, P(self.gx_geom), P(self.gm_geom), P(self.scratch3),
+                             P(self.scratch1), P(self.n_singular), P(self.pair_count) if count else None)
+
+
+def step(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, count: bool = False) -> None:
+    """geometry -> corrections -> hydro -> gravity -> gravity adjoint -> geometry adjoint (one C call)."""
+    gp, hp, c = db.gp.c(), db.hp.c(), io.c(count)
+    ctx.check(N.lib().crk_step(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp), ctypes.byref(c)))
+
+
+class StepGraph:
+    """A captured CUDA graph of one crk_step on fixed leaves and arrays."""
+
+    def __init__(self, ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO):
+        self.ctx, self.keep = ctx, (lv, db, io)
+        gp, hp, c = db.gp.c(), db.hp.c(), io.c(False)
+        h = ctypes.c_void_p()
+        ctx.check(N.lib().crk_step_graph_create(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp),
+                                                ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self) -> None:
+        self.ctx.check(N.lib().crk_graph_launch(self.handle))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            N.lib().crk_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, reps: int = 3) -> dict:
+    """Autotune the kernel variants on these leaves; returns {kernel: (best, [ms per variant])}."""
+    gp, hp, c = db.gp.c(), db.hp.c(), io.c(False)
+    ms = (ctypes.c_float * 24)()
+    best = (ctypes.c_int * 6)()
+    ctx.check(N.lib().crk_tune(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp), ctypes.byref(c),
+                               int(reps), ms, best))
+    names = sorted(N.KERNELS, key=N.KERNELS.get)
+    return {k: (int(best[i]), [float(ms[4 * i + v]) for v in range(4)]) for i, k in enumerate(names)}

@@ -26,6 +26,9 @@ struct crk_image {
 struct crk_rcb_shape {
     int64_t n = -1;
     int max_leaf = 0;
+    std::vector<int64_t> box_start;             // the boxes this shape was built for
+    std::vector<int32_t> box_root;              // root node of each box (-1 for an empty box)
+    std::vector<int32_t> leaf_box;              // box of each leaf (host copy)
     int64_t n_leaves = 0, n_nodes = 0;
     int max_leaf_size = 0;
     std::vector<size_t> level_off, level_size;  // segment tables, 7 int32 columns per level
@@ -34,6 +37,8 @@ struct crk_rcb_shape {
     int32_t *left = nullptr, *right = nullptr;  // device [n_nodes], -1 for leaves
     int32_t *leaf_of = nullptr;                 // device [n_nodes], leaf id or -1
     int32_t *leaf_node = nullptr;               // device [n_leaves]
+    int32_t *d_leaf_box = nullptr;              // device [n_leaves]
+    int32_t *d_box_root = nullptr;              // device [nbox]
 };
 
 struct crk_ctx {
@@ -42,7 +47,7 @@ struct crk_ctx {
     int num_sms = 0;
     std::string err;
     // growable scratch arena: one buffer per slot
-    static const int kSlots = 16;
+    static const int kSlots = 24;  // leaf build 0-16, radix sort 12-14, scan 15
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     int64_t launches = 0;  // kernels this context has launched
@@ -51,6 +56,7 @@ struct crk_ctx {
     std::vector<std::pair<void *, size_t>> block_cache;
     crk_rcb_shape *rcb = nullptr;
     bool trace = false;  // CRK_TRACE=1: synchronise and print phase times of the leaf build
+    bool persistent = false;  // pair kernels: persistent grid + atomic leaf queue
     // kernel variants (autotuner choices), indexed by CRK_K_*; 0 = default
     int variant[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
@@ -67,7 +73,8 @@ struct crk_leaves {
     int64_t n = 0;
     int64_t n_gas = 0;
     int64_t n_leaves = 0;
-    float box = 0.f;
+    float box = 0.f;  // largest box side
+    int nbox = 1;
     int mode = 1;
     float r_cut_grav = 0.f;
     float hmax_all = 0.f;

@@ -25,22 +25,46 @@ __device__ __forceinline__ uint32_t coord_key(float x) {
     return x == 0.0f ? 0u : __float_as_uint(x);
 }
 
+// Positions in [0, L_box), gas h > 0 and finite; largest gas h per box.
 __global__ void validate_kernel(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
-                                const uint8_t *__restrict__ sp, const float *__restrict__ h, int64_t n, float box,
+                                const uint8_t *__restrict__ sp, const float *__restrict__ h, int64_t n,
+                                const int32_t *__restrict__ box_of, const float *__restrict__ box_L,
                                 int32_t *__restrict__ flags /* [0] bad pos, [1] bad h, [2] n_gas */,
-                                unsigned *__restrict__ hmax_bits) {
+                                unsigned *__restrict__ hmax_bits /* per box */) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int b = box_of ? box_of[i] : 0;
+    const float L = box_L[b];
     float c[3] = {x[i], y[i], z[i]};
     bool bad = false;
-    for (int a = 0; a < 3; ++a) bad |= !(c[a] >= 0.0f && c[a] < box);
+    for (int a = 0; a < 3; ++a) bad |= !(c[a] >= 0.0f && c[a] < L);
     if (bad) atomicAdd(&flags[0], 1);
     if (sp[i] == 0) {
         float hi = h[i];
         if (!(hi > 0.0f) || !isfinite(hi)) atomicAdd(&flags[1], 1);
-        else atomicMax(hmax_bits, __float_as_uint(hi));
+        else atomicMax(&hmax_bits[b], __float_as_uint(hi));
         atomicAdd(&flags[2], 1);
     }
+}
+
+// box of each particle from the box starts (binary search)
+__global__ void box_of_kernel(int64_t n, const int64_t *__restrict__ box_start, int nbox, int32_t *__restrict__ box_of) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (box_start[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    box_of[i] = lo;
+}
+
+// keys for the stable re-sort of an axis list by box
+__global__ void box_keys_kernel(int64_t n, const int32_t *__restrict__ list, const int32_t *__restrict__ box_of,
+                                uint32_t *__restrict__ keys) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) keys[p] = (uint32_t)box_of[list[p]];
 }
 
 __global__ void init_axis_keys_kernel(const float *__restrict__ c, int64_t n, uint32_t *__restrict__ keys,
@@ -509,7 +533,8 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
 template <bool kBrute>
 __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
     int64_t n_leaves, const int32_t *__restrict__ leaf_start, const int32_t *__restrict__ leaf_ngas,
-    const float *__restrict__ bbox, const float *__restrict__ hmax, TreeDev tree, double L, double rc, PairOut o) {
+    const float *__restrict__ bbox, const float *__restrict__ hmax, TreeDev tree, double L0, double rc, PairOut o,
+    const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ box_root, const float *__restrict__ box_L) {
     __shared__ int32_t stack[kTravWarps][kStackCap];
     __shared__ int32_t cand[kTravWarps][kCandCap];
     __shared__ int32_t sorted[kTravWarps][kCandCap];
@@ -522,6 +547,9 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
     const bool a_gas = leaf_ngas[a] > 0;
     const float *A = bbox + 6 * a;
     const float ha = hmax[a];
+    const int bx = leaf_box ? leaf_box[a] : 0;
+    const double L = leaf_box ? (double)box_L[bx] : L0;
+    const int32_t root = leaf_box ? box_root[bx] : tree.root;
     const float Lf = (float)L;
     int nc = 0;
     bool bad = false;
@@ -541,7 +569,7 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
             }
         } else {
             int top = 1;
-            if (lane == 0) stack[warp][0] = tree.root;
+            if (lane == 0) stack[warp][0] = root;
             __syncwarp();
             while (top > 0) {
                 const int take = top < 32 ? top : 32;
@@ -694,13 +722,17 @@ void crk_rcb_shape_free(crk_ctx *ctx) {
     cudaFree(r->right);
     cudaFree(r->leaf_of);
     cudaFree(r->leaf_node);
+    cudaFree(r->d_leaf_box);
+    cudaFree(r->d_box_root);
     delete r;
     ctx->rcb = nullptr;
 }
 
-// The RCB tree shape for (n, max_leaf): level segment tables, leaf starts, children.
-static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out) {
-    if (ctx->rcb && ctx->rcb->n == n && ctx->rcb->max_leaf == ml) {
+// The RCB tree shape for the boxes [box_start[b], box_start[b+1]) and
+// max_leaf: level segment tables, leaf starts, children (one root per box).
+static int rcb_shape(crk_ctx *ctx, const std::vector<int64_t> &box_start, int ml, const crk_rcb_shape **out) {
+    const int64_t n = box_start.back();
+    if (ctx->rcb && ctx->rcb->box_start == box_start && ctx->rcb->max_leaf == ml) {
         *out = ctx->rcb;
         return CRK_OK;
     }
@@ -709,11 +741,20 @@ static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out)
     crk_rcb_shape *r = new crk_rcb_shape();
     r->n = n;
     r->max_leaf = ml;
+    r->box_start = box_start;
+    const int nbox = (int)box_start.size() - 1;
     std::vector<std::vector<HostSeg>> levels;
     std::vector<HostSeg> cur;
-    std::vector<int32_t> left(1, -1), right(1, -1);
+    std::vector<int32_t> left, right;
     int32_t next_node = 0;
-    if (n > 0) cur.push_back({0, (int32_t)n, 0, 0, next_node++});
+    r->box_root.assign(nbox, -1);
+    for (int b = 0; b < nbox; ++b)
+        if (box_start[b + 1] > box_start[b]) {
+            r->box_root[b] = next_node;
+            cur.push_back({(int32_t)box_start[b], (int32_t)box_start[b + 1], 0, 0, next_node++});
+        }
+    left.assign(next_node > 0 ? next_node : 1, -1);
+    right.assign(next_node > 0 ? next_node : 1, -1);
     while (!cur.empty()) {
         bool any = false;
         for (auto &sg : cur)
@@ -745,10 +786,13 @@ static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out)
     r->n_leaves = nl;
     r->n_nodes = next_node;
     std::vector<int32_t> leaf_start(nl + 1), leaf_of(next_node > 0 ? next_node : 1, -1), leaf_node(nl > 0 ? nl : 1);
-    for (int64_t a = 0; a < nl; ++a) {
+    r->leaf_box.assign(nl > 0 ? nl : 1, 0);
+    for (int64_t a = 0, b = 0; a < nl; ++a) {
         leaf_start[a] = cur[a].lo;
         leaf_of[cur[a].node] = (int32_t)a;
         leaf_node[a] = cur[a].node;
+        while (b + 1 < nbox && box_start[b + 1] <= cur[a].lo) ++b;
+        r->leaf_box[a] = (int32_t)b;
         r->max_leaf_size = std::max(r->max_leaf_size, cur[a].hi - cur[a].lo);
     }
     leaf_start[nl] = (int32_t)n;
@@ -790,6 +834,8 @@ static int rcb_shape(crk_ctx *ctx, int64_t n, int ml, const crk_rcb_shape **out)
     if (!rc) rc = dev(&r->right, right);
     if (!rc) rc = dev(&r->leaf_of, leaf_of);
     if (!rc) rc = dev(&r->leaf_node, leaf_node);
+    if (!rc) rc = dev(&r->d_leaf_box, r->leaf_box);
+    if (!rc) rc = dev(&r->d_box_root, r->box_root);
     ctx->rcb = r;
     if (rc) {
         crk_rcb_shape_free(ctx);
@@ -814,27 +860,45 @@ struct Tracer {
 };
 }  // namespace
 
-int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
-                     crk_leaves **out) {
-    if (!ctx) return CRK_EINVAL;
+__global__ void init_node_of_kernel(int64_t n, const int32_t *__restrict__ box_of, const int32_t *__restrict__ seg_of_box,
+                                    int32_t *__restrict__ node_of) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) node_of[p] = seg_of_box[box_of[p]];
+}
+
+// Leaves of one box (nbox = 1) or of several independent periodic boxes whose
+// particles are the consecutive ranges box_start[b] .. box_start[b+1].
+static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
+                             const std::vector<int64_t> &box_start, const std::vector<float> &box_side,
+                             crk_leaves **out) {
     if (!p || !lp || !out) return crk_fail(ctx, CRK_EINVAL, "null argument");
     *out = nullptr;
     const int64_t n = p->n;
+    const int nbox = (int)box_side.size();
     if (n < 0 || n > 2000000000LL) return crk_fail(ctx, CRK_EINVAL, "particle count out of range");
     if (n > 0 && (!p->x || !p->y || !p->z || !p->species || !h)) return crk_fail(ctx, CRK_EINVAL, "null array");
-    if (!(p->box > 0.0f)) return crk_fail(ctx, CRK_EINVAL, "box must be positive");
     if (lp->mode != 0 && lp->mode != 1) return crk_fail(ctx, CRK_EINVAL, "leaf mode must be 0 or 1");
+    if (lp->mode == 0 && nbox != 1) return crk_fail(ctx, CRK_EINVAL, "chaining-mesh leaves take one box");
     if (lp->mode == 0 && (lp->cells_per_side < 1 || lp->cells_per_side > 40))
         return crk_fail(ctx, CRK_EINVAL, "cells_per_side must be in [1, 40]");
     if (lp->mode == 1 && (lp->max_leaf < 1 || lp->max_leaf > kMaxLeafCap))
         return crk_fail(ctx, CRK_EINVAL, "max_leaf must be in [1, 1024]");
-    if (!(lp->r_cut_grav > 0.0f) || !((double)lp->r_cut_grav < 0.5 * (double)p->box))
-        return crk_fail(ctx, CRK_EBOX, "r_cut_grav must be positive and below box/2");
+    float box_max = 0.0f;
+    for (int b = 0; b < nbox; ++b) {
+        if (!(box_side[b] > 0.0f)) return crk_fail(ctx, CRK_EINVAL, "box %d: side must be positive", b);
+        if (box_start[b + 1] < box_start[b]) return crk_fail(ctx, CRK_EINVAL, "box starts must not decrease");
+        if (box_start[b + 1] > box_start[b] && (!(lp->r_cut_grav > 0.0f) ||
+                                                !((double)lp->r_cut_grav < 0.5 * (double)box_side[b])))
+            return crk_fail(ctx, CRK_EBOX, "box %d: r_cut_grav must be positive and below box/2", b);
+        box_max = std::max(box_max, box_side[b]);
+    }
+    if (box_start[0] != 0 || box_start[nbox] != n) return crk_fail(ctx, CRK_EINVAL, "box starts must span [0, n]");
 
     Tracer tr(ctx);
     crk_leaves *lv = new crk_leaves();
     lv->n = n;
-    lv->box = p->box;
+    lv->box = box_max;
+    lv->nbox = nbox;
     lv->mode = lp->mode;
     lv->r_cut_grav = lp->r_cut_grav;
     cudaStream_t st = ctx->stream;
@@ -861,12 +925,37 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
         }                                                  \
     } while (0)
     {
-        int32_t *flags = (int32_t *)crk_scratch(ctx, 0, 64);
+        // flags[0..15]; then per box: hmax bits, side, start (int64), segment index
+        const size_t fbytes = 64 + 4 * (size_t)nbox + 4 * (size_t)nbox + 8 * (size_t)(nbox + 1) + 4 * (size_t)nbox;
+        int32_t *flags = (int32_t *)crk_scratch(ctx, 0, fbytes + 64);
         if (!flags) { rc = crk_fail(ctx, CRK_ENOMEM, "scratch"); goto fail; }
-        if (cudaMemsetAsync(flags, 0, 64, st) != cudaSuccess) { rc = crk_fail(ctx, CRK_ECUDA, "memset"); goto fail; }
-        unsigned *hbits = (unsigned *)(flags + 8);
+        unsigned *hbits = (unsigned *)(flags + 16);
+        float *box_L = (float *)(flags + 16 + nbox);
+        int64_t *d_box_start = (int64_t *)(((uintptr_t)(flags + 16 + 2 * nbox) + 7) & ~(uintptr_t)7);
+        int32_t *seg_of_box = (int32_t *)(d_box_start + nbox + 1);
+        std::vector<int32_t> h_seg(nbox, 0);
+        for (int b = 0, q = 0; b < nbox; ++b) {
+            h_seg[b] = q;
+            if (box_start[b + 1] > box_start[b]) ++q;
+        }
+        if (cudaMemsetAsync(flags, 0, 64 + 4 * (size_t)nbox, st) != cudaSuccess ||
+            cudaMemcpyAsync(box_L, box_side.data(), 4 * (size_t)nbox, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_box_start, box_start.data(), 8 * (size_t)(nbox + 1), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(seg_of_box, h_seg.data(), 4 * (size_t)nbox, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = crk_fail(ctx, CRK_ECUDA, "leaf build set-up copies");
+            goto fail;
+        }
+        int32_t *box_of = nullptr;
+        if (nbox > 1 && n > 0) {
+            box_of = (int32_t *)crk_scratch(ctx, 16, sizeof(int32_t) * (size_t)n);
+            if (!box_of) { rc = crk_fail(ctx, CRK_ENOMEM, "scratch"); goto fail; }
+            box_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, d_box_start, nbox, box_of);
+            ++ctx->launches;
+        }
         if (n > 0) {
-            validate_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, p->species, h, n, p->box, flags, hbits);
+            validate_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, p->species, h, n, box_of, box_L, flags,
+                                                              hbits);
             ++ctx->launches;
         }
         int32_t *members = nullptr;  // particle ids grouped by leaf
@@ -887,7 +976,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
                 goto fail;
             }
             if (n > 0) {
-                mesh_keys_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, n, nc, (double)p->box, keys,
+                mesh_keys_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, n, nc, (double)box_side[0], keys,
                                                                    vals, cnts);
                 ++ctx->launches;
             }
@@ -897,7 +986,7 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
             TRY(crk_exclusive_scan_i32(ctx, cnts, lv->leaf_start, nl + 1, nullptr));
             members = vals;
         } else {
-            TRY(rcb_shape(ctx, n, lp->max_leaf, &shape));
+            TRY(rcb_shape(ctx, box_start, lp->max_leaf, &shape));
             nl = shape->n_leaves;
             ALLOC(lv->leaf_start, int32_t, nl + 1);
             if (cudaMemcpyAsync(lv->leaf_start, shape->leaf_start, sizeof(int32_t) * (size_t)(nl + 1),
@@ -929,11 +1018,23 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
                 init_axis_keys_kernel<<<crk_grid(n, 256), 256, 0, st>>>(cs[a], n, keys, Lc[a]);
                 ++ctx->launches;
                 TRY(crk_radix_sort_u32(ctx, keys, Lc[a], n, 32));
+                if (box_of) {  // stable by box: (box, coordinate, index) order
+                    box_keys_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, Lc[a], box_of, keys);
+                    ++ctx->launches;
+                    int bits = 1;
+                    while ((1 << bits) < nbox) ++bits;
+                    TRY(crk_radix_sort_u32(ctx, keys, Lc[a], n, bits));
+                }
             }
             tr.mark("axis sorts");
-            if (n > 0 && cudaMemsetAsync(node_of, 0, sizeof(int32_t) * (size_t)n, st) != cudaSuccess) {
-                rc = crk_fail(ctx, CRK_ECUDA, "memset");
-                goto fail;
+            if (n > 0) {
+                if (box_of) {
+                    init_node_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, box_of, seg_of_box, node_of);
+                    ++ctx->launches;
+                } else if (cudaMemsetAsync(node_of, 0, sizeof(int32_t) * (size_t)n, st) != cudaSuccess) {
+                    rc = crk_fail(ctx, CRK_ECUDA, "memset");
+                    goto fail;
+                }
             }
             for (size_t d = 0; d < shape->level_size.size(); ++d) {
                 int m = (int)shape->level_size[d];
@@ -972,7 +1073,9 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
         KCHECK("leaf data");
         // ---- host checks (one synchronisation)
         int32_t hflags[16];
+        std::vector<unsigned> hb(nbox);
         if (cudaMemcpyAsync(hflags, flags, 64, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hb.data(), hbits, 4 * (size_t)nbox, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             rc = crk_fail(ctx, CRK_ECUDA, "leaf build: %s", cudaGetErrorString(cudaGetLastError()));
             goto fail;
@@ -983,13 +1086,17 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
         if (hflags[4] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "a leaf holds more than %d particles", kMaxLeafCap); goto fail; }
         if (hflags[5] > 0) { rc = crk_fail(ctx, CRK_ESTATE, "internal error: inconsistent RCB partition"); goto fail; }
         lv->n_gas = hflags[2];
-        float hmax_all;
-        std::memcpy(&hmax_all, &hflags[8], sizeof(float));
-        lv->hmax_all = hmax_all;
-        if (!(2.0 * (double)hmax_all < 0.5 * (double)p->box)) {
-            rc = crk_fail(ctx, CRK_EBOX, "2 h_max = %g is not below box/2", 2.0 * hmax_all);
-            goto fail;
+        float hmax_all = 0.0f;
+        for (int b = 0; b < nbox; ++b) {
+            float hm;
+            std::memcpy(&hm, &hb[b], sizeof(float));
+            hmax_all = std::max(hmax_all, hm);
+            if (!(2.0 * (double)hm < 0.5 * (double)box_side[b])) {
+                rc = crk_fail(ctx, CRK_EBOX, "box %d: 2 h_max = %g is not below box/2", b, 2.0 * hm);
+                goto fail;
+            }
         }
+        lv->hmax_all = hmax_all;
         if (lp->mode == 0) {
             std::vector<int32_t> ls(nl + 1);
             if (cudaMemcpy(ls.data(), lv->leaf_start, sizeof(int32_t) * (nl + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -1057,12 +1164,12 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
                     unsigned grid = (unsigned)((nl + kTravWarps - 1) / kTravWarps);
                     if (brute)
                         leaf_pairs_warp_kernel<true><<<grid, kTravWarps * 32, 0, st>>>(
-                            nl, lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, tree, (double)p->box,
-                            (double)lp->r_cut_grav, po);
+                            nl, lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, tree, (double)box_side[0],
+                            (double)lp->r_cut_grav, po, nullptr, nullptr, nullptr);
                     else
                         leaf_pairs_warp_kernel<false><<<grid, kTravWarps * 32, 0, st>>>(
-                            nl, lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, tree, (double)p->box,
-                            (double)lp->r_cut_grav, po);
+                            nl, lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, tree, (double)box_side[0],
+                            (double)lp->r_cut_grav, po, shape->d_leaf_box, shape->d_box_root, box_L);
                     ++ctx->launches;
                 }
                 KCHECK("pair lists");
@@ -1104,6 +1211,27 @@ int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const
 fail:
     crk_leaves_free(ctx, lv);
     return rc;
+}
+
+int crk_build_leaves(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
+                     crk_leaves **out) {
+    if (!ctx) return CRK_EINVAL;
+    if (!p) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (p->n < 0) return crk_fail(ctx, CRK_EINVAL, "particle count out of range");
+    std::vector<int64_t> bs = {0, p->n};
+    std::vector<float> side = {p->box};
+    return build_leaves_impl(ctx, p, h, lp, bs, side, out);
+}
+
+int crk_build_leaves_batch(crk_ctx *ctx, const crk_batch *bt, const float *h, const crk_leaf_params *lp,
+                           crk_leaves **out) {
+    if (!ctx) return CRK_EINVAL;
+    if (!bt || !bt->box_start || !bt->box_side || bt->nbox < 1) return crk_fail(ctx, CRK_EINVAL, "bad batch");
+    std::vector<int64_t> bs(bt->box_start, bt->box_start + bt->nbox + 1);
+    std::vector<float> side(bt->box_side, bt->box_side + bt->nbox);
+    crk_particles p{bt->x, bt->y, bt->z, bt->species, bt->n, 0.0f};
+    for (float s : side) p.box = std::max(p.box, s);
+    return build_leaves_impl(ctx, &p, h, lp, bs, side, out);
 }
 
 int crk_leaves_info(const crk_leaves *lv, int64_t info[6]) {

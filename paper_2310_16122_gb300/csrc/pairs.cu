@@ -35,7 +35,18 @@ struct LeafView {
     const int32_t *img_cnt;
     const crk_image *img;
     int64_t n_leaves;
+    int32_t *queue;  // persistent mode: next leaf to take (zeroed before launch); NULL = one block per leaf
 };
+
+// Next i-leaf of this block: the grid-stride successor, or (persistent mode)
+// the next unclaimed leaf of the work queue.  Block-uniform; every thread calls it.
+__device__ __forceinline__ int64_t next_leaf(const LeafView &lv, int64_t cur, int64_t *slot) {
+    if (!lv.queue) return cur < 0 ? (int64_t)blockIdx.x : cur + gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = atomicAdd(lv.queue, 1);
+    __syncthreads();
+    return *slot;
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -615,7 +626,9 @@ __global__ void gather_kernel(int64_t n, const float4 *__restrict__ pos, const i
                               typename S::P p, typename S::Rec *__restrict__ rec) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    rec[q] = S::gather(p, kperm[q], pos[q]);
+    const float4 ps = pos[q];
+    if (S::kGasOnly && ps.w == 0.0f) return;  // dark matter (h = 0): never read by gas-pair stages
+    rec[q] = S::gather(p, kperm[q], ps);
 }
 
 template <class S, bool kCount>
@@ -628,7 +641,8 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned below = lanemask_lt();
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t a = blockIdx.x; a < lv.n_leaves; a += gridDim.x) {
+    __shared__ int64_t leaf_slot;
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
         const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
         const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
@@ -731,6 +745,159 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
     }
 }
 
+
+// Tiles with sub-warp i-groups: the warp's 32 i-particles form 32/G groups of
+// G consecutive (Z-ordered) particles, each with its own box and its own
+// compacted candidate buffer; lane l sweeps the buffer of group l/G.  Smaller
+// groups have smaller boxes, so a larger share of the swept pairs is in range.
+// Within one 8-lane phase of a shared-memory load every lane reads the same
+// record (G >= 8), so the sweep stays a broadcast.
+template <class S, int G, bool kCount>
+__global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typename S::P p,
+                                                            const typename S::Rec *__restrict__ rec,
+                                                            double *__restrict__ cons_part) {
+    using Rec = typename S::Rec;
+    constexpr int NS = 32 / G;
+    __shared__ Rec buf[kWarps][NS][kCap];
+    __shared__ double cons_sh[kWarps][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sg = lane / G;
+    const unsigned below = lanemask_lt();
+    double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
+    __shared__ int64_t leaf_slot;
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
+        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
+        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
+            const int i = g0 + lane;
+            const bool act = i < hi;
+            const Rec ri = rec[act ? i : g0];
+            typename S::I st;
+            S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
+            // group boxes (empty for groups without active lanes) and largest h
+            float l0 = act ? ri.x : INFINITY, l1 = act ? ri.y : INFINITY, l2 = act ? ri.z : INFINITY;
+            float h0 = act ? ri.x : -INFINITY, h1 = act ? ri.y : -INFINITY, h2 = act ? ri.z : -INFINITY;
+            float hm = act ? lv.pos[i].w : 0.0f;
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                l0 = fminf(l0, __shfl_xor_sync(CRK_FULL_MASK, l0, o));
+                l1 = fminf(l1, __shfl_xor_sync(CRK_FULL_MASK, l1, o));
+                l2 = fminf(l2, __shfl_xor_sync(CRK_FULL_MASK, l2, o));
+                h0 = fmaxf(h0, __shfl_xor_sync(CRK_FULL_MASK, h0, o));
+                h1 = fmaxf(h1, __shfl_xor_sync(CRK_FULL_MASK, h1, o));
+                h2 = fmaxf(h2, __shfl_xor_sync(CRK_FULL_MASK, h2, o));
+                hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
+            }
+            float bl[NS][3], bh[NS][3], bhm[NS];
+            float ul0 = INFINITY, ul1 = INFINITY, ul2 = INFINITY, uh0 = -INFINITY, uh1 = -INFINITY, uh2 = -INFINITY,
+                  uhm = 0.0f;
+#pragma unroll
+            for (int t = 0; t < NS; ++t) {
+                bl[t][0] = __shfl_sync(CRK_FULL_MASK, l0, t * G);
+                bl[t][1] = __shfl_sync(CRK_FULL_MASK, l1, t * G);
+                bl[t][2] = __shfl_sync(CRK_FULL_MASK, l2, t * G);
+                bh[t][0] = __shfl_sync(CRK_FULL_MASK, h0, t * G);
+                bh[t][1] = __shfl_sync(CRK_FULL_MASK, h1, t * G);
+                bh[t][2] = __shfl_sync(CRK_FULL_MASK, h2, t * G);
+                bhm[t] = __shfl_sync(CRK_FULL_MASK, hm, t * G);
+                ul0 = fminf(ul0, bl[t][0]); ul1 = fminf(ul1, bl[t][1]); ul2 = fminf(ul2, bl[t][2]);
+                uh0 = fmaxf(uh0, bh[t][0]); uh1 = fmaxf(uh1, bh[t][1]); uh2 = fmaxf(uh2, bh[t][2]);
+                uhm = fmaxf(uhm, bhm[t]);
+            }
+            int cnt[NS];
+#pragma unroll
+            for (int t = 0; t < NS; ++t) cnt[t] = 0;
+            auto sweep = [&]() {
+                __syncwarp();
+                int kmax = 0, mine = 0;
+#pragma unroll
+                for (int t = 0; t < NS; ++t) {
+                    kmax = max(kmax, cnt[t]);
+                    if (t == sg) mine = cnt[t];
+                }
+                for (int k = 0; k < kmax; ++k)
+                    if (k < mine) S::template interact<kCount>(p, st, ri, buf[warp][sg][k]);
+#pragma unroll
+                for (int t = 0; t < NS; ++t) cnt[t] = 0;
+                __syncwarp();
+            };
+            for (int e = ib; e < ie; ++e) {
+                const crk_image im = lv.img[e];
+                const int jlo = lv.leaf_start[im.b];
+                const int jhi = S::kGasOnly ? jlo + lv.leaf_ngas[im.b] : lv.leaf_start[im.b + 1];
+                {
+                    const float *bb = lv.bbox + 6 * (int64_t)im.b;
+                    float gx = fmaxf(fmaxf(im.sx - uh0, ul0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+                    float gy = fmaxf(fmaxf(im.sy - uh1, ul1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+                    float gz = fmaxf(fmaxf(im.sz - uh2, ul2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+                    float cut = S::leaf_cut(p, uhm, lv.hmax[im.b]);
+                    if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+                }
+                for (int j0 = jlo; j0 < jhi; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool jv = j < jhi;
+                    Rec rj;
+                    if (jv) {
+                        rj = rec[j];
+                        S::shift(rj, im.sx, im.sy, im.sz);
+                        if constexpr (S::kTag) S::tag(rj, e - ib, j - jlo);
+                    }
+                    bool full = false;
+#pragma unroll
+                    for (int t = 0; t < NS; ++t) {
+                        bool keep = false;
+                        if (jv) {
+                            float dx = fmaxf(fmaxf(bl[t][0] - rj.x, rj.x - bh[t][0]), 0.f);
+                            float dy = fmaxf(fmaxf(bl[t][1] - rj.y, rj.y - bh[t][1]), 0.f);
+                            float dz = fmaxf(fmaxf(bl[t][2] - rj.z, rj.z - bh[t][2]), 0.f);
+                            float cut = S::box_cut(p, bhm[t], rj);
+                            keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
+                        }
+                        const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+                        if (keep) buf[warp][t][cnt[t] + __popc(m & below)] = rj;
+                        cnt[t] += __popc(m);
+                        full |= cnt[t] >= 32;
+                    }
+                    if (full) sweep();
+                }
+            }
+            sweep();
+            if (act) S::finish(p, st, ri, lv.kperm[i], i);
+            if constexpr (S::kCons) {
+                double cc[4] = {0.0, 0.0, 0.0, 0.0};
+                if (act) S::cons_terms(p, st, ri, lv.kperm[i], cc);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cc[k] += __shfl_xor_sync(CRK_FULL_MASK, cc[k], o);
+                    cons_acc[k] += cc[k];
+                }
+            }
+            if (kCount) {
+                int cn = act ? st.cnt - 1 : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+                if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+            }
+        }
+        if (S::kGasOnly)
+            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.kperm[q]);
+    }
+    if constexpr (S::kCons) {
+        if (cons_part) {
+            if (lane == 0)
+                for (int k = 0; k < 4; ++k) cons_sh[warp][k] = cons_acc[k];
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 4; ++k) {
+                    double t = 0.0;
+                    for (int w = 0; w < kWarps; ++w) t += cons_sh[w][k];
+                    cons_part[4 * (int64_t)blockIdx.x + k] = t;
+                }
+        }
+    }
+}
+
 __global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, double *__restrict__ out) {
     __shared__ double sh[256];
     for (int k = 0; k < 4; ++k) {
@@ -764,7 +931,8 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t a = blockIdx.x; a < lv.n_leaves; a += gridDim.x) {
+    __shared__ int64_t leaf_slot;
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
         const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
         const crk_image *imgs = lv.img + lv.img_start[a];
@@ -862,9 +1030,20 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
         if (!part) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
     }
     gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
+    int32_t *queue = nullptr;
+    if (ctx->persistent) {
+        queue = (int32_t *)crk_scratch(ctx, 17, 64);
+        if (!queue) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
+        CRK_CUDA(ctx, cudaMemsetAsync(queue, 0, sizeof(int32_t), ctx->stream));
+    }
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
-               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves};
+               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue};
+    if (queue) {
+        // persistent grid: resident blocks on every SM (4 blocks of 128 threads per SM is the design point)
+        int64_t g = (int64_t)ctx->num_sms * 4;
+        if (g < grid) grid = g;
+    }
     if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
     const crk_nlist &nls = gas_pairs ? lv->gas_lists : lv->grav_lists;
     const bool lists = nls.list && ctx->variant[kernel_id] == CRK_VARIANT_LISTS;
@@ -874,6 +1053,16 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
             list_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
         else
             list_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
+    } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
+        if (p.count)
+            pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        else
+            pair_kernel_sub<S, 16, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+    } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES8) {
+        if (p.count)
+            pair_kernel_sub<S, 8, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        else
+            pair_kernel_sub<S, 8, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
     } else if (p.count) {
         pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
     } else {
@@ -980,7 +1169,7 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     if (rc) return rc;
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
                kGas ? lv->himg_start : lv->gimg_start, kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg,
-               nl};
+               nl, nullptr};
     typename LS::Rec *rec = (typename LS::Rec *)crk_scratch(ctx, 4, sizeof(typename LS::Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
     const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
@@ -1080,7 +1269,7 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     // every record is rewritten before it is read, so nothing needs clearing
     gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm, lv->gimg_start, lv->gimg_cnt,
-               lv->gimg, lv->n_leaves};
+               lv->gimg, lv->n_leaves, nullptr};
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {

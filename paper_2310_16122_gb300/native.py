@@ -24,6 +24,8 @@ NOALLOC_MAX_PARTICLES = 1 << 21
 KERNELS = {"geometry": 0, "corrections": 1, "hydro": 2, "gravity": 3, "gravity_adjoint": 4, "geometry_adjoint": 5}
 VARIANT_LISTS = 0
 VARIANT_TILES = 1
+VARIANT_TILES16 = 2
+VARIANT_TILES8 = 3
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
                 -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT", -7: "CRK_ETOOLARGE"}
 
@@ -53,6 +55,19 @@ class crk_hydro_params(ctypes.Structure):
                 ("eta2", ctypes.c_float)]
 
 
+class crk_batch(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("species", ctypes.c_void_p), ("n", ctypes.c_int64), ("nbox", ctypes.c_int),
+                ("box_start", ctypes.POINTER(ctypes.c_int64)), ("box_side", ctypes.POINTER(ctypes.c_float))]
+
+
+class crk_step_io(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in (
+        "m", "v3", "u", "V", "rho", "A", "B", "gradA", "gradB", "dvdt3", "dudt", "conservation", "a3", "abar3",
+        "gx3_grav", "gm_grav", "rhobar", "Vbar", "gx3_geom", "gm_geom", "scratch3", "scratch1", "n_singular",
+        "pair_count")]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -67,8 +82,11 @@ SIGNATURES = {
     "crk_launch_count": [_P, ctypes.POINTER(_I64)],
     "crk_set_trace": [_P, _I],
     "crk_set_variant": [_P, _I, _I],
+    "crk_set_persistent": [_P, _I],
     "crk_get_variant": [_P, _I, ctypes.POINTER(_I)],
     "crk_build_leaves": [_P, ctypes.POINTER(crk_particles), _P, ctypes.POINTER(crk_leaf_params), ctypes.POINTER(_P)],
+    "crk_build_leaves_batch": [_P, ctypes.POINTER(crk_batch), _P, ctypes.POINTER(crk_leaf_params),
+                               ctypes.POINTER(_P)],
     "crk_leaves_info": [_P, ctypes.POINTER(_I64)],
     "crk_leaves_export": [_P, _P, _P, _P, _P, _P, _P, _P],
     "crk_leaves_free": [_P, _P],
@@ -79,8 +97,16 @@ SIGNATURES = {
     "grav_short_adjoint": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P, _P],
     "crk_geometry_adjoint": [_P, _P, _P, _P, _P, _P, _P, _P],
     "grav_short_noalloc": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P],
+    "crk_step": [_P, _P, ctypes.POINTER(crk_grav_params), ctypes.POINTER(crk_hydro_params),
+                 ctypes.POINTER(crk_step_io)],
+    "crk_step_graph_create": [_P, _P, ctypes.POINTER(crk_grav_params), ctypes.POINTER(crk_hydro_params),
+                              ctypes.POINTER(crk_step_io), ctypes.POINTER(_P)],
+    "crk_graph_launch": [_P],
+    "crk_graph_destroy": [_P],
+    "crk_tune": [_P, _P, ctypes.POINTER(crk_grav_params), ctypes.POINTER(crk_hydro_params),
+                 ctypes.POINTER(crk_step_io), _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)],
 }
-_VOID = {"crk_destroy", "crk_leaves_free"}
+_VOID = {"crk_destroy", "crk_leaves_free", "crk_graph_destroy"}
 _STR = {"crk_last_error", "crk_version"}
 
 _lib = None

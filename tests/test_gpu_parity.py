@@ -145,7 +145,11 @@ def test_error_statuses(api, ctx):
     assert e.value.status == N.CRK_EBOX  # 2 h_max >= box/2
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
+VARIANTS = [0, 1, 2, 3]
+VARIANT_IDS = ["lists", "tiles", "tiles16", "tiles8"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("name", ["tiny_mesh", "clustered24", "random1000_leaf7", "random777_mesh3"])
 def test_gravity_parity(api, ctx, name, variant):
     b = box_of(name)
@@ -172,7 +176,7 @@ def set_gas_variant(ctx, variant):
         ctx.set_variant(k, (1 if k.startswith("gravity") else 0) if variant is None else variant)
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("name", ["tiny_mesh", "clustered12", "clustered24", "random777_mesh3"])
 def test_hydro_chain_parity(api, ctx, name, variant):
     b = box_of(name)
@@ -214,7 +218,7 @@ def test_hydro_chain_parity(api, ctx, name, variant):
     assert int(out["count_geom"].item()) == int(out["count_hydro"].item())
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["lists", "tiles"])
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("name", ["clustered12", "clustered24"])
 def test_adjoint_parity(api, ctx, name, variant):
     b = box_of(name)
