@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trace-leaves", action="store_true", help="after timing, print leaf-build phase times")
     ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants")
+    ap.add_argument("--batched-boxes", type=int, default=96)
     return ap.parse_args()
 
 
@@ -119,6 +122,19 @@ class Clocks:
                     reasons.add(k)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def aggregate(ms, pairs, dist=None, device="cpu"):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of every rank's pairs."""
+    if dist is None:
+        return float(ms), float(pairs)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(p[0])
 
 
 def run_reference(args, rank):
@@ -238,6 +254,14 @@ def main():
         mark(7)
         return dict(lv=lv, cons=cons, cg=cg, ch=ch, ca=ca, ns=ns, leaves=lv.n_leaves)
 
+    tuning = None
+    if not args.no_tune and not args.variants:
+        # untimed: the autotuner picks each kernel's variant on this workload's leaves
+        lv_t = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+        io_t = api.StepIO(ctx, db)
+        tuning = api.autotune(ctx, lv_t, db, io_t, reps=2)
+        del lv_t, io_t
+        variants = {k: ctx.get_variant(k) for k in native.KERNELS}
     # counting step (untimed): pair counts of every kernel
     r = step(count=True)
     torch.cuda.synchronize()
@@ -274,14 +298,7 @@ def main():
         for i, s in enumerate(STAGES):
             per_stage[s] += ev[k][i].elapsed_time(ev[k][i + 1])
     per_stage = {s: v / args.steps for s, v in per_stage.items()}
-    t_max = ms
-    total_pairs = pairs_step * args.steps
-    if dist:
-        tt = torch.tensor([ms, float(total_pairs)], dtype=torch.float64, device=f"cuda:{local}")
-        tm = tt.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_max, total_pairs = float(tm[0]), float(tt[1])
+    t_max, total_pairs = aggregate(ms, pairs_step * args.steps, dist, f"cuda:{local}")
     value = total_pairs / (t_max * 1e-3)
 
     if args.trace_leaves:
@@ -344,10 +361,16 @@ def main():
                        "l2": "inputs (~%.1f GB) larger than L2 (129 MB)" % (h2d / 1e9)},
             "pairs_per_step": pairs, "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
             "variants": variants,
+            "autotune_ms": tuning["ms"] if tuning else None,
             "kernels_tflops": all_flops / (kern_ms * 1e-3) / 1e12,
             "roofline": roofline, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 32,
                     "ms_per_step": e2e_ms}}
+    if not args.no_batched:
+        try:
+            line["batched_vs_plain"] = batched_vs_plain(args, local, dist)
+        except Exception as e:  # reported, never silent
+            line["batched_vs_plain"] = {"error": repr(e)}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(box)
@@ -357,6 +380,83 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def batched_vs_plain(args, local, dist):
+    """The many-box workload (96 boxes, sides log-uniform in [12, 48]) as per-box plain launches
+    and as one batched form; same kernels, same pairs, same accuracy."""
+    import torch
+
+    from paper_2310_16122_gb300 import api, workloads as W
+
+    t_gen = time.perf_counter()
+    boxes = W.batched(args.batched_boxes)
+    t_gen = time.perf_counter() - t_gen
+    ctx = api.Context(local)
+    dbs = [api.DeviceBox(b, device=f"cuda:{local}") for b in boxes]
+    ios = [api.StepIO(ctx, db) for db in dbs]
+    dbt = api.DeviceBatch(boxes, device=f"cuda:{local}")
+    iot = api.StepIO(ctx, dbt)
+    stream = ctx.stream
+
+    def plain_step(count=False):
+        for db, io in zip(dbs, ios):
+            lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+            api.step(ctx, lv, db, io, count)
+
+    def batched_step(count=False):
+        lv = api.build_leaves_batch(ctx, dbt)
+        api.step(ctx, lv, dbt, iot, count)
+
+    def pairs(c):
+        c = c.cpu().numpy()
+        return int(2 * (c[0] + c[1] + c[2]))
+
+    plain_step(count=True)
+    batched_step(count=True)
+    torch.cuda.synchronize()
+    p_plain = sum(pairs(io.pair_count) for io in ios)
+    p_batch = pairs(iot.pair_count)
+    res = {}
+    for name, fn in (("plain", plain_step), ("batched", batched_step)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / args.steps
+    # kernel part only (leaves built once): eager crk_step vs CUDA-graph replay on a side stream
+    s2 = torch.cuda.Stream(device=f"cuda:{local}")
+    with torch.cuda.stream(s2):
+        gctx = api.Context(local, stream=s2)
+        lv = api.build_leaves_batch(gctx, dbt)
+        g = api.StepGraph(gctx, lv, dbt, iot)
+        for label, fn in (("eager", lambda: api.step(gctx, lv, dbt, iot)), ("graph", g.launch)):
+            for _ in range(args.warmup):
+                fn()
+            s2.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s2)
+            for _ in range(args.steps):
+                fn()
+            e1.record(s2)
+            s2.synchronize()
+            res["kernels_" + label] = e0.elapsed_time(e1) / args.steps
+        g.close()
+    n_total = sum(b.n for b in boxes)
+    return {"workload": f"{len(boxes)} boxes, sides 12-48 log-uniform, {n_total} particles",
+            "pairs_per_step": p_batch, "pairs_equal": p_plain == p_batch,
+            "plain": {"ms_per_step": res["plain"], "value": p_plain / (res["plain"] * 1e-3),
+                      "form": "per box: leaf build + crk_step (separate launches)"},
+            "batched": {"ms_per_step": res["batched"], "value": p_batch / (res["batched"] * 1e-3),
+                        "form": "one multi-box leaf build + one crk_step over all boxes"},
+            "speedup": res["plain"] / res["batched"],
+            "kernels_ms": {"eager": res["kernels_eager"], "graph": res["kernels_graph"]},
+            "generation_s": t_gen}
 
 
 def ctypes_launches(ctx):

@@ -349,3 +349,35 @@ def tune(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, reps: int = 3) -
                                int(reps), ms, best))
     names = sorted(N.KERNELS, key=N.KERNELS.get)
     return {k: (int(best[i]), [float(ms[4 * i + v]) for v in range(4)]) for i, k in enumerate(names)}
+
+
+def autotune(ctx: Context, lv: Leaves, db, io: StepIO, cache_path: str | None = None, reps: int = 3) -> dict:
+    """Pick every kernel's variant with crk_tune, remembering choices in a JSON cache.
+
+    The cache key is the GPU name and the shape of the leaf structure (particles, leaves,
+    image entries); a hit applies the stored variants without timing anything.
+    """
+    import json
+    import os
+
+    key = (f"{torch.cuda.get_device_name(ctx.device)}|n={lv.n}|leaves={lv.n_leaves}|"
+           f"gimg={lv.n_grav_images}|himg={lv.n_hydro_images}")
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        for k, v in cache[key]["variants"].items():
+            ctx.set_variant(k, int(v))
+        return dict(cache[key], cached=True)
+    res = tune(ctx, lv, db, io, reps)
+    entry = {"variants": {k: b for k, (b, _) in res.items()}, "ms": {k: ms for k, (_, ms) in res.items()}}
+    if cache_path:
+        cache[key] = entry
+        tmp = cache_path + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    return dict(entry, cached=False)

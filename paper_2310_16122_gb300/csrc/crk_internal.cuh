@@ -87,6 +87,8 @@ struct crk_leaves {
     float *bbox = nullptr;          // [n_leaves][6]: lo xyz, hi xyz
     float *hmax = nullptr;          // [n_leaves]
     float4 *pos = nullptr;          // [n] kernel order: leaf-relative x, y, z and h (gas) or 0
+    int32_t *kperm_g = nullptr;     // gravity kernel order (species mixed) -> original index
+    float4 *pos_g = nullptr;        // [n] gravity kernel order: leaf-relative x, y, z and h or 0
     // leaf-pair lists: per i-leaf a, entries [start[a], start[a] + count[a]) in
     // ascending j-leaf order (leaves may be laid out in any order)
     int32_t *gimg_start = nullptr, *gimg_cnt = nullptr;  // gravity images

@@ -271,7 +271,8 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
                                  const uint8_t *__restrict__ sp, const float *__restrict__ h,
                                  int32_t *__restrict__ perm, int32_t *__restrict__ kperm,
                                  int32_t *__restrict__ leaf_ngas, float *__restrict__ bbox,
-                                 float *__restrict__ hmax, float4 *__restrict__ pos, int32_t *__restrict__ err) {
+                                 float *__restrict__ hmax, float4 *__restrict__ pos, int32_t *__restrict__ kperm_g,
+                                 float4 *__restrict__ pos_g, int32_t *__restrict__ err) {
     __shared__ uint64_t key[kMaxLeafCap];
     __shared__ float red[6][32];
     __shared__ int ngs[32];
@@ -334,8 +335,9 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
     const float ox = red[0][0], oy = red[1][0], oz = red[2][0];
     const float ext = fmaxf(fmaxf(red[3][0] - ox, red[4][0] - oy), fmaxf(red[5][0] - oz, 1e-30f));
     const float sc = 1023.0f / ext;
-    // canonical ranks, and the Z-order key of each member (kept in registers)
-    uint64_t zkey[kMaxLeafCap / 128];
+    // canonical ranks, and the Z-order keys of each member (kept in registers):
+    // zkey with the species on top (gas first), gkey without (gravity order)
+    uint64_t zkey[kMaxLeafCap / 128], gkey[kMaxLeafCap / 128];
     int nk = 0;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         uint64_t kt = key[t];
@@ -346,6 +348,7 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
         uint32_t mx3 = spread10((uint32_t)fminf((x[id] - ox) * sc, 1023.0f)) |
                        (spread10((uint32_t)fminf((y[id] - oy) * sc, 1023.0f)) << 1) |
                        (spread10((uint32_t)fminf((z[id] - oz) * sc, 1023.0f)) << 2);
+        gkey[nk] = ((uint64_t)mx3 << 32) | (uint32_t)id;
         zkey[nk++] = ((uint64_t)(sp[id] != 0) << 62) | ((uint64_t)mx3 << 32) | (uint32_t)id;
     }
     __syncthreads();
@@ -359,6 +362,18 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
         int32_t id = (int32_t)(uint32_t)kt;
         kperm[lo + r] = id;
         pos[lo + r] = make_float4(x[id] - ox, y[id] - oy, z[id] - oz, sp[id] == 0 ? h[id] : 0.0f);
+    }
+    __syncthreads();
+    nk = 0;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) key[t] = gkey[nk++];
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        uint64_t kt = key[t];
+        int r = 0;
+        for (int u = 0; u < cnt; ++u) r += key[u] < kt;
+        int32_t id = (int32_t)(uint32_t)kt;
+        kperm_g[lo + r] = id;
+        pos_g[lo + r] = make_float4(x[id] - ox, y[id] - oy, z[id] - oz, sp[id] == 0 ? h[id] : 0.0f);
     }
 }
 
@@ -1064,10 +1079,13 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         ALLOC(lv->bbox, float, 6 * nl);
         ALLOC(lv->hmax, float, nl);
         ALLOC(lv->pos, float4, n);
+        ALLOC(lv->kperm_g, int32_t, n);
+        ALLOC(lv->pos_g, float4, n);
         if (nl > 0) {
             leaf_data_kernel<<<(unsigned)nl, 128, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
                                                            p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
-                                                           lv->bbox, lv->hmax, lv->pos, flags + 4);
+                                                           lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g,
+                                                           flags + 4);
             ++ctx->launches;
         }
         KCHECK("leaf data");

@@ -22,6 +22,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCap = 64;                     // per-warp candidate buffer
+constexpr int kListImgCap = 512;             // image table of one i-leaf staged in shared memory
 constexpr float kSigmaW = 0.61548156588532f;  // 495 / (256 pi), Wendland C4 3-D normalisation
 
 struct LeafView {
@@ -932,10 +933,23 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
     __shared__ int64_t leaf_slot;
+    // the i-leaf's image table in shared memory: first j of the image's leaf
+    // (as a float bit pattern in w) and the shift into the i frame
+    __shared__ float4 itab[kListImgCap];
     for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
         const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
         const crk_image *imgs = lv.img + lv.img_start[a];
+        const int nimg = lv.img_cnt[a];
+        const bool staged = nimg <= kListImgCap;
+        if (staged) {
+            __syncthreads();  // the previous leaf's table is no longer read
+            for (int t = threadIdx.x; t < nimg; t += kThreads) {
+                const crk_image im = imgs[t];
+                itab[t] = make_float4(im.sx, im.sy, im.sz, __int_as_float(lv.leaf_start[im.b]));
+            }
+            __syncthreads();
+        }
         for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
             const int q = (g0 - lo) >> 5;
             const int64_t grp = gl.gstart[a] + q;
@@ -946,12 +960,28 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
             typename S::I st;
             S::init(p, st, ri, a, q, lane);
             const int c = act ? gl.cnt[i] : 0;
-            for (int k = 0; k < c; ++k) {
+            // entry k -> shifted record of j (shared-memory table, or the global image list for
+            // leaves with more images than the table holds)
+            auto fetch = [&](int k) -> Rec {
                 const uint32_t code = __ldg(L + (size_t)k * 32);
-                const crk_image im = imgs[code >> 10];
-                Rec rj = rec[lv.leaf_start[im.b] + (int)(code & 1023u)];
-                S::shift(rj, im.sx, im.sy, im.sz);
-                S::template interact<kCount>(p, st, ri, rj);
+                float4 t;
+                if (staged) {
+                    t = itab[code >> 10];
+                } else {
+                    const crk_image im = imgs[code >> 10];
+                    t = make_float4(im.sx, im.sy, im.sz, __int_as_float(lv.leaf_start[im.b]));
+                }
+                Rec r = rec[__float_as_int(t.w) + (int)(code & 1023u)];
+                S::shift(r, t.x, t.y, t.z);
+                return r;
+            };
+            if (c > 0) {
+                Rec nxt = fetch(0);
+                for (int k = 0; k < c; ++k) {
+                    const Rec rj = nxt;
+                    if (k + 1 < c) nxt = fetch(k + 1);  // in flight while rj is evaluated
+                    S::template interact<kCount>(p, st, ri, rj);
+                }
             }
             if (act) S::finish(p, st, ri, lv.kperm[i], i);
             if constexpr (S::kCons) {
@@ -1029,14 +1059,16 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
         part = (double *)crk_scratch(ctx, 5, sizeof(double) * 4 * (size_t)grid);
         if (!part) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
     }
-    gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
+    const float4 *kpos = gas_pairs ? lv->pos : lv->pos_g;          // gravity: species-mixed kernel order
+    const int32_t *kperm = gas_pairs ? lv->kperm : lv->kperm_g;
+    gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, kpos, kperm, p, rec);
     int32_t *queue = nullptr;
     if (ctx->persistent) {
         queue = (int32_t *)crk_scratch(ctx, 17, 64);
         if (!queue) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
         CRK_CUDA(ctx, cudaMemsetAsync(queue, 0, sizeof(int32_t), ctx->stream));
     }
-    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kpos, kperm,
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
                gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue};
     if (queue) {
@@ -1167,13 +1199,13 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     ++ctx->launches;
     int rc = crk_exclusive_scan_i32(ctx, ng, gstart, nl + 1, tot);
     if (rc) return rc;
-    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm,
-               kGas ? lv->himg_start : lv->gimg_start, kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg,
-               nl, nullptr};
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kGas ? lv->pos : lv->pos_g,
+               kGas ? lv->kperm : lv->kperm_g, kGas ? lv->himg_start : lv->gimg_start,
+               kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg, nl, nullptr};
     typename LS::Rec *rec = (typename LS::Rec *)crk_scratch(ctx, 4, sizeof(typename LS::Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
     const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
-    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, lv->pos, lv->kperm, ListP{}, rec);
+    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec);
     ListP pc{nullptr, gstart, nullptr, cnt, 0, rc2, n, nullptr};
     pair_kernel<LS, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pc, rec, nullptr);
     ctx->launches += 2;
@@ -1267,9 +1299,9 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     p.n = n;
     p.count = nullptr;
     // every record is rewritten before it is read, so nothing needs clearing
-    gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos, lv->kperm, p, rec);
-    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos, lv->kperm, lv->gimg_start, lv->gimg_cnt,
-               lv->gimg, lv->n_leaves, nullptr};
+    gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos_g, lv->kperm_g, p, rec);
+    LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos_g, lv->kperm_g, lv->gimg_start,
+               lv->gimg_cnt, lv->gimg, lv->n_leaves, nullptr};
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {

@@ -158,5 +158,7 @@ def test_persistent_launch_matches(setup):
     torch.cuda.synchronize()
     for a, b in zip((io.acc, io.dv, io.du, io.gx_grav, io.gx_geom), ref):
         assert torch.equal(a, b)
-    # conservation partials are summed per block: same value up to FP64 reassociation
-    assert torch.allclose(io.cons, ref[5], rtol=1e-9, atol=1e-12 * float(ref[5].abs().max()))
+    # the conservation partials are grouped per block, so the FP64 sums agree up to reassociation;
+    # their momentum components are rounding residue near zero, so compare against the summed terms
+    scale = float((dbt.m[None, :] * io.dv.abs()).sum()) + float((dbt.m * io.du.abs()).sum())
+    assert float((io.cons - ref[5]).abs().max()) <= 1e-12 * scale
