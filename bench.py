@@ -232,27 +232,19 @@ def main():
     gas = (db.species == 0).float()
     stream = ctx.stream
 
-    def step(events=None, count=False):
-        def mark(k):
-            if events is not None:
-                events[k].record(stream)
+    # the step's outputs: accelerations, energy rates and both adjoints; the intermediates
+    # (V, rho, A, B, dA, dB) stay in the library's kernel order
+    io = api.StepIO(ctx, db, outputs=False)
+    lev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(max(args.steps, 1))]
 
-        mark(0)
+    def step(k=None, count=False):
+        if k is not None:
+            lev[k][0].record(stream)
         lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
-        mark(1)
-        V, rho, cg = api.geometry(ctx, lv, db.m, count)
-        mark(2)
-        A, B, gA, gB, ns = api.corrections(ctx, lv, V)
-        mark(3)
-        dv, du, cons, ch = api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, count)
-        mark(4)
-        a, ca = api.grav_short(ctx, lv, db.gp, db.m, count)
-        mark(5)
-        gx, gm = api.grav_short_adjoint(ctx, lv, db.gp, db.m, 2.0 * a)
-        mark(6)
-        gx2, gm2 = api.geometry_adjoint(ctx, lv, db.m, V, gas)
-        mark(7)
-        return dict(lv=lv, cons=cons, cg=cg, ch=ch, ca=ca, ns=ns, leaves=lv.n_leaves)
+        if k is not None:
+            lev[k][1].record(stream)
+        api.step(ctx, lv, db, io, count)
+        return lv
 
     tuning = None
     if not args.no_tune and not args.variants:
@@ -263,20 +255,19 @@ def main():
         del lv_t, io_t
         variants = {k: ctx.get_variant(k) for k in native.KERNELS}
     # counting step (untimed): pair counts of every kernel
-    r = step(count=True)
+    lv_c = step(count=True)
+    n_leaves = lv_c.n_leaves
+    del lv_c
     torch.cuda.synchronize()
-    p_h = int(r["ch"].item())
-    p_g = int(r["ca"].item())
-    pairs = {"geometry": int(r["cg"].item()), "corrections": p_h, "hydro": p_h, "gravity": p_g,
-             "gravity_adjoint": p_g, "geometry_adjoint": p_h}
+    c = io.pair_count.cpu().numpy()
+    pairs = {"geometry": int(c[0]), "corrections": int(c[1]), "hydro": int(c[1]), "gravity": int(c[2]),
+             "gravity_adjoint": int(c[2]), "geometry_adjoint": int(c[0])}
     pairs_step = sum(pairs.values())
-    n_leaves = r["leaves"]
-    del r
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     launches0 = ctypes_launches(ctx)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    ctx.check(native.lib().crk_step_profile(ctx.handle, args.steps))
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(local)
     if dist:
@@ -285,7 +276,7 @@ def main():
     clocks.start()
     t0.record(stream)
     for k in range(args.steps):
-        step(ev[k])
+        step(k)
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -293,11 +284,15 @@ def main():
         dist.barrier()
     launches = ctypes_launches(ctx) - launches0
     ms = t0.elapsed_time(t1)
-    per_stage = {s: 0.0 for s in STAGES}
-    for k in range(args.steps):
-        for i, s in enumerate(STAGES):
-            per_stage[s] += ev[k][i].elapsed_time(ev[k][i + 1])
-    per_stage = {s: v / args.steps for s, v in per_stage.items()}
+    import ctypes as _ct
+    prof = (_ct.c_float * 7)()
+    nprof = _ct.c_int(0)
+    ctx.check(native.lib().crk_step_profile_read(ctx.handle, prof, _ct.byref(nprof)))
+    ctx.check(native.lib().crk_step_profile(ctx.handle, 0))
+    per_stage = {"leaves": sum(lev[k][0].elapsed_time(lev[k][1]) for k in range(args.steps)) / args.steps}
+    for i, s_ in enumerate(STAGES[1:]):
+        per_stage[s_] = float(prof[i])
+    per_stage["outputs"] = float(prof[6])
     t_max, total_pairs = aggregate(ms, pairs_step * args.steps, dist, f"cuda:{local}")
     value = total_pairs / (t_max * 1e-3)
 
@@ -317,8 +312,8 @@ def main():
     for _ in range(e2e_steps):
         for k, t in host.items():
             getattr(db, k).copy_(t, non_blocking=True)
-        res = step()
-        out_host.copy_(res["cons"], non_blocking=True)
+        step()
+        out_host.copy_(io.cons, non_blocking=True)
     te1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = te0.elapsed_time(te1) / e2e_steps

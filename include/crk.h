@@ -118,6 +118,8 @@ int crk_set_trace(crk_ctx *ctx, int on);
 #define CRK_VARIANT_TILES 1
 #define CRK_VARIANT_TILES16 2 /* tiles with two 16-particle i-groups per warp */
 #define CRK_VARIANT_TILES8 3  /* tiles with four 8-particle i-groups per warp */
+#define CRK_VARIANT_RING16 4  /* two 16-particle i-groups per warp, balanced ring-buffer sweeps
+                                 (every kernel but hydro, which falls back to TILES) */
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
 /* Launch mode of the pair kernels: 0 (default) one block per i-leaf; 1
  * persistent: a grid of 4 blocks per SM whose blocks take i-leaves from an
@@ -225,13 +227,15 @@ int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, con
                          const float *Vbar, float *gx3, float *gm);
 
 /* One whole step of the path on one set of leaves, in this order: geometry,
- * corrections, hydro, gravity, gravity adjoint, geometry adjoint.  All arrays
- * are caller-owned device arrays laid out as for the single calls.  The
- * adjoint cotangents default to the loss sum |a|^2 + sum_gas rho: when abar3
- * (rhobar) is NULL the step writes 2a into scratch3 (3n floats) and the gas
- * indicator into scratch1 (n floats), which the caller then provides.
- * pair_count (device int64[3], may be NULL) receives the geometry, hydro and
- * gravity pair counts; n_singular and conservation as for the single calls. */
+ * corrections, hydro, gravity, gravity adjoint, geometry adjoint.  Inputs m,
+ * v3, u (caller order, as for the single calls).  The intermediates stay in
+ * the library's kernel order (coalesced, no scatter/gather round trips);
+ * every output pointer may be NULL, and those given receive the values in the
+ * caller's order and layout.  The adjoint cotangents default to the loss
+ * sum |a|^2 + sum_gas rho (abar3 = NULL: 2a; rhobar = NULL: 1 on gas); Vbar
+ * may be NULL.  pair_count (device int64[3], may be NULL) receives the
+ * geometry, hydro and gravity pair counts; n_singular and conservation as for
+ * the single calls. */
 typedef struct {
     const float *m, *v3, *u;                /* inputs */
     float *V, *rho, *A, *B, *gradA, *gradB; /* geometry, corrections */
@@ -242,13 +246,22 @@ typedef struct {
     float *gx3_grav, *gm_grav;              /* gravity adjoint */
     const float *rhobar, *Vbar;             /* geometry cotangents; rhobar NULL = 1 on gas; Vbar may be NULL */
     float *gx3_geom, *gm_geom;              /* geometry adjoint */
-    float *scratch3, *scratch1;             /* needed when abar3 / rhobar are NULL */
     int32_t *n_singular;                    /* may be NULL */
     int64_t *pair_count;                    /* int64[3], may be NULL */
 } crk_step_io;
 
 int crk_step(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io);
+
+/* Per-stage timing of crk_step.  crk_step_profile(ctx, k) creates 8 CUDA
+ * events for each of the next k steps (0 turns profiling off); those steps
+ * record them on the context stream: start, after geometry, corrections,
+ * hydro, gravity, gravity adjoint, geometry adjoint, and after the outputs.
+ * crk_step_profile_read waits for the last recorded event, returns the mean
+ * ms of the 7 intervals over the recorded steps (the first interval includes
+ * the input permutation, the sixth the cotangent kernel) and starts over. */
+int crk_step_profile(crk_ctx *ctx, int max_steps);
+int crk_step_profile_read(crk_ctx *ctx, float ms[7], int *steps);
 
 /* CUDA graph of crk_step (the batched form: one graph launch replays every
  * kernel of the step).  Creation runs one uncaptured step (sizing the scratch
@@ -264,8 +277,9 @@ void crk_graph_destroy(crk_graph *g);
 
 /* Autotuner: times every variant of every kernel on these leaves (best of
  * reps after a warm-up, CUDA events on the context stream), keeps the fastest
- * in the context, and reports ms_out[6 * 4] (kernel-major; -1 = not available)
- * and best_out[6] (host arrays, may be NULL).  Runs one crk_step first. */
+ * in the context, and reports ms_out[6 * 5] (kernel-major; -1 = not available)
+ * and best_out[6] (host arrays, may be NULL).  Runs one crk_step first; every
+ * output array of io must be given (they are overwritten while timing). */
 int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io, int reps, float *ms_out, int *best_out);
 

@@ -285,18 +285,26 @@ def forward(ctx: Context, db: DeviceBox, count=False):
 # ------------------------------------------------------------------- whole step
 
 class StepIO:
-    """Device arrays of one whole step (crk_step): inputs from a DeviceBox, outputs allocated here."""
+    """Device arrays of one whole step (crk_step): inputs from a DeviceBox, outputs allocated here.
 
-    def __init__(self, ctx: Context, db: "DeviceBox"):
+    outputs=False allocates only what a step must return to a caller that wants the
+    accelerations, energy rates and gradients (dv, du, a, both adjoints); the
+    intermediates (V, rho, A, B, dA, dB) then stay inside the library.
+    """
+
+    def __init__(self, ctx: Context, db, outputs: bool = True):
         n = db.n
         e = ctx.empty
         self.db = db
-        self.V, self.rho, self.A, self.B, self.gA, self.gB = e(n), e(n), e(n), e(3, n), e(3, n), e(9, n)
+        self.full = outputs
+        if outputs:
+            self.V, self.rho, self.A, self.B, self.gA, self.gB = e(n), e(n), e(n), e(3, n), e(3, n), e(9, n)
+        else:
+            self.V = self.rho = self.A = self.B = self.gA = self.gB = None
         self.dv, self.du = e(3, n), e(n)
         self.cons = torch.zeros(4, dtype=torch.float64, device=ctx.device)
         self.acc = e(3, n)
         self.gx_grav, self.gm_grav, self.gx_geom, self.gm_geom = e(3, n), e(n), e(3, n), e(n)
-        self.scratch3, self.scratch1 = e(3, n), e(n)
         self.n_singular = torch.zeros(1, dtype=torch.int32, device=ctx.device)
         self.pair_count = torch.zeros(3, dtype=torch.int64, device=ctx.device)
 
@@ -304,8 +312,8 @@ class StepIO:
         d, P = self.db, lambda t: t.data_ptr() if t is not None else None
         return N.crk_step_io(P(d.m), P(d.v3), P(d.u), P(self.V), P(self.rho), P(self.A), P(self.B), P(self.gA),
                              P(self.gB), P(self.dv), P(self.du), P(self.cons), P(self.acc), None, P(self.gx_grav),
-                             P(self.gm_grav), None, None, P(self.gx_geom), P(self.gm_geom), P(self.scratch3),
-                             P(self.scratch1), P(self.n_singular), P(self.pair_count) if count else None)
+                             P(self.gm_grav), None, None, P(self.gx_geom), P(self.gm_geom), P(self.n_singular),
+                             P(self.pair_count) if count else None)
 
 
 def step(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, count: bool = False) -> None:
@@ -343,12 +351,13 @@ class StepGraph:
 def tune(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, reps: int = 3) -> dict:
     """Autotune the kernel variants on these leaves; returns {kernel: (best, [ms per variant])}."""
     gp, hp, c = db.gp.c(), db.hp.c(), io.c(False)
-    ms = (ctypes.c_float * 24)()
+    ms = (ctypes.c_float * (6 * N.N_VARIANTS))()
     best = (ctypes.c_int * 6)()
     ctx.check(N.lib().crk_tune(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp), ctypes.byref(c),
                                int(reps), ms, best))
     names = sorted(N.KERNELS, key=N.KERNELS.get)
-    return {k: (int(best[i]), [float(ms[4 * i + v]) for v in range(4)]) for i, k in enumerate(names)}
+    return {k: (int(best[i]), [float(ms[N.N_VARIANTS * i + v]) for v in range(N.N_VARIANTS)])
+            for i, k in enumerate(names)}
 
 
 def autotune(ctx: Context, lv: Leaves, db, io: StepIO, cache_path: str | None = None, reps: int = 3) -> dict:

@@ -111,6 +111,7 @@ void crk_destroy(crk_ctx *ctx) {
         if (ctx->slot[s]) cudaFree(ctx->slot[s]);
     for (auto &b : ctx->block_cache) cudaFree(b.first);
     crk_rcb_shape_free(ctx);
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -127,7 +128,7 @@ const char *crk_version(void) { return "libcrk 1 sm_103a"; }
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant) {
     if (!ctx) return CRK_EINVAL;
     if (kernel < 0 || kernel > CRK_K_GEOMETRY_ADJOINT) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
-    if (variant < CRK_VARIANT_LISTS || variant > CRK_VARIANT_TILES8)
+    if (variant < CRK_VARIANT_LISTS || variant > CRK_VARIANT_RING16)
         return crk_fail(ctx, CRK_EINVAL, "variant %d not available for kernel %d", variant, kernel);
     ctx->variant[kernel] = variant;
     return CRK_OK;

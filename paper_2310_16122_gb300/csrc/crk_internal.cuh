@@ -57,6 +57,9 @@ struct crk_ctx {
     crk_rcb_shape *rcb = nullptr;
     bool trace = false;  // CRK_TRACE=1: synchronise and print phase times of the leaf build
     bool persistent = false;  // pair kernels: persistent grid + atomic leaf queue
+    // crk_step profiling: 8 events per step (start, after each of the 6 stages, end)
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max = 0, prof_used = 0;
     // kernel variants (autotuner choices), indexed by CRK_K_*; 0 = default
     int variant[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
@@ -88,6 +91,8 @@ struct crk_leaves {
     float *hmax = nullptr;          // [n_leaves]
     float4 *pos = nullptr;          // [n] kernel order: leaf-relative x, y, z and h (gas) or 0
     int32_t *kperm_g = nullptr;     // gravity kernel order (species mixed) -> original index
+    int32_t *kinv = nullptr;        // original index -> kernel order position (inverse of kperm)
+    int32_t *kinv_g = nullptr;      // original index -> gravity kernel order position
     float4 *pos_g = nullptr;        // [n] gravity kernel order: leaf-relative x, y, z and h or 0
     // leaf-pair lists: per i-leaf a, entries [start[a], start[a] + count[a]) in
     // ascending j-leaf order (leaves may be laid out in any order)
@@ -115,6 +120,10 @@ void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes);
 void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes);
 void crk_rcb_shape_free(crk_ctx *ctx);
 int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas);
+int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+                   const crk_step_io *io);
+// records event k (0..7) of the current profiled step, if profiling is on
+void crk_step_mark(crk_ctx *ctx, int k);
 
 #define CRK_CUDA(ctx, call)                                          \
     do {                                                             \

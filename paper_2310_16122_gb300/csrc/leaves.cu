@@ -875,6 +875,14 @@ struct Tracer {
 };
 }  // namespace
 
+__global__ void inverse_perm_kernel(int64_t n, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                                    int32_t *__restrict__ ainv, int32_t *__restrict__ binv) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    ainv[a[q]] = (int32_t)q;
+    binv[b[q]] = (int32_t)q;
+}
+
 __global__ void init_node_of_kernel(int64_t n, const int32_t *__restrict__ box_of, const int32_t *__restrict__ seg_of_box,
                                     int32_t *__restrict__ node_of) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1081,11 +1089,17 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         ALLOC(lv->pos, float4, n);
         ALLOC(lv->kperm_g, int32_t, n);
         ALLOC(lv->pos_g, float4, n);
+        ALLOC(lv->kinv, int32_t, n);
+        ALLOC(lv->kinv_g, int32_t, n);
         if (nl > 0) {
             leaf_data_kernel<<<(unsigned)nl, 128, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
                                                            p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
                                                            lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g,
                                                            flags + 4);
+            ++ctx->launches;
+        }
+        if (n > 0) {
+            inverse_perm_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, lv->kperm, lv->kperm_g, lv->kinv, lv->kinv_g);
             ++ctx->launches;
         }
         KCHECK("leaf data");

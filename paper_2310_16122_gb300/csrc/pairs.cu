@@ -37,6 +37,7 @@ struct LeafView {
     const crk_image *img;
     int64_t n_leaves;
     int32_t *queue;  // persistent mode: next leaf to take (zeroed before launch); NULL = one block per leaf
+    int korder;      // 1: the stage's per-particle arrays are in kernel order (no permutation)
 };
 
 // Next i-leaf of this block: the grid-stride successor, or (persistent mode)
@@ -624,12 +625,12 @@ struct ListStage {
 // --------------------------------------------------------------- framework
 template <class S>
 __global__ void gather_kernel(int64_t n, const float4 *__restrict__ pos, const int32_t *__restrict__ kperm,
-                              typename S::P p, typename S::Rec *__restrict__ rec) {
+                              typename S::P p, typename S::Rec *__restrict__ rec, int korder) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const float4 ps = pos[q];
     if (S::kGasOnly && ps.w == 0.0f) return;  // dark matter (h = 0): never read by gas-pair stages
-    rec[q] = S::gather(p, kperm[q], ps);
+    rec[q] = S::gather(p, korder ? (int32_t)q : kperm[q], ps);
 }
 
 template <class S, bool kCount>
@@ -709,7 +710,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
             __syncwarp();
             for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[warp][k]);
             __syncwarp();
-            if (act) S::finish(p, st, ri, lv.kperm[i], i);
+            if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
             if constexpr (S::kCons) {
                 double c[4] = {0.0, 0.0, 0.0, 0.0};
                 if (act) S::cons_terms(p, st, ri, lv.kperm[i], c);
@@ -728,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
             }
         }
         if (S::kGasOnly)
-            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.kperm[q]);
+            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.korder ? q : lv.kperm[q]);
     }
     if constexpr (S::kCons) {
         // per-block partial in a fixed order; reduced by cons_reduce_kernel (deterministic)
@@ -863,10 +864,10 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
                 }
             }
             sweep();
-            if (act) S::finish(p, st, ri, lv.kperm[i], i);
+            if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
             if constexpr (S::kCons) {
                 double cc[4] = {0.0, 0.0, 0.0, 0.0};
-                if (act) S::cons_terms(p, st, ri, lv.kperm[i], cc);
+                if (act) S::cons_terms(p, st, ri, lv.korder ? i : lv.kperm[i], cc);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -882,7 +883,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
             }
         }
         if (S::kGasOnly)
-            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.kperm[q]);
+            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.korder ? q : lv.kperm[q]);
     }
     if constexpr (S::kCons) {
         if (cons_part) {
@@ -896,6 +897,128 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
                     cons_part[4 * (int64_t)blockIdx.x + k] = t;
                 }
         }
+    }
+}
+
+
+// Two 16-particle i-groups per warp with balanced sweeps: each half-warp has
+// a ring buffer of candidates; a sweep consumes the same number of entries
+// from both rings (as many as both have ready), so neither half idles while
+// the other works.  Only when a ring is about to overflow, and at the end,
+// is a sweep unbalanced.
+constexpr int kRing = 128;  // entries per ring (power of two)
+
+template <class S, bool kCount>
+__global__ void __launch_bounds__(kThreads) pair_kernel_ring(LeafView lv, typename S::P p,
+                                                             const typename S::Rec *__restrict__ rec,
+                                                             double *__restrict__ cons_part) {
+    using Rec = typename S::Rec;
+    static_assert(!S::kCons, "the balanced sub-warp sweep has no conservation sums");
+    __shared__ Rec ring[kWarps][2][kRing];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sg = lane >> 4;
+    const unsigned below = lanemask_lt();
+    __shared__ int64_t leaf_slot;
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
+        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
+        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
+            const int i = g0 + lane;
+            const bool act = i < hi;
+            const Rec ri = rec[act ? i : g0];
+            typename S::I st;
+            S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
+            float l0 = act ? ri.x : INFINITY, l1 = act ? ri.y : INFINITY, l2 = act ? ri.z : INFINITY;
+            float h0 = act ? ri.x : -INFINITY, h1 = act ? ri.y : -INFINITY, h2 = act ? ri.z : -INFINITY;
+            float hm = act ? lv.pos[i].w : 0.0f;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                l0 = fminf(l0, __shfl_xor_sync(CRK_FULL_MASK, l0, o));
+                l1 = fminf(l1, __shfl_xor_sync(CRK_FULL_MASK, l1, o));
+                l2 = fminf(l2, __shfl_xor_sync(CRK_FULL_MASK, l2, o));
+                h0 = fmaxf(h0, __shfl_xor_sync(CRK_FULL_MASK, h0, o));
+                h1 = fmaxf(h1, __shfl_xor_sync(CRK_FULL_MASK, h1, o));
+                h2 = fmaxf(h2, __shfl_xor_sync(CRK_FULL_MASK, h2, o));
+                hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
+            }
+            float bl[2][3], bh[2][3], bhm[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                bl[t][0] = __shfl_sync(CRK_FULL_MASK, l0, 16 * t);
+                bl[t][1] = __shfl_sync(CRK_FULL_MASK, l1, 16 * t);
+                bl[t][2] = __shfl_sync(CRK_FULL_MASK, l2, 16 * t);
+                bh[t][0] = __shfl_sync(CRK_FULL_MASK, h0, 16 * t);
+                bh[t][1] = __shfl_sync(CRK_FULL_MASK, h1, 16 * t);
+                bh[t][2] = __shfl_sync(CRK_FULL_MASK, h2, 16 * t);
+                bhm[t] = __shfl_sync(CRK_FULL_MASK, hm, 16 * t);
+            }
+            const float ul0 = fminf(bl[0][0], bl[1][0]), ul1 = fminf(bl[0][1], bl[1][1]), ul2 = fminf(bl[0][2], bl[1][2]);
+            const float uh0 = fmaxf(bh[0][0], bh[1][0]), uh1 = fmaxf(bh[0][1], bh[1][1]), uh2 = fmaxf(bh[0][2], bh[1][2]);
+            const float uhm = fmaxf(bhm[0], bhm[1]);
+            unsigned head0 = 0, head1 = 0, tail0 = 0, tail1 = 0;  // warp-uniform ring counters
+            // consume k0 entries of ring 0 (lanes 0-15) and k1 of ring 1 (lanes 16-31)
+            auto sweep = [&](unsigned k0, unsigned k1) {
+                __syncwarp();
+                const unsigned kmax = k0 > k1 ? k0 : k1, mine = sg ? k1 : k0, h = sg ? head1 : head0;
+                for (unsigned k = 0; k < kmax; ++k)
+                    if (k < mine) S::template interact<kCount>(p, st, ri, ring[warp][sg][(h + k) & (kRing - 1)]);
+                head0 += k0;
+                head1 += k1;
+                __syncwarp();
+            };
+            for (int e = ib; e < ie; ++e) {
+                const crk_image im = lv.img[e];
+                const int jlo = lv.leaf_start[im.b];
+                const int jhi = S::kGasOnly ? jlo + lv.leaf_ngas[im.b] : lv.leaf_start[im.b + 1];
+                {
+                    const float *bb = lv.bbox + 6 * (int64_t)im.b;
+                    float gx = fmaxf(fmaxf(im.sx - uh0, ul0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+                    float gy = fmaxf(fmaxf(im.sy - uh1, ul1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+                    float gz = fmaxf(fmaxf(im.sz - uh2, ul2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+                    float cut = S::leaf_cut(p, uhm, lv.hmax[im.b]);
+                    if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+                }
+                for (int j0 = jlo; j0 < jhi; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool jv = j < jhi;
+                    Rec rj;
+                    bool keep[2] = {false, false};
+                    if (jv) {
+                        rj = rec[j];
+                        S::shift(rj, im.sx, im.sy, im.sz);
+                        if constexpr (S::kTag) S::tag(rj, e - ib, j - jlo);
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            float dx = fmaxf(fmaxf(bl[t][0] - rj.x, rj.x - bh[t][0]), 0.f);
+                            float dy = fmaxf(fmaxf(bl[t][1] - rj.y, rj.y - bh[t][1]), 0.f);
+                            float dz = fmaxf(fmaxf(bl[t][2] - rj.z, rj.z - bh[t][2]), 0.f);
+                            float cut = S::box_cut(p, bhm[t], rj);
+                            keep[t] = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
+                        }
+                    }
+                    const unsigned m0 = __ballot_sync(CRK_FULL_MASK, keep[0]);
+                    const unsigned m1 = __ballot_sync(CRK_FULL_MASK, keep[1]);
+                    if (keep[0]) ring[warp][0][(tail0 + __popc(m0 & below)) & (kRing - 1)] = rj;
+                    if (keep[1]) ring[warp][1][(tail1 + __popc(m1 & below)) & (kRing - 1)] = rj;
+                    tail0 += __popc(m0);
+                    tail1 += __popc(m1);
+                    const unsigned r0 = tail0 - head0, r1 = tail1 - head1;
+                    const unsigned both = r0 < r1 ? r0 : r1;
+                    if (r0 > kRing - 32 || r1 > kRing - 32) sweep(r0, r1);  // a ring is nearly full
+                    else if (both >= 32) sweep(both, both);                // balanced
+                }
+            }
+            sweep(tail0 - head0, tail1 - head1);
+            if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
+            if (kCount) {
+                int cn = act ? st.cnt - 1 : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+                if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+            }
+        }
+        if (S::kGasOnly)
+            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.korder ? q : lv.kperm[q]);
     }
 }
 
@@ -983,10 +1106,10 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
                     S::template interact<kCount>(p, st, ri, rj);
                 }
             }
-            if (act) S::finish(p, st, ri, lv.kperm[i], i);
+            if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
             if constexpr (S::kCons) {
                 double cc[4] = {0.0, 0.0, 0.0, 0.0};
-                if (act) S::cons_terms(p, st, ri, lv.kperm[i], cc);
+                if (act) S::cons_terms(p, st, ri, lv.korder ? i : lv.kperm[i], cc);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -1002,7 +1125,7 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
             }
         }
         if (S::kGasOnly)
-            for (int t = hi + threadIdx.x; t < end; t += kThreads) S::finish_other(p, lv.kperm[t]);
+            for (int t = hi + threadIdx.x; t < end; t += kThreads) S::finish_other(p, lv.korder ? t : lv.kperm[t]);
     }
     if constexpr (S::kCons) {
         if (cons_part) {
@@ -1044,7 +1167,7 @@ __global__ void list_group_k_kernel(int64_t n_leaves, const int32_t *__restrict_
 
 template <class S>
 int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pairs, int kernel_id,
-              double *cons = nullptr) {
+              double *cons = nullptr, bool korder = false) {
     if (!lv) return crk_fail(ctx, CRK_EINVAL, "null leaves");
     const int64_t n = lv->n;
     if (n == 0) return CRK_OK;
@@ -1061,7 +1184,7 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     }
     const float4 *kpos = gas_pairs ? lv->pos : lv->pos_g;          // gravity: species-mixed kernel order
     const int32_t *kperm = gas_pairs ? lv->kperm : lv->kperm_g;
-    gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, kpos, kperm, p, rec);
+    gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, kpos, kperm, p, rec, korder ? 1 : 0);
     int32_t *queue = nullptr;
     if (ctx->persistent) {
         queue = (int32_t *)crk_scratch(ctx, 17, 64);
@@ -1070,7 +1193,7 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     }
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kpos, kperm,
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
-               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue};
+               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue, korder ? 1 : 0};
     if (queue) {
         // persistent grid: resident blocks on every SM (4 blocks of 128 threads per SM is the design point)
         int64_t g = (int64_t)ctx->num_sms * 4;
@@ -1090,6 +1213,13 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
             pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
         else
             pair_kernel_sub<S, 16, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+    } else if (ctx->variant[kernel_id] == CRK_VARIANT_RING16 && !S::kCons) {
+        if constexpr (!S::kCons) {
+            if (p.count)
+                pair_kernel_ring<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            else
+                pair_kernel_ring<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        }
     } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES8) {
         if (p.count)
             pair_kernel_sub<S, 8, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
@@ -1201,11 +1331,11 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     if (rc) return rc;
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kGas ? lv->pos : lv->pos_g,
                kGas ? lv->kperm : lv->kperm_g, kGas ? lv->himg_start : lv->gimg_start,
-               kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg, nl, nullptr};
+               kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg, nl, nullptr, 0};
     typename LS::Rec *rec = (typename LS::Rec *)crk_scratch(ctx, 4, sizeof(typename LS::Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
     const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
-    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec);
+    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
     ListP pc{nullptr, gstart, nullptr, cnt, 0, rc2, n, nullptr};
     pair_kernel<LS, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pc, rec, nullptr);
     ctx->launches += 2;
@@ -1299,9 +1429,9 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     p.n = n;
     p.count = nullptr;
     // every record is rewritten before it is read, so nothing needs clearing
-    gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos_g, lv->kperm_g, p, rec);
+    gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos_g, lv->kperm_g, p, rec, 0);
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos_g, lv->kperm_g, lv->gimg_start,
-               lv->gimg_cnt, lv->gimg, lv->n_leaves, nullptr};
+               lv->gimg_cnt, lv->gimg, lv->n_leaves, nullptr, 0};
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {
@@ -1312,4 +1442,145 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     }
     ctx->launches += 2;
     return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Whole step with kernel-order intermediates.  The step's inputs are permuted
+// into the two kernel orders once; every intermediate (V, rho, A, B, dA, dB,
+// a, the cotangents) stays in kernel order, so it is written and read
+// coalesced instead of being scattered to the caller's order and gathered
+// back by the next kernel; the outputs the caller asked for are scattered once
+// at the end.
+namespace {
+
+// dst[c*n + q] = src[c*n + perm[q]] for c < ncomp (into kernel order)
+__global__ void to_korder_kernel(int64_t n, int ncomp, const int32_t *__restrict__ perm, const float *__restrict__ src,
+                                 float *__restrict__ dst) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t o = perm[q];
+    for (int c = 0; c < ncomp; ++c) dst[c * n + q] = src[c * n + o];
+}
+
+// dst[c*n + o] = src[c*n + inv[o]]: back to the caller's order as a gather
+// through the inverse permutation (coalesced writes; a scatter would write
+// every 4-byte element into a separate sector)
+__global__ void from_korder_kernel(int64_t n, int ncomp, const int32_t *__restrict__ inv,
+                                   const float *__restrict__ src, float *__restrict__ dst) {
+    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int64_t q = inv[o];
+    for (int c = 0; c < ncomp; ++c) dst[c * n + o] = src[c * n + q];
+}
+
+__global__ void cotangent_kernel(int64_t n, const float *__restrict__ a_g, const float4 *__restrict__ pos,
+                                 float *__restrict__ abar_g, float *__restrict__ rhob_k) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    if (abar_g)
+        for (int c = 0; c < 3; ++c) abar_g[c * n + q] = 2.0f * a_g[c * n + q];
+    if (rhob_k) rhob_k[q] = pos[q].w > 0.0f ? 1.0f : 0.0f;
+}
+
+}  // namespace
+
+int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+                   const crk_step_io *io) {
+    const int64_t n = lv->n;
+    if (n == 0) return CRK_OK;
+    if (!io->m || !io->v3 || !io->u) return crk_fail(ctx, CRK_EINVAL, "step inputs m, v3, u are required");
+    if (gp->r_cut != lv->r_cut_grav) return crk_fail(ctx, CRK_ESTATE, "r_cut differs from the leaves' r_cut_grav");
+    float *buf = (float *)crk_scratch(ctx, 18, sizeof(float) * 48 * (size_t)n);
+    if (!buf) return crk_fail(ctx, CRK_ENOMEM, "step scratch");
+    float *cur = buf;
+    auto take = [&](int k) { float *r = cur; cur += (size_t)k * n; return r; };
+    float *m_k = take(1), *v_k = take(3), *u_k = take(1), *V_k = take(1), *rho_k = take(1), *A_k = take(1);
+    float *B_k = take(3), *gA_k = take(3), *gB_k = take(9), *dv_k = take(3), *du_k = take(1), *rhob_k = take(1);
+    float *Vb_k = take(1), *gx2_k = take(3), *gm2_k = take(1);
+    float *m_g = take(1), *a_g = take(3), *abar_g = take(3), *gx_g = take(3), *gm_g = take(1);
+    cudaStream_t st = ctx->stream;
+    const int g = crk_grid(n, 256);
+    crk_step_mark(ctx, 0);
+    to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm, io->m, m_k);
+    to_korder_kernel<<<g, 256, 0, st>>>(n, 3, lv->kperm, io->v3, v_k);
+    to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm, io->u, u_k);
+    to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm_g, io->m, m_g);
+    ctx->launches += 4;
+    CRK_LAUNCH_CHECK(ctx, "step inputs");
+    unsigned long long *cnt = (unsigned long long *)io->pair_count;
+    int rc;
+    {
+        GeomP p{m_k, V_k, rho_k, n, cnt ? cnt + 0 : nullptr};
+        if ((rc = run_stage<GeomStage>(ctx, lv, p, true, CRK_K_GEOMETRY, nullptr, true))) return rc;
+    }
+    crk_step_mark(ctx, 1);
+    {
+        if (io->n_singular) CRK_CUDA(ctx, cudaMemsetAsync(io->n_singular, 0, sizeof(int32_t), st));
+        CorrP p{V_k, A_k, B_k, gA_k, gB_k, io->n_singular, n, nullptr};
+        if ((rc = run_stage<CorrStage>(ctx, lv, p, true, CRK_K_CORRECTIONS, nullptr, true))) return rc;
+    }
+    crk_step_mark(ctx, 2);
+    {
+        HydroP p{m_k, v_k, u_k, V_k, rho_k, A_k, B_k, gA_k, gB_k, dv_k, du_k, io->conservation,
+                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr};
+        if ((rc = run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, io->conservation, true))) return rc;
+    }
+    crk_step_mark(ctx, 3);
+    {
+        GravP p{};
+        p.m = m_g;
+        p.a3 = a_g;
+        p.rc2 = gp->r_cut * gp->r_cut;
+        p.eps2 = gp->eps * gp->eps;
+        for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
+        p.n = n;
+        p.count = cnt ? cnt + 2 : nullptr;
+        if ((rc = run_stage<GravStage>(ctx, lv, p, false, CRK_K_GRAVITY, nullptr, true))) return rc;
+    }
+    crk_step_mark(ctx, 4);
+    // cotangents: the caller's (permuted into kernel order) or those of sum |a|^2 + sum_gas rho
+    if (io->abar3) to_korder_kernel<<<g, 256, 0, st>>>(n, 3, lv->kperm_g, io->abar3, abar_g);
+    if (io->rhobar) to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm, io->rhobar, rhob_k);
+    if (io->Vbar) to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm, io->Vbar, Vb_k);
+    cotangent_kernel<<<g, 256, 0, st>>>(n, a_g, lv->pos, io->abar3 ? nullptr : abar_g, io->rhobar ? nullptr : rhob_k);
+    ctx->launches += 1 + (io->abar3 != nullptr) + (io->rhobar != nullptr) + (io->Vbar != nullptr);
+    CRK_LAUNCH_CHECK(ctx, "step cotangents");
+    {
+        GravAdjP p{};
+        p.m = m_g;
+        p.abar = abar_g;
+        p.gx3 = gx_g;
+        p.gm = gm_g;
+        p.rc2 = gp->r_cut * gp->r_cut;
+        p.eps2 = gp->eps * gp->eps;
+        for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
+        p.n = n;
+        p.count = nullptr;
+        if ((rc = run_stage<GravAdjStage>(ctx, lv, p, false, CRK_K_GRAVITY_ADJOINT, nullptr, true))) return rc;
+    }
+    crk_step_mark(ctx, 5);
+    {
+        GeomAdjP p{m_k, V_k, rhob_k, io->Vbar ? Vb_k : nullptr, gx2_k, gm2_k, n, nullptr};
+        if ((rc = run_stage<GeomAdjStage>(ctx, lv, p, true, CRK_K_GEOMETRY_ADJOINT, nullptr, true))) return rc;
+    }
+    crk_step_mark(ctx, 6);
+    // outputs back to the caller's order (only those asked for)
+    struct Out {
+        float *dst;
+        const float *src;
+        int comp;
+        const int32_t *perm;
+    } outs[] = {{io->V, V_k, 1, lv->kinv},          {io->rho, rho_k, 1, lv->kinv},     {io->A, A_k, 1, lv->kinv},
+                {io->B, B_k, 3, lv->kinv},          {io->gradA, gA_k, 3, lv->kinv},    {io->gradB, gB_k, 9, lv->kinv},
+                {io->dvdt3, dv_k, 3, lv->kinv},     {io->dudt, du_k, 1, lv->kinv},     {io->a3, a_g, 3, lv->kinv_g},
+                {io->gx3_grav, gx_g, 3, lv->kinv_g}, {io->gm_grav, gm_g, 1, lv->kinv_g}, {io->gx3_geom, gx2_k, 3, lv->kinv},
+                {io->gm_geom, gm2_k, 1, lv->kinv}};
+    for (const Out &o : outs)
+        if (o.dst) {
+            from_korder_kernel<<<g, 256, 0, st>>>(n, o.comp, o.perm, o.src, o.dst);
+            ++ctx->launches;
+        }
+    CRK_LAUNCH_CHECK(ctx, "step outputs");
+    crk_step_mark(ctx, 7);
+    return CRK_OK;
 }

@@ -6,59 +6,54 @@
 
 #include "crk_internal.cuh"
 
-namespace {
-
-// abar = 2 a (cotangent of sum |a|^2); rhobar = 1 on gas, 0 on dark matter
-__global__ void step_cotangents_kernel(int64_t n, const float *__restrict__ a3, const float4 *__restrict__ pos,
-                                       const int32_t *__restrict__ kperm, float *__restrict__ abar3,
-                                       float *__restrict__ rhobar) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    if (abar3) {
-        abar3[q] = 2.0f * a3[q];
-        abar3[n + q] = 2.0f * a3[n + q];
-        abar3[2 * n + q] = 2.0f * a3[2 * n + q];
-    }
-    if (rhobar) rhobar[kperm[q]] = pos[q].w > 0.0f ? 1.0f : 0.0f;
-}
-
-}  // namespace
-
 struct crk_graph {
     crk_ctx *ctx = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
 
+void crk_step_mark(crk_ctx *ctx, int k) {
+    if (ctx->prof_max <= 0 || ctx->prof_used >= ctx->prof_max) return;
+    cudaEventRecord(ctx->prof_ev[8 * (size_t)ctx->prof_used + k], ctx->stream);
+}
+
 int crk_step(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io) {
     if (!ctx) return CRK_EINVAL;
     if (!lv || !gp || !hp || !io) return crk_fail(ctx, CRK_EINVAL, "null argument");
-    const int64_t n = lv->n;
-    if (n == 0) return CRK_OK;
-    int rc;
-    if ((rc = crk_geometry(ctx, lv, io->m, io->V, io->rho, io->pair_count ? io->pair_count + 0 : nullptr))) return rc;
-    if ((rc = crk_corrections(ctx, lv, io->V, io->A, io->B, io->gradA, io->gradB, io->n_singular))) return rc;
-    if ((rc = crk_hydro(ctx, lv, hp, io->m, io->v3, io->u, io->V, io->rho, io->A, io->B, io->gradA, io->gradB,
-                        io->dvdt3, io->dudt, io->conservation, io->pair_count ? io->pair_count + 1 : nullptr)))
-        return rc;
-    if ((rc = grav_short(ctx, lv, gp, io->m, io->a3, io->pair_count ? io->pair_count + 2 : nullptr))) return rc;
-    // cotangents of the step's loss sum |a|^2 + sum_gas rho unless the caller gave its own
-    float *abar = io->abar3 ? nullptr : io->scratch3;
-    float *rhob = io->rhobar ? nullptr : io->scratch1;
-    if (abar || rhob) {
-        if ((abar && !io->scratch3) || (rhob && !io->scratch1))
-            return crk_fail(ctx, CRK_EINVAL, "scratch3/scratch1 needed when abar3/rhobar are NULL");
-        step_cotangents_kernel<<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, io->a3, lv->pos, lv->kperm, abar, rhob);
-        ++ctx->launches;
-        CRK_LAUNCH_CHECK(ctx, "step cotangents");
+    int rc = crk_step_fused(ctx, lv, gp, hp, io);
+    if (rc == CRK_OK && lv->n > 0 && ctx->prof_max > 0 && ctx->prof_used < ctx->prof_max) ++ctx->prof_used;
+    return rc;
+}
+
+int crk_step_profile(crk_ctx *ctx, int max_steps) {
+    if (!ctx || max_steps < 0) return CRK_EINVAL;
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
+    ctx->prof_max = 0;
+    ctx->prof_used = 0;
+    for (int k = 0; k < 8 * max_steps; ++k) {
+        cudaEvent_t e;
+        CRK_CUDA(ctx, cudaEventCreate(&e));
+        ctx->prof_ev.push_back(e);
     }
-    if ((rc = grav_short_adjoint(ctx, lv, gp, io->m, io->abar3 ? io->abar3 : io->scratch3, io->gx3_grav,
-                                 io->gm_grav)))
-        return rc;
-    if ((rc = crk_geometry_adjoint(ctx, lv, io->m, io->V, io->rhobar ? io->rhobar : io->scratch1, io->Vbar,
-                                   io->gx3_geom, io->gm_geom)))
-        return rc;
+    ctx->prof_max = max_steps;
+    return CRK_OK;
+}
+
+int crk_step_profile_read(crk_ctx *ctx, float ms[7], int *steps) {
+    if (!ctx || !ms || !steps) return CRK_EINVAL;
+    for (int k = 0; k < 7; ++k) ms[k] = 0.0f;
+    *steps = ctx->prof_used;
+    if (ctx->prof_used == 0) return CRK_OK;
+    CRK_CUDA(ctx, cudaEventSynchronize(ctx->prof_ev[8 * (size_t)ctx->prof_used - 1]));
+    for (int s = 0; s < ctx->prof_used; ++s)
+        for (int k = 0; k < 7; ++k) {
+            float t = 0.0f;
+            CRK_CUDA(ctx, cudaEventElapsedTime(&t, ctx->prof_ev[8 * (size_t)s + k], ctx->prof_ev[8 * (size_t)s + k + 1]));
+            ms[k] += t / ctx->prof_used;
+        }
+    ctx->prof_used = 0;
     return CRK_OK;
 }
 
@@ -74,6 +69,8 @@ int crk_step_graph_create(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_par
     CRK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     crk_graph *g = new crk_graph();
     g->ctx = ctx;
+    const int prof = ctx->prof_max;  // no profiling events inside the graph
+    ctx->prof_max = 0;
     cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         delete g;
@@ -81,6 +78,7 @@ int crk_step_graph_create(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_par
     }
     rc = crk_step(ctx, lv, gp, hp, io);
     e = cudaStreamEndCapture(ctx->stream, &g->graph);
+    ctx->prof_max = prof;
     if (rc || e != cudaSuccess) {
         if (g->graph) cudaGraphDestroy(g->graph);
         delete g;
@@ -114,14 +112,14 @@ void crk_graph_destroy(crk_graph *g) {
 // Autotuner: time every variant of every kernel on these leaves (CUDA events
 // on the context stream, best of `reps` after one warm-up) and keep the
 // fastest.  Variants that need neighbour lists the leaves do not hold are
-// skipped.  ms_out (host, 6 x 4, may be NULL) receives the timings (-1 when
+// skipped.  ms_out (host, 6 x 5, may be NULL) receives the timings (-1 when
 // skipped), best_out (host, 6, may be NULL) the chosen variants.
 int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io, int reps, float *ms_out, int *best_out) {
     if (!ctx) return CRK_EINVAL;
     if (!lv || !gp || !hp || !io) return crk_fail(ctx, CRK_EINVAL, "null argument");
     if (reps < 1) reps = 1;
-    const int nvar = CRK_VARIANT_TILES8 + 1;
+    const int nvar = CRK_VARIANT_RING16 + 1;
     int keep[6];
     for (int k = 0; k < 6; ++k) keep[k] = ctx->variant[k];
     // inputs of the later kernels come from one full step
@@ -130,8 +128,12 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
     cudaEvent_t e0, e1;
     CRK_CUDA(ctx, cudaEventCreate(&e0));
     CRK_CUDA(ctx, cudaEventCreate(&e1));
-    const float *abar = io->abar3 ? io->abar3 : io->scratch3;
-    const float *rhob = io->rhobar ? io->rhobar : io->scratch1;
+    if (!io->V || !io->rho || !io->A || !io->B || !io->gradA || !io->gradB || !io->dvdt3 || !io->dudt || !io->a3 ||
+        !io->gx3_grav || !io->gm_grav || !io->gx3_geom || !io->gm_geom)
+        return crk_fail(ctx, CRK_EINVAL, "crk_tune needs every output array of the step");
+    // timing only: any arrays of the right size serve as cotangents
+    const float *abar = io->abar3 ? io->abar3 : io->a3;
+    const float *rhob = io->rhobar ? io->rhobar : io->rho;
     for (int k = 0; k < 6; ++k) {
         float best = 1e30f;
         int bv = keep[k];

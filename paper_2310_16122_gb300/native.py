@@ -26,6 +26,8 @@ VARIANT_LISTS = 0
 VARIANT_TILES = 1
 VARIANT_TILES16 = 2
 VARIANT_TILES8 = 3
+VARIANT_RING16 = 4
+N_VARIANTS = 5
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
                 -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT", -7: "CRK_ETOOLARGE"}
 
@@ -64,8 +66,7 @@ class crk_batch(ctypes.Structure):
 class crk_step_io(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "m", "v3", "u", "V", "rho", "A", "B", "gradA", "gradB", "dvdt3", "dudt", "conservation", "a3", "abar3",
-        "gx3_grav", "gm_grav", "rhobar", "Vbar", "gx3_geom", "gm_geom", "scratch3", "scratch1", "n_singular",
-        "pair_count")]
+        "gx3_grav", "gm_grav", "rhobar", "Vbar", "gx3_geom", "gm_geom", "n_singular", "pair_count")]
 
 
 _P = ctypes.c_void_p
@@ -102,6 +103,8 @@ SIGNATURES = {
     "crk_step_graph_create": [_P, _P, ctypes.POINTER(crk_grav_params), ctypes.POINTER(crk_hydro_params),
                               ctypes.POINTER(crk_step_io), ctypes.POINTER(_P)],
     "crk_graph_launch": [_P],
+    "crk_step_profile": [_P, _I],
+    "crk_step_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)],
     "crk_graph_destroy": [_P],
     "crk_tune": [_P, _P, ctypes.POINTER(crk_grav_params), ctypes.POINTER(crk_hydro_params),
                  ctypes.POINTER(crk_step_io), _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)],

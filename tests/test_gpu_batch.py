@@ -162,3 +162,29 @@ def test_persistent_launch_matches(setup):
     # their momentum components are rounding residue near zero, so compare against the summed terms
     scale = float((dbt.m[None, :] * io.dv.abs()).sum()) + float((dbt.m * io.du.abs()).sum())
     assert float((io.cons - ref[5]).abs().max()) <= 1e-12 * scale
+
+
+def test_fused_step_equals_single_calls(setup):
+    """crk_step keeps intermediates in kernel order; its outputs equal the single calls bit for bit."""
+    api, boxes = setup
+    b = boxes[3]
+    ctx = api.Context(0)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    io = api.StepIO(ctx, db)
+    api.step(ctx, lv, db, io)
+    V, rho, _ = api.geometry(ctx, lv, db.m)
+    A, B, gA, gB, _ = api.corrections(ctx, lv, V)
+    dv, du, cons, _ = api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB)
+    a, _ = api.grav_short(ctx, lv, db.gp, db.m)
+    gx, gm = api.grav_short_adjoint(ctx, lv, db.gp, db.m, 2.0 * a)
+    gx2, gm2 = api.geometry_adjoint(ctx, lv, db.m, V, (db.species == 0).float())
+    torch.cuda.synchronize()
+    for x, y in ((io.V, V), (io.rho, rho), (io.A, A), (io.B, B), (io.gA, gA), (io.gB, gB), (io.dv, dv), (io.du, du),
+                 (io.acc, a), (io.gx_grav, gx), (io.gm_grav, gm), (io.gx_geom, gx2), (io.gm_geom, gm2)):
+        assert torch.equal(x, y)
+    # outputs left out are not needed: the step runs with the intermediates kept inside
+    io2 = api.StepIO(ctx, db, outputs=False)
+    api.step(ctx, lv, db, io2)
+    torch.cuda.synchronize()
+    assert torch.equal(io2.dv, dv) and torch.equal(io2.gx_geom, gx2)

@@ -145,8 +145,8 @@ def test_error_statuses(api, ctx):
     assert e.value.status == N.CRK_EBOX  # 2 h_max >= box/2
 
 
-VARIANTS = [0, 1, 2, 3]
-VARIANT_IDS = ["lists", "tiles", "tiles16", "tiles8"]
+VARIANTS = [0, 1, 2, 3, 4]
+VARIANT_IDS = ["lists", "tiles", "tiles16", "tiles8", "ring16"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
