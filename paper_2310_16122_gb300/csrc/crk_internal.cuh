@@ -47,7 +47,7 @@ struct crk_ctx {
     int num_sms = 0;
     std::string err;
     // growable scratch arena: one buffer per slot
-    static const int kSlots = 24;  // leaf build 0-16, radix sort 12-14, scan 15
+    static const int kSlots = 32;  // leaf build 0-16 and 19-31, radix sort 12-14, scan 15, queue 17, step 18
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     int64_t launches = 0;  // kernels this context has launched
@@ -66,6 +66,7 @@ struct crk_ctx {
 
 struct crk_nlist {
     int32_t *gstart = nullptr;  // [n_leaves + 1] first group of each leaf
+    int32_t *gleaf = nullptr;   // [groups] leaf of each group
     int32_t *goff = nullptr;    // [groups + 1] group offsets, units of 32 entries
     int32_t *cnt = nullptr;     // [n] list length per kernel-order position
     uint32_t *list = nullptr;

@@ -22,7 +22,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCap = 64;                     // per-warp candidate buffer
-constexpr int kListImgCap = 512;             // image table of one i-leaf staged in shared memory
+constexpr int kGroupImgCap = 256;            // image table of one i-leaf staged per warp in shared memory
 constexpr float kSigmaW = 0.61548156588532f;  // 495 / (256 pi), Wendland C4 3-D normalisation
 
 struct LeafView {
@@ -48,6 +48,16 @@ __device__ __forceinline__ int64_t next_leaf(const LeafView &lv, int64_t cur, in
     if (threadIdx.x == 0) *slot = atomicAdd(lv.queue, 1);
     __syncthreads();
     return *slot;
+}
+
+// Next group of this warp (warp-granular work: one warp per group of 32
+// consecutive kernel-order particles of one leaf): the grid-stride successor,
+// or (persistent mode) the next unclaimed group of the work queue.  Warp-uniform.
+__device__ __forceinline__ int64_t next_group(const LeafView &lv, int64_t cur, int lane) {
+    if (!lv.queue) return cur < 0 ? (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5) : cur + (int64_t)gridDim.x * kWarps;
+    int g = 0;
+    if (lane == 0) g = atomicAdd(lv.queue, 1);
+    return __shfl_sync(CRK_FULL_MASK, g, 0);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -629,10 +639,124 @@ __global__ void gather_kernel(int64_t n, const float4 *__restrict__ pos, const i
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const float4 ps = pos[q];
-    if (S::kGasOnly && ps.w == 0.0f) return;  // dark matter (h = 0): never read by gas-pair stages
-    rec[q] = S::gather(p, korder ? (int32_t)q : kperm[q], ps);
+    const int32_t o = korder ? (int32_t)q : kperm[q];
+    if (S::kGasOnly && ps.w == 0.0f) {  // dark matter (h = 0): never read by gas-pair stages
+        S::finish_other(p, o);           // its gas-only outputs are zero
+        return;
+    }
+    rec[q] = S::gather(p, o, ps);
 }
 
+// Work of one warp on one i-group (tiles): the kernel-order particles
+// g0 .. min(g0 + 32, hi) - 1 of i-leaf a (first particle lo) against every j
+// of the leaf's images.  Each j within the cut of the group's box is
+// ballot-compacted into the warp's shared-memory buffer; all lanes sweep the
+// buffer (broadcast reads), each accumulating its own i.
+template <class S, bool kCount>
+__device__ __forceinline__ void tile_group(const LeafView &lv, const typename S::P &p,
+                                           const typename S::Rec *__restrict__ rec, typename S::Rec *buf,
+                                           int64_t a, int lo, int g0, int hi, int lane, double cons_acc[4]) {
+    using Rec = typename S::Rec;
+    const unsigned below = lanemask_lt();
+    const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+    const int i = g0 + lane;
+    const bool act = i < hi;
+    const Rec ri = rec[act ? i : g0];
+    typename S::I st;
+    S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
+    // i-group box and largest h (inactive lanes repeat lane 0's particle)
+    float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
+    float hm = lv.pos[act ? i : g0].w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bl0 = fminf(bl0, __shfl_xor_sync(CRK_FULL_MASK, bl0, o));
+        bl1 = fminf(bl1, __shfl_xor_sync(CRK_FULL_MASK, bl1, o));
+        bl2 = fminf(bl2, __shfl_xor_sync(CRK_FULL_MASK, bl2, o));
+        bh0 = fmaxf(bh0, __shfl_xor_sync(CRK_FULL_MASK, bh0, o));
+        bh1 = fmaxf(bh1, __shfl_xor_sync(CRK_FULL_MASK, bh1, o));
+        bh2 = fmaxf(bh2, __shfl_xor_sync(CRK_FULL_MASK, bh2, o));
+        hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
+    }
+    int cnt = 0;
+    for (int e = ib; e < ie; ++e) {
+        const crk_image im = lv.img[e];
+        const int jlo = lv.leaf_start[im.b];
+        const int jhi = S::kGasOnly ? jlo + lv.leaf_ngas[im.b] : lv.leaf_start[im.b + 1];
+        // whole j-leaf against the i-group box (warp-uniform)
+        {
+            const float *bb = lv.bbox + 6 * (int64_t)im.b;
+            float gx = fmaxf(fmaxf(im.sx - bh0, bl0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+            float gy = fmaxf(fmaxf(im.sy - bh1, bl1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+            float gz = fmaxf(fmaxf(im.sz - bh2, bl2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+            float cut = S::leaf_cut(p, hm, lv.hmax[im.b]);
+            if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+        }
+        for (int j0 = jlo; j0 < jhi; j0 += 32) {
+            const int j = j0 + lane;
+            const bool jv = j < jhi;
+            Rec rj;
+            bool keep = false;
+            if (jv) {
+                rj = rec[j];
+                S::shift(rj, im.sx, im.sy, im.sz);
+                if constexpr (S::kTag) S::tag(rj, e - ib, j - jlo);
+                float dx = fmaxf(fmaxf(bl0 - rj.x, rj.x - bh0), 0.f);
+                float dy = fmaxf(fmaxf(bl1 - rj.y, rj.y - bh1), 0.f);
+                float dz = fmaxf(fmaxf(bl2 - rj.z, rj.z - bh2), 0.f);
+                float cut = S::box_cut(p, hm, rj);
+                keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
+            }
+            const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+            if (keep) buf[cnt + __popc(m & below)] = rj;
+            cnt += __popc(m);
+            if (cnt >= 32) {
+                __syncwarp();
+                for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[k]);
+                cnt = 0;
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[k]);
+    __syncwarp();
+    if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
+    if constexpr (S::kCons) {
+        double c[4] = {0.0, 0.0, 0.0, 0.0};
+        if (act) S::cons_terms(p, st, ri, lv.korder ? i : lv.kperm[i], c);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(CRK_FULL_MASK, c[k], o);
+            cons_acc[k] += c[k];
+        }
+    }
+    if (kCount) {
+        int c = act ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
+        if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+    }
+}
+
+// Per-block partial of the FP64 conservation sums in a fixed order (reduced by
+// cons_reduce_kernel: deterministic for a fixed assignment of work to blocks).
+__device__ __forceinline__ void cons_block_partial(double (*cons_sh)[4], const double cons_acc[4],
+                                                   double *__restrict__ cons_part) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) cons_sh[warp][k] = cons_acc[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < kWarps; ++w) t += cons_sh[w][k];
+            cons_part[4 * (int64_t)blockIdx.x + k] = t;
+        }
+}
+
+// Tiles, one block per i-leaf (or leaves from the persistent queue); the
+// block's warps take the leaf's groups in turn.
 template <class S, bool kCount>
 __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S::P p,
                                                         const typename S::Rec *__restrict__ rec,
@@ -641,109 +765,47 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
     __shared__ Rec buf[kWarps][kCap];
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned below = lanemask_lt();
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
     __shared__ int64_t leaf_slot;
     for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
-        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
-        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
-        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
-        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
-            const int i = g0 + lane;
-            const bool act = i < hi;
-            const Rec ri = rec[act ? i : g0];
-            typename S::I st;
-            S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
-            // i-group box and largest h (inactive lanes repeat lane 0's particle)
-            float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
-            float hm = lv.pos[act ? i : g0].w;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bl0 = fminf(bl0, __shfl_xor_sync(CRK_FULL_MASK, bl0, o));
-                bl1 = fminf(bl1, __shfl_xor_sync(CRK_FULL_MASK, bl1, o));
-                bl2 = fminf(bl2, __shfl_xor_sync(CRK_FULL_MASK, bl2, o));
-                bh0 = fmaxf(bh0, __shfl_xor_sync(CRK_FULL_MASK, bh0, o));
-                bh1 = fmaxf(bh1, __shfl_xor_sync(CRK_FULL_MASK, bh1, o));
-                bh2 = fmaxf(bh2, __shfl_xor_sync(CRK_FULL_MASK, bh2, o));
-                hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
-            }
-            int cnt = 0;
-            for (int e = ib; e < ie; ++e) {
-                const crk_image im = lv.img[e];
-                const int jlo = lv.leaf_start[im.b];
-                const int jhi = S::kGasOnly ? jlo + lv.leaf_ngas[im.b] : lv.leaf_start[im.b + 1];
-                // whole j-leaf against the i-group box (warp-uniform)
-                {
-                    const float *bb = lv.bbox + 6 * (int64_t)im.b;
-                    float gx = fmaxf(fmaxf(im.sx - bh0, bl0 - (im.sx + (bb[3] - bb[0]))), 0.f);
-                    float gy = fmaxf(fmaxf(im.sy - bh1, bl1 - (im.sy + (bb[4] - bb[1]))), 0.f);
-                    float gz = fmaxf(fmaxf(im.sz - bh2, bl2 - (im.sz + (bb[5] - bb[2]))), 0.f);
-                    float cut = S::leaf_cut(p, hm, lv.hmax[im.b]);
-                    if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
-                }
-                for (int j0 = jlo; j0 < jhi; j0 += 32) {
-                    const int j = j0 + lane;
-                    const bool jv = j < jhi;
-                    Rec rj;
-                    bool keep = false;
-                    if (jv) {
-                        rj = rec[j];
-                        S::shift(rj, im.sx, im.sy, im.sz);
-                        if constexpr (S::kTag) S::tag(rj, e - ib, j - jlo);
-                        float dx = fmaxf(fmaxf(bl0 - rj.x, rj.x - bh0), 0.f);
-                        float dy = fmaxf(fmaxf(bl1 - rj.y, rj.y - bh1), 0.f);
-                        float dz = fmaxf(fmaxf(bl2 - rj.z, rj.z - bh2), 0.f);
-                        float cut = S::box_cut(p, hm, rj);
-                        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
-                    }
-                    const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
-                    if (keep) buf[warp][cnt + __popc(m & below)] = rj;
-                    cnt += __popc(m);
-                    if (cnt >= 32) {
-                        __syncwarp();
-                        for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[warp][k]);
-                        cnt = 0;
-                        __syncwarp();
-                    }
-                }
-            }
-            __syncwarp();
-            for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[warp][k]);
-            __syncwarp();
-            if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
-            if constexpr (S::kCons) {
-                double c[4] = {0.0, 0.0, 0.0, 0.0};
-                if (act) S::cons_terms(p, st, ri, lv.kperm[i], c);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(CRK_FULL_MASK, c[k], o);
-                    cons_acc[k] += c[k];
-                }
-            }
-            if (kCount) {
-                int c = act ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
-                if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
-            }
-        }
-        if (S::kGasOnly)
-            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.korder ? q : lv.kperm[q]);
+        const int lo = lv.leaf_start[a];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32)
+            tile_group<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
     }
     if constexpr (S::kCons) {
-        // per-block partial in a fixed order; reduced by cons_reduce_kernel (deterministic)
-        if (cons_part) {
-            if (lane == 0)
-                for (int k = 0; k < 4; ++k) cons_sh[warp][k] = cons_acc[k];
-            __syncthreads();
-            if (threadIdx.x == 0)
-                for (int k = 0; k < 4; ++k) {
-                    double t = 0.0;
-                    for (int w = 0; w < kWarps; ++w) t += cons_sh[w][k];
-                    cons_part[4 * (int64_t)blockIdx.x + k] = t;
-                }
-        }
+        if (cons_part) cons_block_partial(cons_sh, cons_acc, cons_part);
+    }
+}
+
+// Group table of one set of leaves: groups of 32 consecutive kernel-order
+// particles (gas only for gas stages), numbered leaf by leaf.
+struct GroupTable {
+    const int32_t *gstart;  // [n_leaves + 1] first group of each leaf
+    const int32_t *gleaf;   // [groups] leaf of each group
+    int64_t groups;
+};
+
+// Tiles, one warp per i-group: every warp works even where a leaf holds fewer
+// groups than a block has warps (gas stages: a leaf of 128 holds about 64 gas).
+template <class S, bool kCount>
+__global__ void __launch_bounds__(kThreads) pair_group_kernel(LeafView lv, typename S::P p,
+                                                              const typename S::Rec *__restrict__ rec,
+                                                              GroupTable gt, double *__restrict__ cons_part) {
+    using Rec = typename S::Rec;
+    __shared__ Rec buf[kWarps][kCap];
+    __shared__ double cons_sh[kWarps][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t grp = next_group(lv, -1, lane); grp < gt.groups; grp = next_group(lv, grp, lane)) {
+        const int64_t a = gt.gleaf[grp];
+        const int lo = lv.leaf_start[a];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
+        const int g0 = lo + 32 * (int)(grp - gt.gstart[a]);
+        tile_group<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
+    }
+    if constexpr (S::kCons) {
+        if (cons_part) cons_block_partial(cons_sh, cons_acc, cons_part);
     }
 }
 
@@ -767,8 +829,8 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
     __shared__ int64_t leaf_slot;
     for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
-        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
-        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
+        const int lo = lv.leaf_start[a];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
         const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
         for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
             const int i = g0 + lane;
@@ -882,8 +944,6 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
                 if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
             }
         }
-        if (S::kGasOnly)
-            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.korder ? q : lv.kperm[q]);
     }
     if constexpr (S::kCons) {
         if (cons_part) {
@@ -919,8 +979,8 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_ring(LeafView lv, typena
     const unsigned below = lanemask_lt();
     __shared__ int64_t leaf_slot;
     for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
-        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
-        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
+        const int lo = lv.leaf_start[a];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
         const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
         for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
             const int i = g0 + lane;
@@ -1017,8 +1077,6 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_ring(LeafView lv, typena
                 if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
             }
         }
-        if (S::kGasOnly)
-            for (int q = hi + threadIdx.x; q < end; q += kThreads) S::finish_other(p, lv.korder ? q : lv.kperm[q]);
     }
 }
 
@@ -1045,101 +1103,101 @@ __global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, 
 struct GasLists {
     const int32_t *gstart, *goff, *cnt;
     const uint32_t *list;
+    const int32_t *gleaf;
+    int64_t groups;
 };
 
+// Exact neighbour lists, one warp per i-group: each lane walks its own list;
+// the i-leaf's image table (first j of the image's leaf as a float bit
+// pattern in w, and the shift into the i frame) is staged in the warp's part
+// of shared memory, and the next record is fetched while the current pair is
+// evaluated.
 template <class S, bool kCount>
 __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S::P p,
                                                         const typename S::Rec *__restrict__ rec, GasLists gl,
                                                         double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
     __shared__ double cons_sh[kWarps][4];
+    __shared__ float4 itab_all[kWarps][kGroupImgCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *itab = itab_all[warp];
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
-    __shared__ int64_t leaf_slot;
-    // the i-leaf's image table in shared memory: first j of the image's leaf
-    // (as a float bit pattern in w) and the shift into the i frame
-    __shared__ float4 itab[kListImgCap];
-    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
-        const int lo = lv.leaf_start[a], end = lv.leaf_start[a + 1];
-        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : end;
+    for (int64_t grp = next_group(lv, -1, lane); grp < gl.groups; grp = next_group(lv, grp, lane)) {
+        const int64_t a = gl.gleaf[grp];
+        const int q = (int)(grp - gl.gstart[a]);
+        const int lo = lv.leaf_start[a];
+        const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
+        const int g0 = lo + 32 * q;
         const crk_image *imgs = lv.img + lv.img_start[a];
         const int nimg = lv.img_cnt[a];
-        const bool staged = nimg <= kListImgCap;
+        const bool staged = nimg <= kGroupImgCap;
         if (staged) {
-            __syncthreads();  // the previous leaf's table is no longer read
-            for (int t = threadIdx.x; t < nimg; t += kThreads) {
+            __syncwarp();  // the previous group's table is no longer read
+            for (int t = lane; t < nimg; t += 32) {
                 const crk_image im = imgs[t];
                 itab[t] = make_float4(im.sx, im.sy, im.sz, __int_as_float(lv.leaf_start[im.b]));
             }
-            __syncthreads();
+            __syncwarp();
         }
-        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
-            const int q = (g0 - lo) >> 5;
-            const int64_t grp = gl.gstart[a] + q;
-            const uint32_t *L = gl.list + (size_t)gl.goff[grp] * 32 + lane;
-            const int i = g0 + lane;
-            const bool act = i < hi;
-            const Rec ri = rec[act ? i : g0];
-            typename S::I st;
-            S::init(p, st, ri, a, q, lane);
-            const int c = act ? gl.cnt[i] : 0;
-            // entry k -> shifted record of j (shared-memory table, or the global image list for
-            // leaves with more images than the table holds)
-            auto fetch = [&](int k) -> Rec {
-                const uint32_t code = __ldg(L + (size_t)k * 32);
-                float4 t;
-                if (staged) {
-                    t = itab[code >> 10];
-                } else {
-                    const crk_image im = imgs[code >> 10];
-                    t = make_float4(im.sx, im.sy, im.sz, __int_as_float(lv.leaf_start[im.b]));
-                }
-                Rec r = rec[__float_as_int(t.w) + (int)(code & 1023u)];
-                S::shift(r, t.x, t.y, t.z);
-                return r;
-            };
-            if (c > 0) {
-                Rec nxt = fetch(0);
-                for (int k = 0; k < c; ++k) {
-                    const Rec rj = nxt;
-                    if (k + 1 < c) nxt = fetch(k + 1);  // in flight while rj is evaluated
-                    S::template interact<kCount>(p, st, ri, rj);
-                }
+        const uint32_t *L = gl.list + (size_t)gl.goff[grp] * 32 + lane;
+        const int i = g0 + lane;
+        const bool act = i < hi;
+        const Rec ri = rec[act ? i : g0];
+        typename S::I st;
+        S::init(p, st, ri, a, q, lane);
+        const int c = act ? gl.cnt[i] : 0;
+        // entry k -> shifted record of j (shared-memory table, or the global image list for
+        // leaves with more images than the table holds)
+        auto fetch = [&](int k) -> Rec {
+            const uint32_t code = __ldg(L + (size_t)k * 32);
+            float4 t;
+            if (staged) {
+                t = itab[code >> 10];
+            } else {
+                const crk_image im = imgs[code >> 10];
+                t = make_float4(im.sx, im.sy, im.sz, __int_as_float(lv.leaf_start[im.b]));
             }
-            if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
-            if constexpr (S::kCons) {
-                double cc[4] = {0.0, 0.0, 0.0, 0.0};
-                if (act) S::cons_terms(p, st, ri, lv.korder ? i : lv.kperm[i], cc);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) cc[k] += __shfl_xor_sync(CRK_FULL_MASK, cc[k], o);
-                    cons_acc[k] += cc[k];
-                }
-            }
-            if (kCount) {
-                int cn = act ? st.cnt - 1 : 0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
-                if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+            Rec r = rec[__float_as_int(t.w) + (int)(code & 1023u)];
+            S::shift(r, t.x, t.y, t.z);
+            return r;
+        };
+        if (c > 0) {
+            Rec nxt = fetch(0);
+            for (int k = 0; k < c; ++k) {
+                const Rec rj = nxt;
+                if (k + 1 < c) nxt = fetch(k + 1);  // in flight while rj is evaluated
+                S::template interact<kCount>(p, st, ri, rj);
             }
         }
-        if (S::kGasOnly)
-            for (int t = hi + threadIdx.x; t < end; t += kThreads) S::finish_other(p, lv.korder ? t : lv.kperm[t]);
+        if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
+        if constexpr (S::kCons) {
+            double cc[4] = {0.0, 0.0, 0.0, 0.0};
+            if (act) S::cons_terms(p, st, ri, lv.korder ? i : lv.kperm[i], cc);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cc[k] += __shfl_xor_sync(CRK_FULL_MASK, cc[k], o);
+                cons_acc[k] += cc[k];
+            }
+        }
+        if (kCount) {
+            int cn = act ? st.cnt - 1 : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+            if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+        }
     }
     if constexpr (S::kCons) {
-        if (cons_part) {
-            if (lane == 0)
-                for (int k = 0; k < 4; ++k) cons_sh[warp][k] = cons_acc[k];
-            __syncthreads();
-            if (threadIdx.x == 0)
-                for (int k = 0; k < 4; ++k) {
-                    double t = 0.0;
-                    for (int w = 0; w < kWarps; ++w) t += cons_sh[w][k];
-                    cons_part[4 * (int64_t)blockIdx.x + k] = t;
-                }
-        }
+        if (cons_part) cons_block_partial(cons_sh, cons_acc, cons_part);
     }
+}
+
+// groups of each leaf, and the leaf of each group
+__global__ void list_group_leaf_kernel(int64_t n_leaves, const int32_t *__restrict__ gstart,
+                                       int32_t *__restrict__ gleaf) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_leaves) return;
+    for (int32_t g = gstart[a]; g < gstart[a + 1]; ++g) gleaf[g] = (int32_t)a;
 }
 
 __global__ void list_group_count_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
@@ -1174,9 +1232,17 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     using Rec = typename S::Rec;
     Rec *rec = (Rec *)crk_scratch(ctx, 4, sizeof(Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
-    int64_t grid = lv->n_leaves;
+    const crk_nlist &nls = gas_pairs ? lv->gas_lists : lv->grav_lists;
+    const bool lists = nls.list && ctx->variant[kernel_id] == CRK_VARIANT_LISTS;
+    // one block per i-leaf, or (lists) one warp per i-group
+    int64_t grid = lists ? (nls.groups + kWarps - 1) / kWarps : lv->n_leaves;
     if (grid < 1) grid = 1;
     if (grid > 2147483647LL) grid = 2147483647LL;
+    if (ctx->persistent) {
+        // persistent grid: resident blocks on every SM (4 blocks of 128 threads per SM is the design point)
+        int64_t g = (int64_t)ctx->num_sms * 4;
+        if (g < grid) grid = g;
+    }
     double *part = nullptr;
     if (cons) {
         part = (double *)crk_scratch(ctx, 5, sizeof(double) * 4 * (size_t)grid);
@@ -1194,16 +1260,9 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kpos, kperm,
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
                gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue, korder ? 1 : 0};
-    if (queue) {
-        // persistent grid: resident blocks on every SM (4 blocks of 128 threads per SM is the design point)
-        int64_t g = (int64_t)ctx->num_sms * 4;
-        if (g < grid) grid = g;
-    }
     if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
-    const crk_nlist &nls = gas_pairs ? lv->gas_lists : lv->grav_lists;
-    const bool lists = nls.list && ctx->variant[kernel_id] == CRK_VARIANT_LISTS;
     if (lists) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.gleaf, nls.groups};
         if (p.count)
             list_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
         else
@@ -1334,15 +1393,20 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
                kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg, nl, nullptr, 0};
     typename LS::Rec *rec = (typename LS::Rec *)crk_scratch(ctx, 4, sizeof(typename LS::Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
-    const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
-    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
-    ListP pc{nullptr, gstart, nullptr, cnt, 0, rc2, n, nullptr};
-    pair_kernel<LS, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pc, rec, nullptr);
-    ctx->launches += 2;
-    CRK_LAUNCH_CHECK(ctx, "neighbour counts");
     int32_t ngroups = 0;
     CRK_CUDA(ctx, cudaMemcpyAsync(&ngroups, tot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CRK_CUDA(ctx, cudaStreamSynchronize(st));
+    int32_t *gleaf = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups > 0 ? ngroups : 1));
+    if (!gleaf) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
+    list_group_leaf_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, gstart, gleaf);
+    const GroupTable gt{gstart, gleaf, ngroups};
+    const unsigned ggrid = (unsigned)((ngroups + kWarps - 1) / kWarps > 0 ? (ngroups + kWarps - 1) / kWarps : 1);
+    const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
+    gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
+    ListP pc{nullptr, gstart, nullptr, cnt, 0, rc2, n, nullptr};
+    pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pc, rec, gt, nullptr);
+    ctx->launches += 3;
+    CRK_LAUNCH_CHECK(ctx, "neighbour counts");
     int32_t *goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
     int32_t *gk = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(ngroups + 1));
     if (!goff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
@@ -1358,10 +1422,11 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     uint32_t *list = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(entries > 0 ? entries : 1));
     if (!list) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
     ListP pf{list, gstart, goff, cnt, 1, rc2, n, nullptr};
-    pair_kernel<LS, false><<<(unsigned)nl, kThreads, 0, st>>>(v, pf, rec, nullptr);
+    pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "neighbour lists");
     out.gstart = gstart;
+    out.gleaf = gleaf;
     out.goff = goff;
     out.cnt = cnt;
     out.list = list;
@@ -1435,8 +1500,10 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list};
-        list_kernel<GravStage, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, nullptr);
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.gleaf, nls.groups};
+        const int64_t lgrid = (nls.groups + kWarps - 1) / kWarps;
+        list_kernel<GravStage, false><<<(unsigned)(lgrid > 0 ? lgrid : 1), kThreads, 0, ctx->stream>>>(v, p, rec, gl,
+                                                                                                     nullptr);
     } else {
         pair_kernel<GravStage, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, nullptr);
     }
