@@ -3,11 +3,13 @@
 // then the periodic leaf-pair image lists used by every pair kernel.
 //
 // RCB without per-node sorts: every particle is ranked once per axis by a
-// stable radix sort of (coordinate, index).  Each level keeps three index
-// lists, each sorted along its axis inside every node.  A node's tight box is
-// read off the ends of its three segments; the split takes the first
-// floor(n/2) of the chosen axis' segment, and the two other lists are
-// stably partitioned by a prefix sum of the side flags.  The shape of the
+// stable radix sort of (coordinate, index).  Each level keeps three lists,
+// each sorted along its axis inside every node, whose entries carry the
+// particle's ranks along the two other axes.  A node's tight box is read off
+// the ends of its three segments; the split takes the first floor(n/2) of the
+// chosen axis' segment, which is a threshold on the rank along that axis, so
+// the two other lists are stably partitioned by comparing the ranks they
+// carry (a prefix sum of the left flags orders the output).  The shape of the
 // tree depends on n alone, so the host precomputes every level's segments.
 #include <algorithm>
 #include <chrono>
@@ -99,29 +101,91 @@ struct LevelDev {
     const int32_t *lo, *hi, *k, *child, *node;
     int32_t *axis;
     const int32_t *leftbase;  // sum of k over the earlier segments of the level
+    int32_t *thr;             // rank along the split axis of the first right-going particle
 };
 
-__global__ void rcb_axis_kernel(int nseg, LevelDev lv, const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
-                                const int32_t *__restrict__ L2, const float *__restrict__ x,
+// The three axis lists carry ranks, not particle ids.  S[t] is the stable
+// (coordinate, index) order along axis t (box-major for batches) and R[t] its
+// inverse (the rank of each particle along t).  Entry p of list a holds the
+// ranks of its particle along the two other axes:
+// A[a][c][p] = rank along axis (a + 1 + c) % 3.  Inside a node, list a is
+// sorted by rank along a, so the node's split is a rank threshold: an entry of
+// another list goes left iff its rank along the split axis is below the rank
+// of the first right-going entry of the split axis' own list.  A level is then
+// pure streaming (no per-particle side flag is scattered or gathered).
+struct RankLists {
+    const int32_t *A[3][2];
+};
+struct RankListsOut {
+    int32_t *A[3][2];
+};
+struct AxisOrder {
+    const int32_t *S[3];
+    const int32_t *R[3];
+};
+
+__device__ __forceinline__ unsigned lanemask_lt_u() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int rank_comp(int a, int t) { return (t - a + 2) % 3; }  // component of list a holding t
+
+// particle id of entry p of list a
+__device__ __forceinline__ int32_t rank_entry_id(const RankLists &L, const AxisOrder &o, int a, int64_t p) {
+    const int32_t r = L.A[a][0][p];
+    return a == 0 ? o.S[1][r] : (a == 1 ? o.S[2][r] : o.S[0][r]);
+}
+
+__global__ void rank_of_kernel(int64_t n, AxisOrder o, int32_t *__restrict__ R0, int32_t *__restrict__ R1,
+                               int32_t *__restrict__ R2) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    R0[o.S[0][p]] = (int32_t)p;
+    R1[o.S[1][p]] = (int32_t)p;
+    R2[o.S[2][p]] = (int32_t)p;
+}
+
+__global__ void rank_lists_kernel(int64_t n, AxisOrder o, RankListsOut L) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int32_t id = o.S[a][p];
+        L.A[a][0][p] = o.R[(a + 1) % 3][id];
+        L.A[a][1][p] = o.R[(a + 2) % 3][id];
+    }
+}
+
+// final member order (list 0) as particle ids
+__global__ void rank_members_kernel(int64_t n, RankLists L, AxisOrder o, int32_t *__restrict__ members) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) members[p] = rank_entry_id(L, o, 0, p);
+}
+
+// per split node: tight box from the ends of its three list segments, split
+// axis (longest extent, ties to the lower axis), rank threshold
+__global__ void rcb_axis_kernel(int nseg, LevelDev lv, RankLists L, AxisOrder o, const float *__restrict__ x,
                                 const float *__restrict__ y, const float *__restrict__ z, float *__restrict__ node_box) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     int k = lv.k[s];
     if (k <= 0) return;
     int lo = lv.lo[s], hi = lv.hi[s];
-    const int32_t *Ls[3] = {L0, L1, L2};
     const float *cs[3] = {x, y, z};
     float blo[3], bhi[3];
     double ext[3];
     for (int a = 0; a < 3; ++a) {
-        blo[a] = cs[a][Ls[a][lo]];
-        bhi[a] = cs[a][Ls[a][hi - 1]];
+        blo[a] = cs[a][rank_entry_id(L, o, a, lo)];
+        bhi[a] = cs[a][rank_entry_id(L, o, a, hi - 1)];
         ext[a] = __dsub_rn((double)bhi[a], (double)blo[a]);
     }
     int axis = 0;
     if (ext[1] > ext[axis]) axis = 1;
     if (ext[2] > ext[axis]) axis = 2;
     lv.axis[s] = axis;
+    lv.thr[s] = o.R[axis][rank_entry_id(L, o, axis, lo + k)];
     float *nb = node_box + 6 * (int64_t)lv.node[s];
     for (int a = 0; a < 3; ++a) {
         nb[a] = blo[a];
@@ -129,48 +193,54 @@ __global__ void rcb_axis_kernel(int nseg, LevelDev lv, const int32_t *__restrict
     }
 }
 
-__global__ void rcb_side_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
-                                const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
-                                const int32_t *__restrict__ L2, uint8_t *__restrict__ side,
-                                int32_t *__restrict__ node_of_next) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int s = node_of[p];
-    int k = lv.k[s];
-    int lo = lv.lo[s];
-    int right = (k > 0 && (int)p - lo >= k) ? 1 : 0;
-    if (k > 0) {
-        int ax = lv.axis[s];
-        const int32_t *L = ax == 0 ? L0 : (ax == 1 ? L1 : L2);
-        side[L[p]] = (uint8_t)right;
-    }
-    node_of_next[p] = lv.child[s] + right;
-}
-
-// Fused stable partition of the three axis lists, one level at a time.  The
-// prefix count of left-going entries at a segment's start equals the sum of k
-// over the earlier split segments (every split segment sends exactly k
-// entries left in every list), so the prefix is never materialised: tiles
-// count, a 3-column scan orders the tiles, and the scatter re-derives the
-// tile-local prefixes.
+// Stable partition of the three lists, one level at a time.  The prefix count
+// of left-going entries at a segment's start equals the sum of k over the
+// earlier split segments (every split segment sends exactly k entries left in
+// every list), so the prefix is never materialised: tiles count, a 3-column
+// scan orders the tiles, and the scatter re-derives the tile-local prefixes.
 constexpr int kPartThreads = 256;
 constexpr int kPartItems = 8;
 constexpr int kPartTile = kPartThreads * kPartItems;
 
-__global__ void rcb_count3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
-                                  const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
-                                  const int32_t *__restrict__ L2, const uint8_t *__restrict__ side,
+// left flags of entry p (bit b: list b), or 0 for entries of unsplit segments
+__device__ __forceinline__ unsigned rcb_left3(const LevelDev &lv, const RankLists &L, int s, int64_t p) {
+    const int ks = lv.k[s];
+    if (ks <= 0) return 0u;
+    const int ax = lv.axis[s], lo = lv.lo[s];
+    const int32_t th = lv.thr[s];
+    unsigned f = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        bool left;
+        if (b == ax) {
+            left = (int)p - lo < ks;
+        } else {
+            const int32_t *col = rank_comp(b, ax) == 0 ? L.A[b][0] : L.A[b][1];  // no dynamic index into the parameter
+            left = col[p] < th;
+        }
+        f |= (unsigned)left << b;
+    }
+    return f;
+}
+
+__global__ void rcb_count3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of, RankLists L,
                                   int32_t *__restrict__ bsum, int64_t nb) {
     __shared__ int32_t wt[32];
     const int64_t base = (int64_t)blockIdx.x * kPartTile;
-    int32_t c[3] = {0, 0, 0};
+    int32_t seg[kPartItems];
+#pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
         int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
-        if (p >= n) break;
-        if (lv.k[node_of[p]] <= 0) continue;
-        c[0] += side[L0[p]] == 0;
-        c[1] += side[L1[p]] == 0;
-        c[2] += side[L2[p]] == 0;
+        seg[k] = p < n ? node_of[p] : -1;
+    }
+    int32_t c[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+        int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
+        unsigned f = seg[k] >= 0 ? rcb_left3(lv, L, seg[k], p) : 0u;
+        c[0] += f & 1u;
+        c[1] += (f >> 1) & 1u;
+        c[2] += (f >> 2) & 1u;
     }
     for (int b = 0; b < 3; ++b) {
         int32_t tot;
@@ -196,56 +266,83 @@ __global__ void rcb_scan3_kernel(int32_t *__restrict__ bsum, int64_t nb) {
     }
 }
 
-__global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of,
-                                    const int32_t *__restrict__ L0, const int32_t *__restrict__ L1,
-                                    const int32_t *__restrict__ L2, const uint8_t *__restrict__ side,
-                                    const int32_t *__restrict__ bsum, int64_t nb, int32_t *__restrict__ O0,
-                                    int32_t *__restrict__ O1, int32_t *__restrict__ O2, int32_t *__restrict__ err) {
-    __shared__ int32_t wt[32];
-    const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;  // blocked
-    const int32_t *Ls[3] = {L0, L1, L2};
-    int32_t *Os[3] = {O0, O1, O2};
+// Entries are taken in rows of kPartThreads consecutive positions (entry k of
+// thread t is position base + k kPartThreads + t), so the left-going (and the
+// right-going) entries of one warp row land in consecutive output positions:
+// coalesced stores.  The tile-local prefix of an entry is the count over
+// earlier (row, warp) pairs plus the ballot rank inside its warp.
+constexpr int kPartWarps = kPartThreads / 32;
+
+__global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of, RankLists L,
+                                    const int32_t *__restrict__ bsum, int64_t nb, RankListsOut O,
+                                    int32_t *__restrict__ node_of_next, int32_t *__restrict__ err) {
+    static_assert(kPartItems * kPartWarps == 64, "prefix table: two entries per lane of one warp");
+    __shared__ int32_t wc[3][kPartItems * kPartWarps];  // left count per (list, row, warp), then its prefix
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = lanemask_lt_u();
+    const int64_t base = (int64_t)blockIdx.x * kPartTile;
     int32_t seg[kPartItems];
-    uint32_t flags = 0;  // bit 3k+b: entry k of list b goes left
-    int32_t c[3] = {0, 0, 0};
+    unsigned f[kPartItems];
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
-        int64_t p = base + k;
+        int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
         seg[k] = p < n ? node_of[p] : -1;
-        if (seg[k] >= 0 && lv.k[seg[k]] > 0) {
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                bool left = side[Ls[b][p]] == 0;
-                flags |= (uint32_t)left << (3 * k + b);
-                c[b] += left;
-            }
-        }
-    }
-    int32_t pre[3];
-    for (int b = 0; b < 3; ++b) {
-        int32_t tot;
-        pre[b] = crk_block_scan(c[b], wt, tot) + bsum[(int64_t)b * nb + blockIdx.x];
     }
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
-        int64_t p = base + k;
-        if (seg[k] < 0) continue;
-        const int s = seg[k];
-        const int ks = lv.k[s];
+        int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
+        f[k] = seg[k] >= 0 ? rcb_left3(lv, L, seg[k], p) : 0u;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            int32_t id = Ls[b][p];
-            if (ks <= 0) {
-                Os[b][p] = id;
-                continue;
+            const unsigned m = __ballot_sync(0xffffffffu, (f[k] >> b) & 1u);
+            if (lane == 0) wc[b][k * kPartWarps + warp] = __popc(m);
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int b = 0; b < 3; ++b) {
+            const int32_t e0 = wc[b][2 * lane], e1 = wc[b][2 * lane + 1];
+            int32_t v = e0 + e1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
             }
-            const int lo = lv.lo[s];
-            const int lb = pre[b] - lv.leftbase[s];  // left-going entries before p in this segment
-            const bool left = (flags >> (3 * k + b)) & 1u;
-            const int np = left ? lo + lb : lo + ks + ((int)p - lo - lb);
-            if (np >= lo && np < lv.hi[s]) Os[b][np] = id;
-            else atomicAdd(err, 1);  // inconsistent partition: reported, never written out of the segment
-            pre[b] += left;
+            const int32_t ex = v - e0 - e1;
+            wc[b][2 * lane] = ex;
+            wc[b][2 * lane + 1] = ex + e0;
+        }
+    }
+    __syncthreads();
+    int32_t tile0[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) tile0[b] = bsum[(int64_t)b * nb + blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+        const int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
+        const int s = seg[k];
+        const bool valid = s >= 0;
+        const int ks = valid ? lv.k[s] : 0;
+        const int lo = valid ? lv.lo[s] : 0;
+        if (valid) node_of_next[p] = lv.child[s] + ((ks > 0 && (int)p - lo >= ks) ? 1 : 0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const bool left = (f[k] >> b) & 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, left);
+            if (!valid) continue;
+            const int32_t r0 = L.A[b][0][p], r1 = L.A[b][1][p];
+            int64_t np = p;
+            if (ks > 0) {
+                // left-going entries before p in this segment
+                const int lb = tile0[b] + wc[b][k * kPartWarps + warp] + __popc(m & below) - lv.leftbase[s];
+                np = left ? lo + lb : lo + ks + ((int)p - lo - lb);
+                if (!(np >= lo && np < lv.hi[s])) {
+                    atomicAdd(err, 1);  // inconsistent partition: reported, never written out of the segment
+                    continue;
+                }
+            }
+            O.A[b][0][np] = r0;
+            O.A[b][1][np] = r1;
         }
     }
 }
@@ -273,7 +370,8 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
                                  int32_t *__restrict__ leaf_ngas, float *__restrict__ bbox,
                                  float *__restrict__ hmax, float4 *__restrict__ pos, int32_t *__restrict__ kperm_g,
                                  float4 *__restrict__ pos_g, int32_t *__restrict__ err) {
-    __shared__ uint64_t key[kMaxLeafCap];
+    __shared__ uint64_t key[kMaxLeafCap], zkey[kMaxLeafCap], gkey[kMaxLeafCap];
+    __shared__ float4 pm[kMaxLeafCap];  // member position and h (0 for dark matter), gathered once
     __shared__ float red[6][32];
     __shared__ int ngs[32];
     __shared__ float hms[32];
@@ -289,15 +387,18 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
     float hm = 0.0f;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         int32_t id = members[lo + t];
-        key[t] = ((uint64_t)(sp[id] != 0) << 32) | (uint32_t)id;
+        const bool gas = sp[id] == 0;
+        key[t] = ((uint64_t)!gas << 32) | (uint32_t)id;
         float c[3] = {x[id], y[id], z[id]};
+        const float hh = gas ? h[id] : 0.0f;
+        pm[t] = make_float4(c[0], c[1], c[2], hh);
         for (int q = 0; q < 3; ++q) {
             mn[q] = fminf(mn[q], c[q]);
             mx[q] = fmaxf(mx[q], c[q]);
         }
-        if (sp[id] == 0) {
+        if (gas) {
             ++ng;
-            hm = fmaxf(hm, h[id]);
+            hm = fmaxf(hm, hh);
         }
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -335,45 +436,37 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
     const float ox = red[0][0], oy = red[1][0], oz = red[2][0];
     const float ext = fmaxf(fmaxf(red[3][0] - ox, red[4][0] - oy), fmaxf(red[5][0] - oz, 1e-30f));
     const float sc = 1023.0f / ext;
-    // canonical ranks, and the Z-order keys of each member (kept in registers):
-    // zkey with the species on top (gas first), gkey without (gravity order)
-    uint64_t zkey[kMaxLeafCap / 128], gkey[kMaxLeafCap / 128];
-    int nk = 0;
+    // canonical ranks, and the Z-order keys of each member: zkey with the
+    // species on top (gas first), gkey without (gravity order)
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         uint64_t kt = key[t];
         int r = 0;
         for (int u = 0; u < cnt; ++u) r += key[u] < kt;
         int32_t id = (int32_t)(uint32_t)kt;
         perm[lo + r] = id;
-        uint32_t mx3 = spread10((uint32_t)fminf((x[id] - ox) * sc, 1023.0f)) |
-                       (spread10((uint32_t)fminf((y[id] - oy) * sc, 1023.0f)) << 1) |
-                       (spread10((uint32_t)fminf((z[id] - oz) * sc, 1023.0f)) << 2);
-        gkey[nk] = ((uint64_t)mx3 << 32) | (uint32_t)id;
-        zkey[nk++] = ((uint64_t)(sp[id] != 0) << 62) | ((uint64_t)mx3 << 32) | (uint32_t)id;
+        const float4 c = pm[t];
+        uint32_t mx3 = spread10((uint32_t)fminf((c.x - ox) * sc, 1023.0f)) |
+                       (spread10((uint32_t)fminf((c.y - oy) * sc, 1023.0f)) << 1) |
+                       (spread10((uint32_t)fminf((c.z - oz) * sc, 1023.0f)) << 2);
+        gkey[t] = ((uint64_t)mx3 << 32) | (uint32_t)id;
+        zkey[t] = ((kt >> 32) << 62) | ((uint64_t)mx3 << 32) | (uint32_t)id;
     }
     __syncthreads();
-    nk = 0;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) key[t] = zkey[nk++];
-    __syncthreads();
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        uint64_t kt = key[t];
+        uint64_t kt = zkey[t];
         int r = 0;
-        for (int u = 0; u < cnt; ++u) r += key[u] < kt;
-        int32_t id = (int32_t)(uint32_t)kt;
-        kperm[lo + r] = id;
-        pos[lo + r] = make_float4(x[id] - ox, y[id] - oy, z[id] - oz, sp[id] == 0 ? h[id] : 0.0f);
+        for (int u = 0; u < cnt; ++u) r += zkey[u] < kt;
+        const float4 c = pm[t];
+        kperm[lo + r] = (int32_t)(uint32_t)kt;
+        pos[lo + r] = make_float4(c.x - ox, c.y - oy, c.z - oz, c.w);
     }
-    __syncthreads();
-    nk = 0;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) key[t] = gkey[nk++];
-    __syncthreads();
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        uint64_t kt = key[t];
+        uint64_t kt = gkey[t];
         int r = 0;
-        for (int u = 0; u < cnt; ++u) r += key[u] < kt;
-        int32_t id = (int32_t)(uint32_t)kt;
-        kperm_g[lo + r] = id;
-        pos_g[lo + r] = make_float4(x[id] - ox, y[id] - oy, z[id] - oz, sp[id] == 0 ? h[id] : 0.0f);
+        for (int u = 0; u < cnt; ++u) r += gkey[u] < kt;
+        const float4 c = pm[t];
+        kperm_g[lo + r] = (int32_t)(uint32_t)kt;
+        pos_g[lo + r] = make_float4(c.x - ox, c.y - oy, c.z - oz, c.w);
     }
 }
 
@@ -1020,19 +1113,28 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             ALLOC(node_box, float, 6 * shape->n_nodes);
             ALLOC(node_hmax, float, shape->n_nodes);
             tr.mark("shape");
-            int32_t *Lc[3], *Ln[3];
+            int32_t *Lc[3];
             size_t nb = sizeof(int32_t) * (size_t)(n > 0 ? n : 1);
             uint32_t *keys = (uint32_t *)crk_scratch(ctx, 1, nb);
+            int32_t *R[3], *Ac[3][2], *An[3][2];
             for (int a = 0; a < 3; ++a) {
                 Lc[a] = (int32_t *)crk_scratch(ctx, 2 + a, nb);
-                Ln[a] = (int32_t *)crk_scratch(ctx, 5 + a, nb);
+                R[a] = (int32_t *)crk_scratch(ctx, 5 + a, nb);
+                for (int c = 0; c < 2; ++c) {
+                    Ac[a][c] = (int32_t *)crk_scratch(ctx, 19 + 2 * a + c, nb);
+                    An[a][c] = (int32_t *)crk_scratch(ctx, 25 + 2 * a + c, nb);
+                }
             }
             int32_t *node_of = (int32_t *)crk_scratch(ctx, 8, nb);
             int32_t *node_nx = (int32_t *)crk_scratch(ctx, 9, nb);
-            uint8_t *side = (uint8_t *)crk_scratch(ctx, 10, (size_t)(n > 0 ? n : 1));
+            int32_t *mem = (int32_t *)crk_scratch(ctx, 10, nb);
             int32_t *flag = (int32_t *)crk_scratch(ctx, 11, nb + 3 * sizeof(int32_t) * (size_t)(n / 2048 + 2));
-            if (!keys || !node_of || !node_nx || !side || !flag || !Lc[0] || !Lc[1] || !Lc[2] || !Ln[0] || !Ln[1] ||
-                !Ln[2]) {
+            size_t max_seg = 1;
+            for (size_t m : shape->level_size) max_seg = std::max(max_seg, m);
+            int32_t *thr = (int32_t *)crk_scratch(ctx, 31, sizeof(int32_t) * max_seg);
+            bool ok = keys && node_of && node_nx && mem && flag && thr;
+            for (int a = 0; a < 3; ++a) ok = ok && Lc[a] && R[a] && Ac[a][0] && Ac[a][1] && An[a][0] && An[a][1];
+            if (!ok) {
                 rc = crk_fail(ctx, CRK_ENOMEM, "scratch");
                 goto fail;
             }
@@ -1050,7 +1152,12 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                 }
             }
             tr.mark("axis sorts");
+            const AxisOrder ord{{Lc[0], Lc[1], Lc[2]}, {R[0], R[1], R[2]}};
             if (n > 0) {
+                rank_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, ord, R[0], R[1], R[2]);
+                rank_lists_kernel<<<crk_grid(n, 256), 256, 0, st>>>(
+                    n, ord, RankListsOut{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}});
+                ctx->launches += 2;
                 if (box_of) {
                     init_node_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, box_of, seg_of_box, node_of);
                     ++ctx->launches;
@@ -1062,23 +1169,28 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             for (size_t d = 0; d < shape->level_size.size(); ++d) {
                 int m = (int)shape->level_size[d];
                 int32_t *tab = shape->dtab + shape->level_off[d];
-                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m};
-                rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, Lc[0], Lc[1], Lc[2], p->x, p->y, p->z,
-                                                                  node_box);
-                rcb_side_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side, node_nx);
+                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m, thr};
+                const RankLists Lr{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}};
+                const RankListsOut Lo{{{An[0][0], An[0][1]}, {An[1][0], An[1][1]}, {An[2][0], An[2][1]}}};
+                rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, Lr, ord, p->x, p->y, p->z, node_box);
                 const int64_t nbt = (n + kPartTile - 1) / kPartTile;
-                rcb_count3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side,
-                                                                          flag, nbt);
+                rcb_count3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lr, flag, nbt);
                 rcb_scan3_kernel<<<1, 1024, 0, st>>>(flag, nbt);
-                rcb_scatter3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lc[0], Lc[1], Lc[2], side,
-                                                                            flag, nbt, Ln[0], Ln[1], Ln[2], flags + 5);
-                ctx->launches += 5;
-                for (int b = 0; b < 3; ++b) std::swap(Lc[b], Ln[b]);
+                rcb_scatter3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lr, flag, nbt, Lo, node_nx,
+                                                                            flags + 5);
+                ctx->launches += 4;
+                for (int a = 0; a < 3; ++a)
+                    for (int c = 0; c < 2; ++c) std::swap(Ac[a][c], An[a][c]);
                 std::swap(node_of, node_nx);
                 KCHECK("rcb level");
             }
+            if (n > 0) {
+                rank_members_kernel<<<crk_grid(n, 256), 256, 0, st>>>(
+                    n, RankLists{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}}, ord, mem);
+                ++ctx->launches;
+            }
             tr.mark("rcb levels");
-            members = Lc[0];
+            members = mem;
         }
         lv->n_leaves = nl;
         ALLOC(lv->perm, int32_t, n);

@@ -140,6 +140,58 @@ struct GravStage {
         p.a3[2 * p.n + orig] = s.az;
     }
     __device__ static void finish_other(const P &, int32_t) {}
+
+    // Two candidates per lane step with packed FP32 (f32x2) arithmetic: the
+    // same operations and roundings per pair as interact, half the
+    // instructions.  Rec2 holds two candidates field-interleaved, so each
+    // field pair is one register pair.
+    static constexpr bool kPair = true;
+    struct __align__(16) Rec2 {
+        float2 x, y, z, m;
+    };
+    struct I2 {
+        float2 nx, ny, nz;  // -x_i, broadcast
+        float2 ax, ay, az;
+        int cnt;
+    };
+    __device__ static void put2(Rec2 *b, int c, const Rec &r) {
+        float *d = reinterpret_cast<float *>(b + (c >> 1)) + (c & 1);
+        d[0] = r.x; d[2] = r.y; d[4] = r.z; d[6] = r.m;
+    }
+    __device__ static Rec far_dummy(float fx, float fy, float fz) { return {fx, fy, fz, 0.0f}; }
+    __device__ static void init2(const P &, I2 &s, const Rec &ri) {
+        s.nx = make_float2(-ri.x, -ri.x);
+        s.ny = make_float2(-ri.y, -ri.y);
+        s.nz = make_float2(-ri.z, -ri.z);
+        s.ax = s.ay = s.az = make_float2(0.f, 0.f);
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact2(const P &p, I2 &s, const Rec2 &rj) {
+        const float2 dx = __fadd2_rn(rj.x, s.nx), dy = __fadd2_rn(rj.y, s.ny), dz = __fadd2_rn(rj.z, s.nz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const float2 t = __fadd2_rn(r2, make_float2(p.eps2, p.eps2));
+        const float2 rinv = make_float2(rsqrtf(t.x), rsqrtf(t.y));
+        const float2 r3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+        // -P5(r^2) by Horner with negated coefficients (negation is exact)
+        float2 np = __ffma2_rn(make_float2(-p.c[5], -p.c[5]), r2, make_float2(-p.c[4], -p.c[4]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[3], -p.c[3]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[2], -p.c[2]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[1], -p.c[1]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[0], -p.c[0]));
+        const float2 g = __fmul2_rn(rj.m, __fadd2_rn(r3, np));
+        const bool in0 = r2.x < p.rc2, in1 = r2.y < p.rc2;
+        const float2 f = make_float2(in0 ? g.x : 0.0f, in1 ? g.y : 0.0f);
+        s.ax = __ffma2_rn(f, dx, s.ax);
+        s.ay = __ffma2_rn(f, dy, s.ay);
+        s.az = __ffma2_rn(f, dz, s.az);
+        if (kCount) s.cnt += (int)in0 + (int)in1;
+    }
+    __device__ static void finish2(const P &p, I2 &s, int32_t orig) {
+        p.a3[orig] = s.ax.x + s.ax.y;
+        p.a3[p.n + orig] = s.ay.x + s.ay.y;
+        p.a3[2 * p.n + orig] = s.az.x + s.az.y;
+    }
 };
 
 struct GravAdjP {
@@ -202,6 +254,79 @@ struct GravAdjStage {
         p.gm[o] = s.gm;
     }
     __device__ static void finish_other(const P &, int32_t) {}
+
+    // Two candidates per lane step with packed FP32 (f32x2) arithmetic (see GravStage).
+    static constexpr bool kPair = true;
+    struct __align__(16) Rec2 {
+        float2 x, y, z, m;
+        float2 bx, by, bz, pad;
+    };
+    struct I2 {
+        float2 nx, ny, nz;     // -x_i, broadcast
+        float2 mi, nbx, nby, nbz;  // m_i, -abar_i, broadcast
+        float2 gx, gy, gz, sg;  // sg accumulates g (abar_j . d); gm = -sg
+        int cnt;
+    };
+    __device__ static void put2(Rec2 *b, int c, const Rec &r) {
+        float *d = reinterpret_cast<float *>(b + (c >> 1)) + (c & 1);
+        d[0] = r.x; d[2] = r.y; d[4] = r.z; d[6] = r.m;
+        d[8] = r.bx; d[10] = r.by; d[12] = r.bz; d[14] = 0.0f;
+    }
+    __device__ static Rec far_dummy(float fx, float fy, float fz) { return {fx, fy, fz, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}; }
+    __device__ static void init2(const P &, I2 &s, const Rec &ri) {
+        s.nx = make_float2(-ri.x, -ri.x);
+        s.ny = make_float2(-ri.y, -ri.y);
+        s.nz = make_float2(-ri.z, -ri.z);
+        s.mi = make_float2(ri.m, ri.m);
+        s.nbx = make_float2(-ri.bx, -ri.bx);
+        s.nby = make_float2(-ri.by, -ri.by);
+        s.nbz = make_float2(-ri.bz, -ri.bz);
+        s.gx = s.gy = s.gz = s.sg = make_float2(0.f, 0.f);
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact2(const P &p, I2 &s, const Rec2 &rj) {
+        const float2 dx = __fadd2_rn(rj.x, s.nx), dy = __fadd2_rn(rj.y, s.ny), dz = __fadd2_rn(rj.z, s.nz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const float2 t = __fadd2_rn(r2, make_float2(p.eps2, p.eps2));
+        const float2 rinv = make_float2(rsqrtf(t.x), rsqrtf(t.y));
+        const float2 ri2 = __fmul2_rn(rinv, rinv);
+        const float2 r3 = __fmul2_rn(ri2, rinv);
+        float2 np = __ffma2_rn(make_float2(-p.c[5], -p.c[5]), r2, make_float2(-p.c[4], -p.c[4]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[3], -p.c[3]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[2], -p.c[2]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[1], -p.c[1]));
+        np = __ffma2_rn(np, r2, make_float2(-p.c[0], -p.c[0]));  // -P5
+        const float c5 = -5.0f * p.c[5], c4 = -4.0f * p.c[4], c3 = -3.0f * p.c[3], c2 = -2.0f * p.c[2];
+        float2 ndp = __ffma2_rn(make_float2(c5, c5), r2, make_float2(c4, c4));
+        ndp = __ffma2_rn(ndp, r2, make_float2(c3, c3));
+        ndp = __ffma2_rn(ndp, r2, make_float2(c2, c2));
+        ndp = __ffma2_rn(ndp, r2, make_float2(-p.c[1], -p.c[1]));  // -P5'
+        const bool in0 = r2.x < p.rc2, in1 = r2.y < p.rc2;
+        const float2 gv = __fadd2_rn(r3, np);
+        // g' (times 2): 2 (-1.5 r^-5 - P5')
+        const float2 dv = __fmul2_rn(make_float2(2.0f, 2.0f),
+                                     __ffma2_rn(__fmul2_rn(make_float2(-1.5f, -1.5f), r3), ri2, ndp));
+        const float2 g = make_float2(in0 ? gv.x : 0.0f, in1 ? gv.y : 0.0f);
+        const float2 dg2 = make_float2(in0 ? dv.x : 0.0f, in1 ? dv.y : 0.0f);
+        // w = m_i abar_j - m_j abar_i
+        const float2 wx = __ffma2_rn(s.mi, rj.bx, __fmul2_rn(rj.m, s.nbx));
+        const float2 wy = __ffma2_rn(s.mi, rj.by, __fmul2_rn(rj.m, s.nby));
+        const float2 wz = __ffma2_rn(s.mi, rj.bz, __fmul2_rn(rj.m, s.nbz));
+        const float2 dw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
+        const float2 k = __fmul2_rn(dg2, dw);
+        s.gx = __ffma2_rn(g, wx, __ffma2_rn(k, dx, s.gx));
+        s.gy = __ffma2_rn(g, wy, __ffma2_rn(k, dy, s.gy));
+        s.gz = __ffma2_rn(g, wz, __ffma2_rn(k, dz, s.gz));
+        s.sg = __ffma2_rn(g, __ffma2_rn(rj.bx, dx, __ffma2_rn(rj.by, dy, __fmul2_rn(rj.bz, dz))), s.sg);
+        if (kCount) s.cnt += (int)in0 + (int)in1;
+    }
+    __device__ static void finish2(const P &p, I2 &s, int32_t o) {
+        p.gx3[o] = s.gx.x + s.gx.y;
+        p.gx3[p.n + o] = s.gy.x + s.gy.y;
+        p.gx3[2 * p.n + o] = s.gz.x + s.gz.y;
+        p.gm[o] = -(s.sg.x + s.sg.y);
+    }
 };
 
 struct GeomP {
@@ -212,6 +337,7 @@ struct GeomP {
 };
 
 struct GeomStage {
+    static constexpr bool kPair = false;
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
@@ -259,6 +385,7 @@ struct GeomAdjP {
 };
 
 struct GeomAdjStage {
+    static constexpr bool kPair = false;
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
@@ -317,6 +444,7 @@ struct CorrP {
 };
 
 struct CorrStage {
+    static constexpr bool kPair = false;
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
@@ -460,6 +588,7 @@ struct HydroP {
 };
 
 struct HydroStage {
+    static constexpr bool kPair = false;
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = true;
     static constexpr bool kTag = false;
@@ -579,6 +708,7 @@ struct ListP {
 
 template <bool kGas>
 struct ListStage {
+    static constexpr bool kPair = false;
     static constexpr bool kGasOnly = kGas;
     static constexpr bool kCons = false;
     static constexpr bool kTag = true;
@@ -739,6 +869,104 @@ __device__ __forceinline__ void tile_group(const LeafView &lv, const typename S:
     }
 }
 
+// tile_group for stages with packed two-candidate interactions (kPair): the
+// candidate buffer holds field-interleaved candidate pairs; an odd tail is
+// padded with a massless dummy outside every i's cut, which adds exact zeros.
+template <class S, bool kCount>
+__device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typename S::P &p,
+                                                const typename S::Rec *__restrict__ rec, typename S::Rec2 *buf,
+                                                int64_t a, int lo, int g0, int hi, int lane) {
+    using Rec = typename S::Rec;
+    static_assert(!S::kCons && !S::kGasOnly && !S::kTag, "packed sweep: gravity-type stages only");
+    const unsigned below = lanemask_lt();
+    const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+    const int i = g0 + lane;
+    const bool act = i < hi;
+    const Rec ri = rec[act ? i : g0];
+    typename S::I2 st;
+    S::init2(p, st, ri);
+    float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
+    float hm = lv.pos[act ? i : g0].w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bl0 = fminf(bl0, __shfl_xor_sync(CRK_FULL_MASK, bl0, o));
+        bl1 = fminf(bl1, __shfl_xor_sync(CRK_FULL_MASK, bl1, o));
+        bl2 = fminf(bl2, __shfl_xor_sync(CRK_FULL_MASK, bl2, o));
+        bh0 = fmaxf(bh0, __shfl_xor_sync(CRK_FULL_MASK, bh0, o));
+        bh1 = fmaxf(bh1, __shfl_xor_sync(CRK_FULL_MASK, bh1, o));
+        bh2 = fmaxf(bh2, __shfl_xor_sync(CRK_FULL_MASK, bh2, o));
+        hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
+    }
+    const float far = 2.0f * S::leaf_cut(p, hm, hm) + 1.0f;
+    const Rec dummy = S::far_dummy(bh0 + far, bh1 + far, bh2 + far);
+    auto sweep = [&](int cnt) {
+        if (cnt & 1) {
+            if (lane == 0) S::put2(buf, cnt, dummy);
+            ++cnt;
+        }
+        __syncwarp();
+        for (int k = 0; k < (cnt >> 1); ++k) S::template interact2<kCount>(p, st, buf[k]);
+        __syncwarp();
+    };
+    int cnt = 0;
+    for (int e = ib; e < ie; ++e) {
+        const crk_image im = lv.img[e];
+        const int jlo = lv.leaf_start[im.b];
+        const int jhi = lv.leaf_start[im.b + 1];
+        {
+            const float *bb = lv.bbox + 6 * (int64_t)im.b;
+            float gx = fmaxf(fmaxf(im.sx - bh0, bl0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+            float gy = fmaxf(fmaxf(im.sy - bh1, bl1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+            float gz = fmaxf(fmaxf(im.sz - bh2, bl2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+            float cut = S::leaf_cut(p, hm, lv.hmax[im.b]);
+            if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+        }
+        for (int j0 = jlo; j0 < jhi; j0 += 32) {
+            const int j = j0 + lane;
+            const bool jv = j < jhi;
+            Rec rj;
+            bool keep = false;
+            if (jv) {
+                rj = rec[j];
+                S::shift(rj, im.sx, im.sy, im.sz);
+                float dx = fmaxf(fmaxf(bl0 - rj.x, rj.x - bh0), 0.f);
+                float dy = fmaxf(fmaxf(bl1 - rj.y, rj.y - bh1), 0.f);
+                float dz = fmaxf(fmaxf(bl2 - rj.z, rj.z - bh2), 0.f);
+                float cut = S::box_cut(p, hm, rj);
+                keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
+            }
+            const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+            if (keep) S::put2(buf, cnt + __popc(m & below), rj);
+            cnt += __popc(m);
+            if (cnt >= 32) {
+                sweep(cnt);
+                cnt = 0;
+            }
+        }
+    }
+    sweep(cnt);
+    if (act) S::finish2(p, st, lv.korder ? i : lv.kperm[i]);
+    if (kCount) {
+        int c = act ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
+        if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+    }
+}
+
+// one i-group, tiles (packed sweep where the stage has one)
+template <class S, bool kCount>
+__device__ __forceinline__ void tile_group_any(const LeafView &lv, const typename S::P &p,
+                                               const typename S::Rec *__restrict__ rec, typename S::Rec *buf,
+                                               int64_t a, int lo, int g0, int hi, int lane, double cons_acc[4]) {
+    if constexpr (S::kPair) {
+        static_assert(sizeof(typename S::Rec2) == 2 * sizeof(typename S::Rec), "pair record layout");
+        tile_group_pair<S, kCount>(lv, p, rec, reinterpret_cast<typename S::Rec2 *>(buf), a, lo, g0, hi, lane);
+    } else {
+        tile_group<S, kCount>(lv, p, rec, buf, a, lo, g0, hi, lane, cons_acc);
+    }
+}
+
 // Per-block partial of the FP64 conservation sums in a fixed order (reduced by
 // cons_reduce_kernel: deterministic for a fixed assignment of work to blocks).
 __device__ __forceinline__ void cons_block_partial(double (*cons_sh)[4], const double cons_acc[4],
@@ -762,7 +990,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
                                                         const typename S::Rec *__restrict__ rec,
                                                         double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
-    __shared__ Rec buf[kWarps][kCap];
+    __shared__ __align__(16) Rec buf[kWarps][kCap];
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -771,7 +999,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
         const int lo = lv.leaf_start[a];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
         for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32)
-            tile_group<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
+            tile_group_any<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
     }
     if constexpr (S::kCons) {
         if (cons_part) cons_block_partial(cons_sh, cons_acc, cons_part);
@@ -793,7 +1021,7 @@ __global__ void __launch_bounds__(kThreads) pair_group_kernel(LeafView lv, typen
                                                               const typename S::Rec *__restrict__ rec,
                                                               GroupTable gt, double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
-    __shared__ Rec buf[kWarps][kCap];
+    __shared__ __align__(16) Rec buf[kWarps][kCap];
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -802,7 +1030,7 @@ __global__ void __launch_bounds__(kThreads) pair_group_kernel(LeafView lv, typen
         const int lo = lv.leaf_start[a];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
         const int g0 = lo + 32 * (int)(grp - gt.gstart[a]);
-        tile_group<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
+        tile_group_any<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
     }
     if constexpr (S::kCons) {
         if (cons_part) cons_block_partial(cons_sh, cons_acc, cons_part);
