@@ -67,10 +67,12 @@ struct crk_ctx {
 struct crk_nlist {
     int32_t *gstart = nullptr;  // [n_leaves + 1] first group of each leaf
     int32_t *gleaf = nullptr;   // [groups] leaf of each group
-    int32_t *goff = nullptr;    // [groups + 1] group offsets, units of 32 entries
+    int32_t *goff = nullptr;    // [groups + 1] list row offsets, units of 32 entries
     int32_t *cnt = nullptr;     // [n] list length per kernel-order position
-    uint32_t *list = nullptr;
-    int64_t groups = 0, entries = 0;
+    uint16_t *list = nullptr;   // per-lane indices into the group's j table, k-major rows of 32
+    int32_t *uoff = nullptr;    // [groups + 1] first j-table entry of each group
+    uint32_t *ucode = nullptr;  // j-table entries: image << 10 | j inside the j-leaf
+    int64_t groups = 0, entries = 0, table = 0;
 };
 
 struct crk_leaves {

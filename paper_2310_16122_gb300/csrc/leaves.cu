@@ -28,24 +28,44 @@ __device__ __forceinline__ uint32_t coord_key(float x) {
 }
 
 // Positions in [0, L_box), gas h > 0 and finite; largest gas h per box.
+// Counts and maxima are combined per warp first, so the global atomics are
+// one per warp and box (millions of same-address atomics would serialise).
 __global__ void validate_kernel(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
                                 const uint8_t *__restrict__ sp, const float *__restrict__ h, int64_t n,
                                 const int32_t *__restrict__ box_of, const float *__restrict__ box_L,
                                 int32_t *__restrict__ flags /* [0] bad pos, [1] bad h, [2] n_gas */,
                                 unsigned *__restrict__ hmax_bits /* per box */) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int b = box_of ? box_of[i] : 0;
-    const float L = box_L[b];
-    float c[3] = {x[i], y[i], z[i]};
-    bool bad = false;
-    for (int a = 0; a < 3; ++a) bad |= !(c[a] >= 0.0f && c[a] < L);
-    if (bad) atomicAdd(&flags[0], 1);
-    if (sp[i] == 0) {
-        float hi = h[i];
-        if (!(hi > 0.0f) || !isfinite(hi)) atomicAdd(&flags[1], 1);
-        else atomicMax(&hmax_bits[b], __float_as_uint(hi));
-        atomicAdd(&flags[2], 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < n;
+    const int b = in && box_of ? box_of[i] : 0;
+    bool bad = false, gas = false, badh = false;
+    unsigned hb = 0u;
+    if (in) {
+        const float L = box_L[b];
+        float c[3] = {x[i], y[i], z[i]};
+        for (int a = 0; a < 3; ++a) bad |= !(c[a] >= 0.0f && c[a] < L);
+        gas = sp[i] == 0;
+        if (gas) {
+            const float hi = h[i];
+            badh = !(hi > 0.0f) || !isfinite(hi);
+            if (!badh) hb = __float_as_uint(hi);  // positive floats order like their bits
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned nbad = __reduce_add_sync(CRK_FULL_MASK, (unsigned)bad);
+    const unsigned nbadh = __reduce_add_sync(CRK_FULL_MASK, (unsigned)badh);
+    const unsigned ngas = __reduce_add_sync(CRK_FULL_MASK, (unsigned)gas);
+    if (lane == 0) {
+        if (nbad) atomicAdd(&flags[0], (int)nbad);
+        if (nbadh) atomicAdd(&flags[1], (int)nbadh);
+        if (ngas) atomicAdd(&flags[2], (int)ngas);
+    }
+    const int b0 = __shfl_sync(CRK_FULL_MASK, b, 0);
+    if (__all_sync(CRK_FULL_MASK, b == b0)) {
+        const unsigned m = __reduce_max_sync(CRK_FULL_MASK, hb);
+        if (lane == 0 && m) atomicMax(&hmax_bits[b0], m);
+    } else if (hb) {
+        atomicMax(&hmax_bits[b], hb);
     }
 }
 
@@ -101,7 +121,12 @@ struct LevelDev {
     const int32_t *lo, *hi, *k, *child, *node;
     int32_t *axis;
     const int32_t *leftbase;  // sum of k over the earlier segments of the level
-    int32_t *thr;             // rank along the split axis of the first right-going particle
+};
+
+// everything the partition needs about one segment, in one 32-byte record
+struct __align__(16) SegRec {
+    int32_t lo, hi, k, child;
+    int32_t axis, leftbase, thr, pad;  // thr: rank along the split axis of the first right-going particle
 };
 
 // The three axis lists carry ranks, not particle ids.  S[t] is the stable
@@ -167,12 +192,17 @@ __global__ void rank_members_kernel(int64_t n, RankLists L, AxisOrder o, int32_t
 // per split node: tight box from the ends of its three list segments, split
 // axis (longest extent, ties to the lower axis), rank threshold
 __global__ void rcb_axis_kernel(int nseg, LevelDev lv, RankLists L, AxisOrder o, const float *__restrict__ x,
-                                const float *__restrict__ y, const float *__restrict__ z, float *__restrict__ node_box) {
+                                const float *__restrict__ y, const float *__restrict__ z, float *__restrict__ node_box,
+                                SegRec *__restrict__ seg) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     int k = lv.k[s];
-    if (k <= 0) return;
     int lo = lv.lo[s], hi = lv.hi[s];
+    SegRec r{lo, hi, k, lv.child[s], 0, lv.leftbase[s], 0, 0};
+    if (k <= 0) {
+        seg[s] = r;
+        return;
+    }
     const float *cs[3] = {x, y, z};
     float blo[3], bhi[3];
     double ext[3];
@@ -185,7 +215,9 @@ __global__ void rcb_axis_kernel(int nseg, LevelDev lv, RankLists L, AxisOrder o,
     if (ext[1] > ext[axis]) axis = 1;
     if (ext[2] > ext[axis]) axis = 2;
     lv.axis[s] = axis;
-    lv.thr[s] = o.R[axis][rank_entry_id(L, o, axis, lo + k)];
+    r.axis = axis;
+    r.thr = o.R[axis][rank_entry_id(L, o, axis, lo + k)];
+    seg[s] = r;
     float *nb = node_box + 6 * (int64_t)lv.node[s];
     for (int a = 0; a < 3; ++a) {
         nb[a] = blo[a];
@@ -203,11 +235,11 @@ constexpr int kPartItems = 8;
 constexpr int kPartTile = kPartThreads * kPartItems;
 
 // left flags of entry p (bit b: list b), or 0 for entries of unsplit segments
-__device__ __forceinline__ unsigned rcb_left3(const LevelDev &lv, const RankLists &L, int s, int64_t p) {
-    const int ks = lv.k[s];
+__device__ __forceinline__ unsigned rcb_left3(const SegRec &sr, const RankLists &L, int64_t p) {
+    const int ks = sr.k;
     if (ks <= 0) return 0u;
-    const int ax = lv.axis[s], lo = lv.lo[s];
-    const int32_t th = lv.thr[s];
+    const int ax = sr.axis, lo = sr.lo;
+    const int32_t th = sr.thr;
     unsigned f = 0;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -223,8 +255,9 @@ __device__ __forceinline__ unsigned rcb_left3(const LevelDev &lv, const RankList
     return f;
 }
 
-__global__ void rcb_count3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of, RankLists L,
-                                  int32_t *__restrict__ bsum, int64_t nb) {
+__global__ void __launch_bounds__(kPartThreads) rcb_count3_kernel(int64_t n, const SegRec *__restrict__ segs,
+                                                                   const int32_t *__restrict__ node_of, RankLists L,
+                                                                   int32_t *__restrict__ bsum, int64_t nb) {
     __shared__ int32_t wt[32];
     const int64_t base = (int64_t)blockIdx.x * kPartTile;
     int32_t seg[kPartItems];
@@ -237,7 +270,11 @@ __global__ void rcb_count3_kernel(int64_t n, LevelDev lv, const int32_t *__restr
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
         int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
-        unsigned f = seg[k] >= 0 ? rcb_left3(lv, L, seg[k], p) : 0u;
+        unsigned f = 0u;
+        if (seg[k] >= 0) {
+            const SegRec sr = segs[seg[k]];
+            f = rcb_left3(sr, L, p);
+        }
         c[0] += f & 1u;
         c[1] += (f >> 1) & 1u;
         c[2] += (f >> 2) & 1u;
@@ -273,9 +310,11 @@ __global__ void rcb_scan3_kernel(int32_t *__restrict__ bsum, int64_t nb) {
 // earlier (row, warp) pairs plus the ballot rank inside its warp.
 constexpr int kPartWarps = kPartThreads / 32;
 
-__global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__restrict__ node_of, RankLists L,
-                                    const int32_t *__restrict__ bsum, int64_t nb, RankListsOut O,
-                                    int32_t *__restrict__ node_of_next, int32_t *__restrict__ err) {
+__global__ void __launch_bounds__(kPartThreads, 4) rcb_scatter3_kernel(int64_t n, const SegRec *__restrict__ segs,
+                                                                      const int32_t *__restrict__ node_of, RankLists L,
+                                                                      const int32_t *__restrict__ bsum, int64_t nb,
+                                                                      RankListsOut O, int32_t *__restrict__ node_of_next,
+                                                                      int32_t *__restrict__ err) {
     static_assert(kPartItems * kPartWarps == 64, "prefix table: two entries per lane of one warp");
     __shared__ int32_t wc[3][kPartItems * kPartWarps];  // left count per (list, row, warp), then its prefix
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -291,7 +330,11 @@ __global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__res
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
         int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
-        f[k] = seg[k] >= 0 ? rcb_left3(lv, L, seg[k], p) : 0u;
+        f[k] = 0u;
+        if (seg[k] >= 0) {
+            const SegRec sr = segs[seg[k]];
+            f[k] = rcb_left3(sr, L, p);
+        }
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const unsigned m = __ballot_sync(0xffffffffu, (f[k] >> b) & 1u);
@@ -320,11 +363,11 @@ __global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__res
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
         const int64_t p = base + (int64_t)k * kPartThreads + threadIdx.x;
-        const int s = seg[k];
-        const bool valid = s >= 0;
-        const int ks = valid ? lv.k[s] : 0;
-        const int lo = valid ? lv.lo[s] : 0;
-        if (valid) node_of_next[p] = lv.child[s] + ((ks > 0 && (int)p - lo >= ks) ? 1 : 0);
+        const bool valid = seg[k] >= 0;
+        SegRec sr{0, 0, 0, 0, 0, 0, 0, 0};
+        if (valid) sr = segs[seg[k]];
+        const int ks = sr.k, lo = sr.lo;
+        if (valid) node_of_next[p] = sr.child + ((ks > 0 && (int)p - lo >= ks) ? 1 : 0);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const bool left = (f[k] >> b) & 1u;
@@ -334,9 +377,9 @@ __global__ void rcb_scatter3_kernel(int64_t n, LevelDev lv, const int32_t *__res
             int64_t np = p;
             if (ks > 0) {
                 // left-going entries before p in this segment
-                const int lb = tile0[b] + wc[b][k * kPartWarps + warp] + __popc(m & below) - lv.leftbase[s];
+                const int lb = tile0[b] + wc[b][k * kPartWarps + warp] + __popc(m & below) - sr.leftbase;
                 np = left ? lo + lb : lo + ks + ((int)p - lo - lb);
-                if (!(np >= lo && np < lv.hi[s])) {
+                if (!(np >= lo && np < sr.hi)) {
                     atomicAdd(err, 1);  // inconsistent partition: reported, never written out of the segment
                     continue;
                 }
@@ -1131,8 +1174,8 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             int32_t *flag = (int32_t *)crk_scratch(ctx, 11, nb + 3 * sizeof(int32_t) * (size_t)(n / 2048 + 2));
             size_t max_seg = 1;
             for (size_t m : shape->level_size) max_seg = std::max(max_seg, m);
-            int32_t *thr = (int32_t *)crk_scratch(ctx, 31, sizeof(int32_t) * max_seg);
-            bool ok = keys && node_of && node_nx && mem && flag && thr;
+            SegRec *segs = (SegRec *)crk_scratch(ctx, 31, sizeof(SegRec) * max_seg);
+            bool ok = keys && node_of && node_nx && mem && flag && segs;
             for (int a = 0; a < 3; ++a) ok = ok && Lc[a] && R[a] && Ac[a][0] && Ac[a][1] && An[a][0] && An[a][1];
             if (!ok) {
                 rc = crk_fail(ctx, CRK_ENOMEM, "scratch");
@@ -1169,14 +1212,14 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             for (size_t d = 0; d < shape->level_size.size(); ++d) {
                 int m = (int)shape->level_size[d];
                 int32_t *tab = shape->dtab + shape->level_off[d];
-                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m, thr};
+                LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m};
                 const RankLists Lr{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}};
                 const RankListsOut Lo{{{An[0][0], An[0][1]}, {An[1][0], An[1][1]}, {An[2][0], An[2][1]}}};
-                rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, Lr, ord, p->x, p->y, p->z, node_box);
+                rcb_axis_kernel<<<crk_grid(m, 128), 128, 0, st>>>(m, dv, Lr, ord, p->x, p->y, p->z, node_box, segs);
                 const int64_t nbt = (n + kPartTile - 1) / kPartTile;
-                rcb_count3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lr, flag, nbt);
+                rcb_count3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, segs, node_of, Lr, flag, nbt);
                 rcb_scan3_kernel<<<1, 1024, 0, st>>>(flag, nbt);
-                rcb_scatter3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, dv, node_of, Lr, flag, nbt, Lo, node_nx,
+                rcb_scatter3_kernel<<<(unsigned)nbt, kPartThreads, 0, st>>>(n, segs, node_of, Lr, flag, nbt, Lo, node_nx,
                                                                             flags + 5);
                 ctx->launches += 4;
                 for (int a = 0; a < 3; ++a)

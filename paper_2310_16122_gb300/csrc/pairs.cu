@@ -22,7 +22,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCap = 64;                     // per-warp candidate buffer
-constexpr int kGroupImgCap = 256;            // image table of one i-leaf staged per warp in shared memory
+constexpr int kGroupImgCap = 128;            // image table of one i-leaf staged per warp in shared memory
 constexpr float kSigmaW = 0.61548156588532f;  // 495 / (256 pi), Wendland C4 3-D normalisation
 
 struct LeafView {
@@ -694,12 +694,18 @@ struct HydroStage {
 };
 
 
-// Builds the exact neighbour lists (count pass, then fill pass): gas pairs
-// (r < h_i + h_j) or gravity pairs (r < r_cut).
+// Builds the exact neighbour lists of every i-group (count pass, then fill
+// pass): gas pairs (r < h_i + h_j) or gravity pairs (r < r_cut).  A group's
+// lists index a table of the distinct j the group needs (the union over its
+// lanes, in the order the sweep meets them), so that a pair kernel stages each
+// j of the group once and every lane reads its j from that table.
 struct ListP {
-    uint32_t *list;
-    const int32_t *gstart, *goff;
-    int32_t *cnt;
+    uint16_t *list;                    // fill: per-lane table indices, k-major rows of 32
+    uint32_t *ucode;                   // fill: table entries
+    const int32_t *gstart, *goff, *uoff;
+    int32_t *cnt;                      // count: list length per kernel-order position
+    int32_t *ucnt;                     // count: table size per group
+    int32_t *umax;                     // count: largest table (atomicMax)
     int fill;
     float rc2;
     int64_t n;
@@ -718,8 +724,11 @@ struct ListStage {
         uint32_t code, pad0, pad1, pad2;
     };
     struct I {
-        uint32_t *out;
-        int c;
+        uint16_t *out;
+        uint32_t *uout;
+        int64_t grp;
+        int c;    // this lane's list length
+        int u;    // table size (warp-uniform)
         int cnt;
     };
     __device__ static Rec gather(const P &, int32_t, float4 ps) { return {ps.x, ps.y, ps.z, ps.w, 0u, 0u, 0u, 0u}; }
@@ -735,9 +744,13 @@ struct ListStage {
     }
     __device__ static void init(const P &p, I &s, const Rec &, int64_t a, int q, int lane) {
         s.c = 0;
+        s.u = 0;
         s.cnt = 0;
-        s.out = p.fill ? p.list + (size_t)p.goff[p.gstart[a] + q] * 32 + lane : nullptr;
+        s.grp = p.gstart[a] + q;
+        s.out = p.fill ? p.list + (size_t)p.goff[s.grp] * 32 + lane : nullptr;
+        s.uout = p.fill ? p.ucode + p.uoff[s.grp] : nullptr;
     }
+    // called by all 32 lanes together (the sweep is warp-uniform)
     template <bool kCount>
     __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
         bool in;
@@ -751,13 +764,23 @@ struct ListStage {
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             in = r2 < p.rc2;
         }
-        if (in) {
-            if (s.out) s.out[(size_t)s.c * 32] = rj.code;
-            ++s.c;
+        const unsigned m = __ballot_sync(CRK_FULL_MASK, in);
+        if (m) {
+            if (in) {
+                if (s.out) s.out[(size_t)s.c * 32] = (uint16_t)s.u;
+                ++s.c;
+            }
+            if (s.uout && (int)(threadIdx.x & 31) == __ffs(m) - 1) s.uout[s.u] = rj.code;
+            ++s.u;
         }
     }
     __device__ static void finish(const P &p, I &s, const Rec &, int32_t, int64_t i) {
-        if (!p.fill) p.cnt[i] = s.c;
+        if (p.fill) return;
+        p.cnt[i] = s.c;
+        if ((threadIdx.x & 31) == 0) {  // lane 0 is always active
+            p.ucnt[s.grp] = s.u;
+            atomicMax(p.umax, s.u);
+        }
     }
     __device__ static void finish_other(const P &, int32_t) {}
 };
@@ -1330,25 +1353,37 @@ __global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, 
 // lanes (k beyond their length) idle.
 struct GasLists {
     const int32_t *gstart, *goff, *cnt;
-    const uint32_t *list;
+    const uint16_t *list;
+    const int32_t *uoff;
+    const uint32_t *ucode;
     const int32_t *gleaf;
     int64_t groups;
 };
 
-// Exact neighbour lists, one warp per i-group: each lane walks its own list;
-// the i-leaf's image table (first j of the image's leaf as a float bit
-// pattern in w, and the shift into the i frame) is staged in the warp's part
-// of shared memory, and the next record is fetched while the current pair is
-// evaluated.
+// j-table entries staged per warp in shared memory (records of at most 32
+// bytes; the hydro record is too large to stage, its lanes gather directly)
+template <class S>
+__host__ __device__ constexpr int table_cap() {
+    return sizeof(typename S::Rec) <= 32 ? 320 : 0;
+}
+
+// Exact neighbour lists, one warp per i-group.  The warp stages the group's
+// j table in shared memory (each distinct j of the group gathered once,
+// shifted into the i frame), then each lane walks its own list of table
+// indices.  Table entries beyond the staged capacity are gathered from global
+// memory through the leaf's image table.
 template <class S, bool kCount>
 __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S::P p,
                                                         const typename S::Rec *__restrict__ rec, GasLists gl,
                                                         double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
+    constexpr int kTab = table_cap<S>();
+    extern __shared__ __align__(16) unsigned char list_dyn[];
     __shared__ double cons_sh[kWarps][4];
     __shared__ float4 itab_all[kWarps][kGroupImgCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *itab = itab_all[warp];
+    Rec *table = reinterpret_cast<Rec *>(list_dyn) + (size_t)warp * kTab;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t grp = next_group(lv, -1, lane); grp < gl.groups; grp = next_group(lv, grp, lane)) {
         const int64_t a = gl.gleaf[grp];
@@ -1359,25 +1394,18 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
         const crk_image *imgs = lv.img + lv.img_start[a];
         const int nimg = lv.img_cnt[a];
         const bool staged = nimg <= kGroupImgCap;
+        __syncwarp();  // the previous group's tables are no longer read
         if (staged) {
-            __syncwarp();  // the previous group's table is no longer read
             for (int t = lane; t < nimg; t += 32) {
                 const crk_image im = imgs[t];
                 itab[t] = make_float4(im.sx, im.sy, im.sz, __int_as_float(lv.leaf_start[im.b]));
             }
             __syncwarp();
         }
-        const uint32_t *L = gl.list + (size_t)gl.goff[grp] * 32 + lane;
-        const int i = g0 + lane;
-        const bool act = i < hi;
-        const Rec ri = rec[act ? i : g0];
-        typename S::I st;
-        S::init(p, st, ri, a, q, lane);
-        const int c = act ? gl.cnt[i] : 0;
-        // entry k -> shifted record of j (shared-memory table, or the global image list for
-        // leaves with more images than the table holds)
-        auto fetch = [&](int k) -> Rec {
-            const uint32_t code = __ldg(L + (size_t)k * 32);
+        const uint32_t *U = gl.ucode + gl.uoff[grp];
+        const int nu = gl.uoff[grp + 1] - gl.uoff[grp];
+        // table entry -> shifted record of j
+        auto fetch = [&](uint32_t code) -> Rec {
             float4 t;
             if (staged) {
                 t = itab[code >> 10];
@@ -1389,23 +1417,50 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
             S::shift(r, t.x, t.y, t.z);
             return r;
         };
-        if (c > 0) {
-            Rec nxt = fetch(0);
-            for (int k = 0; k < c; ++k) {
-                const Rec rj = nxt;
-                if (k + 1 < c) nxt = fetch(k + 1);  // in flight while rj is evaluated
-                S::template interact<kCount>(p, st, ri, rj);
+        if constexpr (kTab > 0) {
+            const int ns = nu < kTab ? nu : kTab;
+#pragma unroll 4
+            for (int u = lane; u < ns; u += 32) table[u] = fetch(__ldg(U + u));
+            __syncwarp();
+        }
+        auto entry = [&](int idx) -> Rec {
+            if constexpr (kTab > 0) {
+                if (idx < kTab) return table[idx];
             }
+            return fetch(__ldg(U + idx));
+        };
+        const uint16_t *Lp = gl.list + (size_t)gl.goff[grp] * 32 + lane;
+        const int i = g0 + lane;
+        const bool act = i < hi;
+        const Rec ri = rec[act ? i : g0];
+        typename S::I st;
+        S::init(p, st, ri, a, q, lane);
+        const int c = act ? gl.cnt[i] : 0;
+        // indices four rows ahead, so their loads overlap the pair arithmetic
+        int k = 0;
+        int nx0 = 0 < c ? __ldg(Lp) : 0, nx1 = 1 < c ? __ldg(Lp + 32) : 0, nx2 = 2 < c ? __ldg(Lp + 64) : 0,
+            nx3 = 3 < c ? __ldg(Lp + 96) : 0;
+        for (; k < c; k += 4) {
+            const int i0 = nx0, i1 = nx1, i2 = nx2, i3 = nx3;
+            const uint16_t *Lk = Lp + (size_t)(k + 4) * 32;
+            nx0 = k + 4 < c ? __ldg(Lk) : 0;
+            nx1 = k + 5 < c ? __ldg(Lk + 32) : 0;
+            nx2 = k + 6 < c ? __ldg(Lk + 64) : 0;
+            nx3 = k + 7 < c ? __ldg(Lk + 96) : 0;
+            S::template interact<kCount>(p, st, ri, entry(i0));
+            if (k + 1 < c) S::template interact<kCount>(p, st, ri, entry(i1));
+            if (k + 2 < c) S::template interact<kCount>(p, st, ri, entry(i2));
+            if (k + 3 < c) S::template interact<kCount>(p, st, ri, entry(i3));
         }
         if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
         if constexpr (S::kCons) {
             double cc[4] = {0.0, 0.0, 0.0, 0.0};
             if (act) S::cons_terms(p, st, ri, lv.korder ? i : lv.kperm[i], cc);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int kk = 0; kk < 4; ++kk) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) cc[k] += __shfl_xor_sync(CRK_FULL_MASK, cc[k], o);
-                cons_acc[k] += cc[k];
+                for (int o = 16; o > 0; o >>= 1) cc[kk] += __shfl_xor_sync(CRK_FULL_MASK, cc[kk], o);
+                cons_acc[kk] += cc[kk];
             }
         }
         if (kCount) {
@@ -1418,6 +1473,18 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
     if constexpr (S::kCons) {
         if (cons_part) cons_block_partial(cons_sh, cons_acc, cons_part);
     }
+}
+
+// dynamic shared memory of list_kernel<S>, and the opt-in above the 48 KB default (once per kernel)
+template <class S, bool kCount>
+size_t list_kernel_smem() {
+    const size_t bytes = (size_t)kWarps * table_cap<S>() * sizeof(typename S::Rec);
+    static bool set = false;
+    if (!set) {
+        cudaFuncSetAttribute(list_kernel<S, kCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        set = true;
+    }
+    return bytes;
 }
 
 // groups of each leaf, and the leaf of each group
@@ -1490,11 +1557,13 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
                gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue, korder ? 1 : 0};
     if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
     if (lists) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.gleaf, nls.groups};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.ucode, nls.gleaf, nls.groups};
         if (p.count)
-            list_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
+            list_kernel<S, true><<<(unsigned)grid, kThreads, list_kernel_smem<S, true>(), ctx->stream>>>(v, p, rec, gl,
+                                                                                                       part);
         else
-            list_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, gl, part);
+            list_kernel<S, false><<<(unsigned)grid, kThreads, list_kernel_smem<S, false>(), ctx->stream>>>(v, p, rec, gl,
+                                                                                                         part);
     } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
         if (p.count)
             pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
@@ -1609,7 +1678,7 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     int32_t *gstart = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(nl + 1));
     int32_t *cnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)n);
     int32_t *ng = (int32_t *)crk_scratch(ctx, 6, sizeof(int32_t) * (size_t)(nl + 1));
-    int32_t *tot = (int32_t *)crk_scratch(ctx, 7, 64);
+    int32_t *tot = (int32_t *)crk_scratch(ctx, 7, 64);  // [0] groups, [1] rows, [2] table entries, [4] largest table
     if (!gstart || !cnt || !ng || !tot) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
     CRK_CUDA(ctx, cudaMemsetAsync(ng, 0, sizeof(int32_t) * (size_t)(nl + 1), st));
     list_group_count_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, kGas, ng);
@@ -1630,29 +1699,48 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     const GroupTable gt{gstart, gleaf, ngroups};
     const unsigned ggrid = (unsigned)((ngroups + kWarps - 1) / kWarps > 0 ? (ngroups + kWarps - 1) / kWarps : 1);
     const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
+    int32_t *ucnt = (int32_t *)crk_scratch(ctx, 9, sizeof(int32_t) * (size_t)(ngroups + 1));
+    if (!ucnt) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
+    CRK_CUDA(ctx, cudaMemsetAsync(ucnt, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
+    CRK_CUDA(ctx, cudaMemsetAsync(tot + 4, 0, sizeof(int32_t), st));
     gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
-    ListP pc{nullptr, gstart, nullptr, cnt, 0, rc2, n, nullptr};
+    ListP pc{nullptr, nullptr, gstart, nullptr, nullptr, cnt, ucnt, tot + 4, 0, rc2, n, nullptr};
     pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pc, rec, gt, nullptr);
     ctx->launches += 3;
     CRK_LAUNCH_CHECK(ctx, "neighbour counts");
     int32_t *goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+    int32_t *uoff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
     int32_t *gk = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(ngroups + 1));
-    if (!goff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
+    if (!goff || !uoff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
     CRK_CUDA(ctx, cudaMemsetAsync(gk, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
     list_group_k_kernel<<<(unsigned)nl, kThreads, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, kGas, gstart, cnt, gk);
     ++ctx->launches;
     rc = crk_exclusive_scan_i32(ctx, gk, goff, ngroups + 1, tot + 1);
     if (rc) return rc;
-    int32_t rows = 0;
-    CRK_CUDA(ctx, cudaMemcpyAsync(&rows, goff + ngroups, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    rc = crk_exclusive_scan_i32(ctx, ucnt, uoff, ngroups + 1, tot + 2);
+    if (rc) return rc;
+    int32_t sizes[5] = {0, 0, 0, 0, 0};
+    CRK_CUDA(ctx, cudaMemcpyAsync(sizes, tot, sizeof(sizes), cudaMemcpyDeviceToHost, st));
     CRK_CUDA(ctx, cudaStreamSynchronize(st));
+    const int32_t rows = sizes[1], umax = sizes[4];
+    const int64_t tsize = (int64_t)(uint32_t)sizes[2];
+    // table indices are 16-bit, and the offsets 32-bit: without lists the kernels use tiles
+    if (umax > 65535 || rows < 0 || sizes[2] < 0) {
+        if (ctx->trace) fprintf(stderr, "[crk] %s lists skipped (largest group table %d)\n", kGas ? "gas" : "gravity", umax);
+        return CRK_OK;
+    }
     const int64_t entries = (int64_t)rows * 32;
-    uint32_t *list = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(entries > 0 ? entries : 1));
-    if (!list) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
-    ListP pf{list, gstart, goff, cnt, 1, rc2, n, nullptr};
+    uint16_t *list = (uint16_t *)crk_leaves_alloc(ctx, lv, sizeof(uint16_t) * (size_t)(entries > 0 ? entries : 1));
+    uint32_t *ucode = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(tsize > 0 ? tsize : 1));
+    if (!list || !ucode)
+        return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
+    ListP pf{list, ucode, gstart, goff, uoff, cnt, nullptr, nullptr, 1, rc2, n, nullptr};
     pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "neighbour lists");
+    out.uoff = uoff;
+    out.ucode = ucode;
+    out.table = tsize;
     out.gstart = gstart;
     out.gleaf = gleaf;
     out.goff = goff;
@@ -1728,10 +1816,10 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.gleaf, nls.groups};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.ucode, nls.gleaf, nls.groups};
         const int64_t lgrid = (nls.groups + kWarps - 1) / kWarps;
-        list_kernel<GravStage, false><<<(unsigned)(lgrid > 0 ? lgrid : 1), kThreads, 0, ctx->stream>>>(v, p, rec, gl,
-                                                                                                     nullptr);
+        list_kernel<GravStage, false><<<(unsigned)(lgrid > 0 ? lgrid : 1), kThreads,
+                                        list_kernel_smem<GravStage, false>(), ctx->stream>>>(v, p, rec, gl, nullptr);
     } else {
         pair_kernel<GravStage, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, nullptr);
     }
@@ -1744,8 +1832,8 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
 // into the two kernel orders once; every intermediate (V, rho, A, B, dA, dB,
 // a, the cotangents) stays in kernel order, so it is written and read
 // coalesced instead of being scattered to the caller's order and gathered
-// back by the next kernel; the outputs the caller asked for are scattered once
-// at the end.
+// back by the next kernel; the outputs the caller asked for are gathered back
+// to the caller's order once at the end.
 namespace {
 
 // dst[c*n + q] = src[c*n + perm[q]] for c < ncomp (into kernel order)
@@ -1757,15 +1845,35 @@ __global__ void to_korder_kernel(int64_t n, int ncomp, const int32_t *__restrict
     for (int c = 0; c < ncomp; ++c) dst[c * n + q] = src[c * n + o];
 }
 
-// dst[c*n + o] = src[c*n + inv[o]]: back to the caller's order as a gather
-// through the inverse permutation (coalesced writes; a scatter would write
-// every 4-byte element into a separate sector)
-__global__ void from_korder_kernel(int64_t n, int ncomp, const int32_t *__restrict__ inv,
-                                   const float *__restrict__ src, float *__restrict__ dst) {
+
+// Several gathers through two permutations in one pass: column k gets
+// dst[o] = src[perm_sel[o]] (o in the destination order).  One thread loads
+// both permutation entries once and has every column's load in flight.
+constexpr int kMaxPermCols = 40;
+struct PermCol {
+    float *dst;
+    const float *src;
+    int sel;  // 0: first permutation, 1: second
+};
+struct PermCols {
+    PermCol c[kMaxPermCols];
+    int ncol;
+};
+
+__global__ void permute_cols_kernel(int64_t n, const int32_t *__restrict__ p0, const int32_t *__restrict__ p1,
+                                    PermCols cols) {
     int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n) return;
-    const int64_t q = inv[o];
-    for (int c = 0; c < ncomp; ++c) dst[c * n + o] = src[c * n + q];
+    const int64_t q0 = p0[o], q1 = p1[o];
+    // every load first: a store through one column could alias a later column's source as far as
+    // the compiler knows, which would serialise the gathers
+    float v[kMaxPermCols];
+#pragma unroll
+    for (int k = 0; k < kMaxPermCols; ++k)
+        if (k < cols.ncol) v[k] = __ldg(cols.c[k].src + (cols.c[k].sel ? q1 : q0));
+#pragma unroll
+    for (int k = 0; k < kMaxPermCols; ++k)
+        if (k < cols.ncol) cols.c[k].dst[o] = v[k];
 }
 
 __global__ void cotangent_kernel(int64_t n, const float *__restrict__ a_g, const float4 *__restrict__ pos,
@@ -1796,11 +1904,17 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
     cudaStream_t st = ctx->stream;
     const int g = crk_grid(n, 256);
     crk_step_mark(ctx, 0);
-    to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm, io->m, m_k);
-    to_korder_kernel<<<g, 256, 0, st>>>(n, 3, lv->kperm, io->v3, v_k);
-    to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm, io->u, u_k);
-    to_korder_kernel<<<g, 256, 0, st>>>(n, 1, lv->kperm_g, io->m, m_g);
-    ctx->launches += 4;
+    {
+        // inputs into the two kernel orders: m, v, u (gas order) and m (gravity order)
+        PermCols in{};
+        auto col = [&](float *dst, const float *src, int sel) { in.c[in.ncol++] = PermCol{dst, src, sel}; };
+        col(m_k, io->m, 0);
+        for (int c = 0; c < 3; ++c) col(v_k + (size_t)c * n, io->v3 + (size_t)c * n, 0);
+        col(u_k, io->u, 0);
+        col(m_g, io->m, 1);
+        permute_cols_kernel<<<g, 256, 0, st>>>(n, lv->kperm, lv->kperm_g, in);
+        ++ctx->launches;
+    }
     CRK_LAUNCH_CHECK(ctx, "step inputs");
     unsigned long long *cnt = (unsigned long long *)io->pair_count;
     int rc;
@@ -1870,11 +1984,15 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
                 {io->dvdt3, dv_k, 3, lv->kinv},     {io->dudt, du_k, 1, lv->kinv},     {io->a3, a_g, 3, lv->kinv_g},
                 {io->gx3_grav, gx_g, 3, lv->kinv_g}, {io->gm_grav, gm_g, 1, lv->kinv_g}, {io->gx3_geom, gx2_k, 3, lv->kinv},
                 {io->gm_geom, gm2_k, 1, lv->kinv}};
+    PermCols oc{};
     for (const Out &o : outs)
-        if (o.dst) {
-            from_korder_kernel<<<g, 256, 0, st>>>(n, o.comp, o.perm, o.src, o.dst);
-            ++ctx->launches;
-        }
+        if (o.dst)
+            for (int c = 0; c < o.comp; ++c)
+                oc.c[oc.ncol++] = PermCol{o.dst + (size_t)c * n, o.src + (size_t)c * n, o.perm == lv->kinv_g ? 1 : 0};
+    if (oc.ncol > 0) {
+        permute_cols_kernel<<<g, 256, 0, st>>>(n, lv->kinv, lv->kinv_g, oc);
+        ++ctx->launches;
+    }
     CRK_LAUNCH_CHECK(ctx, "step outputs");
     crk_step_mark(ctx, 7);
     return CRK_OK;
