@@ -8,8 +8,9 @@
  * What the paper fixes, and what it leaves open.
  *   The paper (Sec. 5, opening paragraph) names the hot kernels and what each
  *   computes in one sentence: Geometry (gas-particle volumes), Corrections
- *   (reproducing-kernel coefficients), Acceleration (momentum derivative) and
- *   Energy (internal-energy derivative).  Sec. 3.1 adds the short-range
+ *   (reproducing-kernel coefficients), Extras (density and state gradients),
+ *   Acceleration (momentum derivative) and Energy (internal-energy
+ *   derivative).  Sec. 3.1 adds the short-range
  *   gravity solver (direct particle-particle force under a particle-mesh force
  *   split), the two species (dark matter: gravity only; gas: gravity + hydro)
  *   and the RCB tree; Sec. 5.3 adds that kernels run over pairs of leaves; the
@@ -480,6 +481,18 @@ int orc_corrections(int64_t n, const double *pos, const uint8_t *species, const 
 /*   f_ij = -1/2 V_i V_j (P_i + P_j + Q)(grad_i W^R_ij - grad_j W^R_ji)       */
 /*   m_i dv_i/dt = sum_j f_ij,   m_i du_i/dt = -1/2 sum_j (v_i - v_j).f_ij    */
 /* f_ij = -f_ji, so momentum and total energy are conserved pair by pair.    */
+/*                                                                          */
+/* Limited viscosity (dvg != NULL; the Extras velocity gradients feed it,   */
+/* paper silent on the form).  Both velocities are reconstructed linearly to */
+/* the pair midpoint before mu is formed, with a van Leer limiter on the     */
+/* gradients projected on the pair direction:                               */
+/*   s_i = (dv_i) x,  s_j = (dv_j) x   ((dv)[a][b] = d v^a / d x^b)          */
+/*   r = (x.s_i)/(x.s_j)  (0 if x.s_j = 0),  phi = 4r/(1+r)^2 if r > 0 else 0 */
+/*   v*_ij = v_ij - phi/2 (s_i + s_j)  replaces v_ij in mu                   */
+/* phi and v*_ij.x are unchanged under i <-> j, so Q_ij = Q_ji and the       */
+/* conservation is kept; a linear velocity field with its exact gradient     */
+/* gives v*_ij = 0 (no viscosity in a smooth shear or compression).  The     */
+/* work term keeps the true v_ij.                                            */
 /* ------------------------------------------------------------------------ */
 static void grad_WR(const double x[3], double W, double dWr, double A, const double *B, const double *gA,
                     const double *gB, double out[3]) {
@@ -492,8 +505,8 @@ static void grad_WR(const double x[3], double W, double dWr, double A, const dou
 
 int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m, const double *v,
               const double *u, const double *V, const double *rho, const double *A, const double *B, const double *gA,
-              const double *gB, double L, double gamma, double alpha, double beta, double eta2, const int64_t *sub,
-              int64_t nsub, int brute, double *dvdt, double *dudt, int64_t *npairs) {
+              const double *gB, const double *dvg, double L, double gamma, double alpha, double beta, double eta2,
+              const int64_t *sub, int64_t nsub, int brute, double *dvdt, double *dudt, int64_t *npairs) {
     double hmax = max_h_gas(n, species, h);
     if (n < 0 || L <= 0 || !(2.0 * hmax < 0.5 * L)) return ORC_EBOX;
     uint8_t *gmask = gas_mask(n, species);
@@ -527,7 +540,20 @@ int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double
             double Pj = (gamma - 1.0) * rho[j] * u[j];
             double cj = sqrt(gamma * (gamma - 1.0) * u[j]);
             double vij[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
-            double vx = vij[0] * x[0] + vij[1] * x[1] + vij[2] * x[2];
+            double vs[3] = {vij[0], vij[1], vij[2]}; /* velocity difference seen by the viscosity */
+            if (dvg) {
+                double si[3], sj[3];
+                for (int a = 0; a < 3; ++a) {
+                    si[a] = dvg[9 * i + 3 * a] * x[0] + dvg[9 * i + 3 * a + 1] * x[1] + dvg[9 * i + 3 * a + 2] * x[2];
+                    sj[a] = dvg[9 * j + 3 * a] * x[0] + dvg[9 * j + 3 * a + 1] * x[1] + dvg[9 * j + 3 * a + 2] * x[2];
+                }
+                double ai = x[0] * si[0] + x[1] * si[1] + x[2] * si[2];
+                double aj = x[0] * sj[0] + x[1] * sj[1] + x[2] * sj[2];
+                double rr = aj != 0.0 ? ai / aj : 0.0;
+                double phi = rr > 0.0 ? 4.0 * rr / ((1.0 + rr) * (1.0 + rr)) : 0.0;
+                for (int a = 0; a < 3; ++a) vs[a] = vij[a] - 0.5 * phi * (si[a] + sj[a]);
+            }
+            double vx = vs[0] * x[0] + vs[1] * x[1] + vs[2] * x[2];
             double mu = vx < 0.0 ? hij * vx / (r2 + eta2 * hij * hij) : 0.0;
             double Q = 0.5 * (rho[i] + rho[j]) * (-alpha * 0.5 * (ci + cj) * mu + beta * mu * mu);
             double pre = -0.5 * V[i] * V[j] * (Pi + Pj + Q);
@@ -538,6 +564,61 @@ int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double
         }
         for (int c = 0; c < 3; ++c) dvdt[3 * i + c] = F[c] / m[i];
         dudt[i] = E / m[i];
+    });
+    cells_free(&cl);
+    free(gmask);
+    if (npairs) *npairs = pairs;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Extras (Sec. 5: "evaluates the density and state gradients").  Paper      */
+/* silent; CRKSPH reading, over gas j including j = i, with the corrected    */
+/* kernel W^R_ij = A_i (1 + B_i.x_ij) W_ij and its evaluation-point gradient */
+/* grad_i W^R_ij (as in orc_hydro):                                          */
+/*   rhoR_i = sum_j m_j W^R_ij                     (corrected-kernel density) */
+/*   dv_i[3a + b] = sum_j V_j (v_j^a - v_i^a) (grad_i W^R_ij)^b  = dv^a/dx^b */
+/* The first reproduces a density rho0 exactly when m_j = rho0 V_j; the      */
+/* second is exact for a linear velocity field.  Dark matter gets zeros.    */
+/* ------------------------------------------------------------------------ */
+int orc_extras(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m, const double *v,
+               const double *V, const double *A, const double *B, const double *gA, const double *gB, double L,
+               const int64_t *sub, int64_t nsub, int brute, double *rhoR, double *dvg, int64_t *npairs) {
+    double hmax = max_h_gas(n, species, h);
+    if (n < 0 || L <= 0 || !(2.0 * hmax < 0.5 * L)) return ORC_EBOX;
+    uint8_t *gmask = gas_mask(n, species);
+    CellList cl;
+    if (cells_build(&cl, n, pos, gmask, L, 2.0 * hmax > 0 ? 2.0 * hmax : L, brute)) { free(gmask); return ORC_ENOMEM; }
+    int64_t pairs = 0;
+    FOR_EACH_I(sub, nsub, n, {
+        if (species[i] != 0) {
+            rhoR[i] = 0.0;
+            for (int c = 0; c < 9; ++c) dvg[9 * i + c] = 0.0;
+            continue;
+        }
+        int64_t nc = cells_candidates(&cl, &pos[3 * i], buf);
+        double rho = 0.0, G[9] = {0.0};
+        for (int64_t t = 0; t < nc; ++t) {
+            int64_t j = buf[t];
+            double x[3];
+            min_image(&pos[3 * i], &pos[3 * j], L, x); /* x_ij */
+            double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            double hij = 0.5 * (h[i] + h[j]);
+            if (!(r2 < 4.0 * hij * hij)) continue;
+            if (j != i) ++pairs;
+            double W, dWr;
+            wendland(sqrt(r2), hij, &W, &dWr);
+            double Bx = B[3 * i] * x[0] + B[3 * i + 1] * x[1] + B[3 * i + 2] * x[2];
+            rho += m[j] * A[i] * (1.0 + Bx) * W;
+            double g[3];
+            grad_WR(x, W, dWr, A[i], &B[3 * i], &gA[3 * i], &gB[9 * i], g);
+            for (int a = 0; a < 3; ++a) {
+                double dva = v[3 * j + a] - v[3 * i + a];
+                for (int b = 0; b < 3; ++b) G[3 * a + b] += V[j] * dva * g[b];
+            }
+        }
+        rhoR[i] = rho;
+        for (int c = 0; c < 9; ++c) dvg[9 * i + c] = G[c];
     });
     cells_free(&cl);
     free(gmask);

@@ -60,9 +60,11 @@ def lib():
                                        ctypes.c_int, _d, _d, _i64]
             L.orc_corrections.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
                                           ctypes.c_int, _d, _d, _d, _d, _i64, _i64]
-            L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+            L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
+            L.orc_extras.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_double,
+                                     _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
             L.orc_geometry_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, ctypes.c_double, _i64,
                                                ctypes.c_int64, ctypes.c_int, _d, _d]
             L.orc_leaves_mesh.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_double, ctypes.c_int, _i32, _i32]
@@ -71,7 +73,8 @@ def lib():
                                          ctypes.c_double, _i32, ctypes.c_int64, _i32, _i32, ctypes.c_int64, _i64]
             L.orc_mark_neighbours.argtypes = [ctypes.c_int64, _d, _u8, _d, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int, _u8, _u8]
-            for name in ("orc_mark_neighbours", "orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections", "orc_hydro",
+            for name in ("orc_mark_neighbours", "orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections",
+                         "orc_hydro", "orc_extras",
                          "orc_geometry_adjoint", "orc_leaves_mesh", "orc_leaves_rcb", "orc_leaf_pairs"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -211,18 +214,39 @@ def corrections(I: Inputs, V, sub=None, brute=False, with_pairs=False):
     return A, B, gA, gB, int(ns_.value)
 
 
-def hydro(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, sub=None, brute=False):
-    """dv/dt f64[n,3], du/dt f64[n] (gas only) and the hydro pair count."""
+def hydro(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, sub=None, brute=False, dvg=None):
+    """dv/dt f64[n,3], du/dt f64[n] (gas only) and the hydro pair count.
+
+    dvg (f64[n,9], dvg[i, 3a+b] = dv^a/dx^b, e.g. from extras) switches on the
+    limited viscosity: velocities reconstructed to the pair midpoint."""
     args = [_f64(a) for a in (V, rho, A, B, gA, gB)]
+    g = _f64(dvg).reshape(I.n, 9) if dvg is not None else None
     dv = np.zeros((I.n, 3))
     du = np.zeros(I.n)
     npairs = ctypes.c_int64(0)
     s, ns = _sub(sub)
     _check(lib().orc_hydro(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d), _p(I.v, _d),
-                           _p(I.u, _d), *[_p(a, _d) for a in args], I.L, float(gamma), float(alpha), float(beta),
-                           float(eta2), _p(s, _i64), ns, int(brute), _p(dv, _d), _p(du, _d), ctypes.byref(npairs)),
+                           _p(I.u, _d), *[_p(a, _d) for a in args], _p(g, _d), I.L, float(gamma), float(alpha),
+                           float(beta), float(eta2), _p(s, _i64), ns, int(brute), _p(dv, _d), _p(du, _d),
+                           ctypes.byref(npairs)),
            "hydro")
     return dv, du, int(npairs.value)
+
+
+def extras(I: Inputs, V, A, B, gA, gB, sub=None, brute=False, with_pairs=False):
+    """Corrected-kernel density rhoR f64[n] and velocity gradient f64[n,9] (dv[i, 3a+b] = dv^a/dx^b), gas only."""
+    args = [_f64(a) for a in (V, A, B, gA, gB)]
+    rhoR = np.zeros(I.n)
+    dvg = np.zeros((I.n, 9))
+    npairs = ctypes.c_int64(0)
+    s, ns = _sub(sub)
+    _check(lib().orc_extras(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d), _p(I.v, _d),
+                            *[_p(a, _d) for a in args], I.L, _p(s, _i64), ns, int(brute), _p(rhoR, _d), _p(dvg, _d),
+                            ctypes.byref(npairs)),
+           "extras")
+    if with_pairs:
+        return rhoR, dvg, int(npairs.value)
+    return rhoR, dvg
 
 
 def geometry_adjoint(I: Inputs, rhobar, Vbar=None, sub=None, brute=False):
