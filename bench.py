@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trace-leaves", action="store_true", help="after timing, print leaf-build phase times")
-    ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8)")
+    ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8, 4 ring16)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--no-extras", action="store_true", help="skip the Extras-chain measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants")
     ap.add_argument("--batched-boxes", type=int, default=96)
     return ap.parse_args()
@@ -361,6 +362,11 @@ def main():
             "roofline": roofline, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 32,
                     "ms_per_step": e2e_ms}}
+    if not args.no_extras:
+        try:
+            line["extras_chain"] = extras_chain(api, ctx, db, stream, peak_tflops)
+        except Exception as e:  # reported, never silent
+            line["extras_chain"] = {"error": repr(e)}
     if not args.no_batched:
         try:
             line["batched_vs_plain"] = batched_vs_plain(args, local, dist)
@@ -375,6 +381,51 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+EXTRAS_FLOPS_PER_PAIR = {"extras": 103, "hydro_limited": 215, "hydro": 160}
+
+
+def extras_chain(api, ctx, db, stream, peak_tflops, reps=3):
+    """The Extras row after the step: crk_extras and crk_hydro_limited on the same leaves.
+
+    Single calls (caller-order arrays), each timed with CUDA events on the
+    context stream, best of `reps` after one warm-up, beside the plain crk_hydro
+    on the same inputs.  Outside the headline step and its timed region.
+    """
+    import torch
+
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, rho, _ = api.geometry(ctx, lv, db.m)
+    A, B, gA, gB, _ = api.corrections(ctx, lv, V)
+    rr, G, c = api.extras(ctx, lv, db.m, db.v3, V, A, B, gA, gB, count=True)
+    torch.cuda.synchronize()
+    pairs = int(c.cpu().numpy()[0])
+    calls = {
+        "extras": lambda: api.extras(ctx, lv, db.m, db.v3, V, A, B, gA, gB),
+        "hydro_limited": lambda: api.hydro_limited(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB, G),
+        "hydro": lambda: api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB),
+    }
+    ms = {}
+    for k, f in calls.items():
+        f()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f()
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        ms[k] = best
+    tf = {k: EXTRAS_FLOPS_PER_PAIR[k] * pairs / (ms[k] * 1e-3) / 1e12 for k in ms}
+    return {"pairs_per_launch": pairs, "ms": {k: round(v, 4) for k, v in ms.items()},
+            "pairs_per_s": {k: pairs / (v * 1e-3) for k, v in ms.items()},
+            "tflops": tf, "frac_of_fp32_peak": {k: v / peak_tflops for k, v in tf.items()},
+            "flops_per_pair": EXTRAS_FLOPS_PER_PAIR,
+            "note": "single calls in the caller's order (record gathers through the leaf permutation), "
+                    "best of %d after a warm-up" % reps}
 
 
 def batched_vs_plain(args, local, dist):

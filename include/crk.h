@@ -114,12 +114,21 @@ int crk_set_trace(crk_ctx *ctx, int on);
 #define CRK_K_GRAVITY 3
 #define CRK_K_GRAVITY_ADJOINT 4
 #define CRK_K_GEOMETRY_ADJOINT 5
+#define CRK_K_EXTRAS 6
 #define CRK_VARIANT_LISTS 0
 #define CRK_VARIANT_TILES 1
 #define CRK_VARIANT_TILES16 2 /* tiles with two 16-particle i-groups per warp */
 #define CRK_VARIANT_TILES8 3  /* tiles with four 8-particle i-groups per warp */
 #define CRK_VARIANT_RING16 4  /* two 16-particle i-groups per warp, balanced ring-buffer sweeps
                                  (every kernel but hydro, which falls back to TILES) */
+/* the paper's half-warp leaf-pair scheme (Sec. 5.3), gravity kernels only: lanes 0-15 hold 16
+ * particles of leaf A, lanes 16-31 16 of leaf B, and the pair is evaluated in both directions
+ * in one step; partial sums are added atomically.  The partner's particle arrives by register
+ * shuffle, through shared memory, or by a second load.  The gas kernels run tiles instead. */
+#define CRK_VARIANT_HALFWARP_SHFL 5
+#define CRK_VARIANT_HALFWARP_SMEM 6
+#define CRK_VARIANT_HALFWARP_LOAD 7
+#define CRK_N_VARIANTS 8
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
 /* Launch mode of the pair kernels: 0 (default) one block per i-leaf; 1
  * persistent: a grid of 4 blocks per SM whose blocks take i-leaves from an
@@ -204,6 +213,32 @@ int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, co
               const float *u, const float *V, const float *rho, const float *A, const float *B, const float *gradA,
               const float *gradB, float *dvdt3, float *dudt, double *conservation, int64_t *pair_count);
 
+/* Extras (Sec. 5: "evaluates the density and state gradients").  The paper
+ * prints no formula; CRKSPH reading, over gas j including j = i, with the
+ * corrected kernel W^R_ij = A_i (1 + B_i.x_ij) W_ij and its evaluation-point
+ * gradient (as in crk_hydro):
+ *   rho_r_i = sum_j m_j W^R_ij                        (corrected-kernel density)
+ *   dvdx_i[3a+b] = sum_j V_j (v_j^a - v_i^a) (grad_i W^R_ij)^b   (d v^a / d x^b)
+ * Inputs m, v3, V and the corrections A, B, gradA, gradB (caller order);
+ * outputs rho_r[n], dvdx[9n] with dvdx[(3a+b)n + i]; dark matter gets 0.
+ * pair_count as for crk_geometry. */
+int crk_extras(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *v3, const float *V, const float *A,
+               const float *B, const float *gradA, const float *gradB, float *rho_r, float *dvdx,
+               int64_t *pair_count);
+
+/* crk_hydro with the limited viscosity (the paper prints no formula; CRKSPH
+ * reading fed by crk_extras): the viscosity sees both velocities
+ * reconstructed linearly to the pair midpoint, v*_ij = v_ij - phi/2 (s_i + s_j)
+ * with s = dvdx x_ij, and the van Leer limiter phi = 4r/(1+r)^2 for
+ * r = (x.s_i)/(x.s_j) > 0, else 0.  Q_ij stays symmetric, so momentum and
+ * energy are conserved as before; the work term keeps the true v_ij.  dvdx is
+ * the crk_extras output layout; rho is the density the equation of state uses
+ * (crk_extras' rho_r in the Extras chain). */
+int crk_hydro_limited(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m,
+                      const float *v3, const float *u, const float *V, const float *rho, const float *A,
+                      const float *B, const float *gradA, const float *gradB, const float *dvdx, float *dvdt3,
+                      float *dudt, double *conservation, int64_t *pair_count);
+
 /* Short-range gravity (Sec. 3.1), G = 1, all species:
  *   a_i = sum_{j != i, r < r_c} m_j (x_j - x_i) g(r^2).
  * Input m[n]; output a3[3n]. */
@@ -235,7 +270,9 @@ int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, con
  * sum |a|^2 + sum_gas rho (abar3 = NULL: 2a; rhobar = NULL: 1 on gas); Vbar
  * may be NULL.  pair_count (device int64[3], may be NULL) receives the
  * geometry, hydro and gravity pair counts; n_singular and conservation as for
- * the single calls. */
+ * the single calls.  With extras != 0 the step runs crk_extras after the
+ * corrections and crk_hydro_limited in place of crk_hydro, with rho_r as the
+ * equation-of-state density (rho then still receives the geometry density). */
 typedef struct {
     const float *m, *v3, *u;                /* inputs */
     float *V, *rho, *A, *B, *gradA, *gradB; /* geometry, corrections */
@@ -248,6 +285,8 @@ typedef struct {
     float *gx3_geom, *gm_geom;              /* geometry adjoint */
     int32_t *n_singular;                    /* may be NULL */
     int64_t *pair_count;                    /* int64[3], may be NULL */
+    int extras;                             /* nonzero: Extras chain (see below) */
+    float *rho_r, *dvdx;                    /* Extras outputs, may be NULL */
 } crk_step_io;
 
 int crk_step(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
@@ -277,7 +316,7 @@ void crk_graph_destroy(crk_graph *g);
 
 /* Autotuner: times every variant of every kernel on these leaves (best of
  * reps after a warm-up, CUDA events on the context stream), keeps the fastest
- * in the context, and reports ms_out[6 * 5] (kernel-major; -1 = not available)
+ * in the context, and reports ms_out[6 * CRK_N_VARIANTS] (kernel-major; -1 = not available)
  * and best_out[6] (host arrays, may be NULL).  Runs one crk_step first; every
  * output array of io must be given (they are overwritten while timing). */
 int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,

@@ -188,6 +188,34 @@ def hydro(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A, B, gA,
     return dv, du, cons, c
 
 
+def extras(ctx: Context, lv: Leaves, m, v3, V, A, B, gA, gB, count=False):
+    """Corrected-kernel density rho_r [n] and velocity gradient dvdx [9, n] (dvdx[3a+b] = dv^a/dx^b)."""
+    n = lv.n
+    rho_r, dvdx = ctx.empty(n), ctx.empty(9, n)
+    c = _count(ctx, count)
+    ctx.check(N.lib().crk_extras(ctx.handle, lv.handle, _f32(m, "m", n), _f32(v3, "v3", 3 * n), _f32(V, "V", n),
+                                 _f32(A, "A", n), _f32(B, "B", 3 * n), _f32(gA, "gradA", 3 * n),
+                                 _f32(gB, "gradB", 9 * n), rho_r.data_ptr(), dvdx.data_ptr(),
+                                 c.data_ptr() if c is not None else None))
+    return rho_r, dvdx, c
+
+
+def hydro_limited(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A, B, gA, gB, dvdx, count=False):
+    """crk_hydro with the limited viscosity fed by the Extras velocity gradient."""
+    n = lv.n
+    dv, du = ctx.empty(3, n), ctx.empty(n)
+    cons = torch.zeros(4, dtype=torch.float64, device=ctx.device)
+    c = _count(ctx, count)
+    hpc = hp.c()
+    ctx.check(N.lib().crk_hydro_limited(ctx.handle, lv.handle, ctypes.byref(hpc), _f32(m, "m", n),
+                                        _f32(v3, "v3", 3 * n), _f32(u, "u", n), _f32(V, "V", n),
+                                        _f32(rho, "rho", n), _f32(A, "A", n), _f32(B, "B", 3 * n),
+                                        _f32(gA, "gradA", 3 * n), _f32(gB, "gradB", 9 * n),
+                                        _f32(dvdx, "dvdx", 9 * n), dv.data_ptr(), du.data_ptr(), cons.data_ptr(),
+                                        c.data_ptr() if c is not None else None))
+    return dv, du, cons, c
+
+
 def grav_short(ctx: Context, lv: Leaves, gp: GravParams, m, count=False):
     n = lv.n
     a = ctx.empty(3, n)
@@ -292,11 +320,13 @@ class StepIO:
     intermediates (V, rho, A, B, dA, dB) then stay inside the library.
     """
 
-    def __init__(self, ctx: Context, db, outputs: bool = True):
+    def __init__(self, ctx: Context, db, outputs: bool = True, extras: bool = False):
         n = db.n
         e = ctx.empty
         self.db = db
         self.full = outputs
+        self.extras = extras
+        self.rho_r, self.dvdx = (e(n), e(9, n)) if (extras and outputs) else (None, None)
         if outputs:
             self.V, self.rho, self.A, self.B, self.gA, self.gB = e(n), e(n), e(n), e(3, n), e(3, n), e(9, n)
         else:
@@ -313,7 +343,8 @@ class StepIO:
         return N.crk_step_io(P(d.m), P(d.v3), P(d.u), P(self.V), P(self.rho), P(self.A), P(self.B), P(self.gA),
                              P(self.gB), P(self.dv), P(self.du), P(self.cons), P(self.acc), None, P(self.gx_grav),
                              P(self.gm_grav), None, None, P(self.gx_geom), P(self.gm_geom), P(self.n_singular),
-                             P(self.pair_count) if count else None)
+                             P(self.pair_count) if count else None, 1 if self.extras else 0, P(self.rho_r),
+                             P(self.dvdx))
 
 
 def step(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, count: bool = False) -> None:
@@ -355,7 +386,7 @@ def tune(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, reps: int = 3) -
     best = (ctypes.c_int * 6)()
     ctx.check(N.lib().crk_tune(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp), ctypes.byref(c),
                                int(reps), ms, best))
-    names = sorted(N.KERNELS, key=N.KERNELS.get)
+    names = sorted(N.KERNELS, key=N.KERNELS.get)[:6]  # the six kernels of crk_step
     return {k: (int(best[i]), [float(ms[N.N_VARIANTS * i + v]) for v in range(N.N_VARIANTS)])
             for i, k in enumerate(names)}
 

@@ -127,15 +127,15 @@ const char *crk_version(void) { return "libcrk 1 sm_103a"; }
 
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant) {
     if (!ctx) return CRK_EINVAL;
-    if (kernel < 0 || kernel > CRK_K_GEOMETRY_ADJOINT) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
-    if (variant < CRK_VARIANT_LISTS || variant > CRK_VARIANT_RING16)
+    if (kernel < 0 || kernel > CRK_K_EXTRAS) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
+    if (variant < CRK_VARIANT_LISTS || variant >= CRK_N_VARIANTS)
         return crk_fail(ctx, CRK_EINVAL, "variant %d not available for kernel %d", variant, kernel);
     ctx->variant[kernel] = variant;
     return CRK_OK;
 }
 
 int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant) {
-    if (!ctx || !variant || kernel < 0 || kernel > CRK_K_GEOMETRY_ADJOINT) return CRK_EINVAL;
+    if (!ctx || !variant || kernel < 0 || kernel > CRK_K_EXTRAS) return CRK_EINVAL;
     *variant = ctx->variant[kernel];
     return CRK_OK;
 }

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <type_traits>
+
 #include "crk_internal.cuh"
 
 namespace {
@@ -59,6 +61,9 @@ __device__ __forceinline__ int64_t next_group(const LeafView &lv, int64_t cur, i
     if (lane == 0) g = atomicAdd(lv.queue, 1);
     return __shfl_sync(CRK_FULL_MASK, g, 0);
 }
+
+// index of kernel-order position q in the stage's per-particle arrays
+__device__ __forceinline__ int32_t stage_index(const LeafView &lv, int q) { return lv.korder ? q : lv.kperm[q]; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -119,7 +124,7 @@ struct GravStage {
     __device__ static float box_cut(const P &p, float, const Rec &) { return sqrtf(p.rc2); }
     __device__ static float leaf_cut(const P &p, float, float) { return sqrtf(p.rc2); }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.ax = s.ay = s.az = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) { s.ax = s.ay = s.az = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
         float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
@@ -187,6 +192,13 @@ struct GravStage {
         s.az = __ffma2_rn(f, dz, s.az);
         if (kCount) s.cnt += (int)in0 + (int)in1;
     }
+    // partial sums of one i from one leaf-pair tile (half-warp arms): added atomically
+    __device__ static void flush(const P &p, const I &s, int32_t o) {
+        atomicAdd(&p.a3[o], s.ax);
+        atomicAdd(&p.a3[p.n + o], s.ay);
+        atomicAdd(&p.a3[2 * p.n + o], s.az);
+    }
+    static void zero_outputs(const P &p, cudaStream_t st) { cudaMemsetAsync(p.a3, 0, sizeof(float) * 3 * p.n, st); }
     __device__ static void finish2(const P &p, I2 &s, int32_t orig) {
         p.a3[orig] = s.ax.x + s.ax.y;
         p.a3[p.n + orig] = s.ay.x + s.ay.y;
@@ -222,7 +234,7 @@ struct GravAdjStage {
     __device__ static float box_cut(const P &p, float, const Rec &) { return sqrtf(p.rc2); }
     __device__ static float leaf_cut(const P &p, float, float) { return sqrtf(p.rc2); }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.gx = s.gy = s.gz = s.gm = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) { s.gx = s.gy = s.gz = s.gm = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
         float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;  // d_ij = x_j - x_i
@@ -321,6 +333,16 @@ struct GravAdjStage {
         s.sg = __ffma2_rn(g, __ffma2_rn(rj.bx, dx, __ffma2_rn(rj.by, dy, __fmul2_rn(rj.bz, dz))), s.sg);
         if (kCount) s.cnt += (int)in0 + (int)in1;
     }
+    __device__ static void flush(const P &p, const I &s, int32_t o) {
+        atomicAdd(&p.gx3[o], s.gx);
+        atomicAdd(&p.gx3[p.n + o], s.gy);
+        atomicAdd(&p.gx3[2 * p.n + o], s.gz);
+        atomicAdd(&p.gm[o], s.gm);
+    }
+    static void zero_outputs(const P &p, cudaStream_t st) {
+        cudaMemsetAsync(p.gx3, 0, sizeof(float) * 3 * p.n, st);
+        cudaMemsetAsync(p.gm, 0, sizeof(float) * p.n, st);
+    }
     __device__ static void finish2(const P &p, I2 &s, int32_t o) {
         p.gx3[o] = s.gx.x + s.gx.y;
         p.gx3[p.n + o] = s.gy.x + s.gy.y;
@@ -353,7 +375,7 @@ struct GeomStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.s = s.c = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) { s.s = s.c = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
         float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
@@ -406,7 +428,7 @@ struct GeomAdjStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.gx = s.gy = s.gz = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) { s.gx = s.gy = s.gz = 0.f; s.cnt = 0; }
     template <bool kCount>
     __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
         float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;  // x_kj
@@ -466,7 +488,7 @@ struct CorrStage {
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) {
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) {
         s.m0 = s.c0 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) s.m1[a] = s.c1[a] = s.dm0[a] = 0.f;
@@ -585,23 +607,35 @@ struct HydroP {
     float gamma, alpha, beta, eta2;
     int64_t n;
     unsigned long long *count;
+    const float *dvg;  // limited viscosity: velocity gradient [9][n], dv^a/dx^b at 3a+b
 };
 
-struct HydroStage {
+struct HydroRec {
+    float x, y, z, h;
+    float vx, vy, vz, P;
+    float c, rho, V, A;
+    float B[3], gA0;
+    float gA1, gA2, gB0, gB1;
+    float gB[7];  // gB[2..8]
+    float pad;
+};
+struct HydroRecLim : HydroRec {
+    float G[9];  // velocity gradient, dv^a/dx^b at 3a+b
+    float pad2[3];
+};
+
+// kLim: the viscosity sees both velocities reconstructed linearly to the pair
+// midpoint, s = (dv) x, with the van Leer limiter
+// phi = 4 r/(1+r)^2, r = (x.s_i)/(x.s_j), written 4 a_i a_j/(a_i + a_j)^2 for
+// a_i a_j > 0 (else 0): the same value without a division by a_j alone.
+template <bool kLim>
+struct HydroStageT {
     static constexpr bool kPair = false;
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = true;
     static constexpr bool kTag = false;
     using P = HydroP;
-    struct __align__(16) Rec {
-        float x, y, z, h;
-        float vx, vy, vz, P;
-        float c, rho, V, A;
-        float B[3], gA0;
-        float gA1, gA2, gB0, gB1;
-        float gB[7];  // gB[2..8]
-        float pad;
-    };
+    struct __align__(16) Rec : std::conditional_t<kLim, HydroRecLim, HydroRec> {};
     struct I {
         float fx, fy, fz, e;
         int cnt;
@@ -622,12 +656,16 @@ struct HydroStage {
         r.gB0 = p.gB[o]; r.gB1 = p.gB[n + o];
         for (int k = 0; k < 7; ++k) r.gB[k] = p.gB[(2 + k) * n + o];
         r.pad = 0.f;
+        if constexpr (kLim) {
+            for (int k = 0; k < 9; ++k) r.G[k] = p.dvg[k * n + o];
+            r.pad2[0] = r.pad2[1] = r.pad2[2] = 0.f;
+        }
         return r;
     }
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
-    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int) { s.fx = s.fy = s.fz = s.e = 0.f; s.cnt = 0; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) { s.fx = s.fy = s.fz = s.e = 0.f; s.cnt = 0; }
     // grad W^R of record r at separation x (x = x_r - x_other): gA (1 + B.x) W + A (gB.x + B) W + A (1 + B.x) dWr x
     __device__ static void grad_wr(const Rec &r, const float x[3], float W, float dWr, float g[3]) {
         float Bx = fmaf(r.B[0], x[0], fmaf(r.B[1], x[1], r.B[2] * x[2]));
@@ -656,7 +694,26 @@ struct HydroStage {
         float xm[3] = {-x[0], -x[1], -x[2]};
         grad_wr(rj, xm, W, dWr, gj);
         float vij[3] = {ri.vx - rj.vx, ri.vy - rj.vy, ri.vz - rj.vz};
-        float vx = fmaf(vij[0], x[0], fmaf(vij[1], x[1], vij[2] * x[2]));
+        float vx;
+        if constexpr (kLim) {
+            float si[3], sj[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                si[a] = fmaf(ri.G[3 * a], x[0], fmaf(ri.G[3 * a + 1], x[1], ri.G[3 * a + 2] * x[2]));
+                sj[a] = fmaf(rj.G[3 * a], x[0], fmaf(rj.G[3 * a + 1], x[1], rj.G[3 * a + 2] * x[2]));
+            }
+            const float ai = fmaf(x[0], si[0], fmaf(x[1], si[1], x[2] * si[2]));
+            const float aj = fmaf(x[0], sj[0], fmaf(x[1], sj[1], x[2] * sj[2]));
+            const float aa = ai * aj, as = ai + aj;
+            const float phi = aa > 0.0f ? __fdividef(4.0f * aa, as * as) : 0.0f;
+            const float hp = 0.5f * phi;
+            float vs[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) vs[a] = fmaf(-hp, si[a] + sj[a], vij[a]);
+            vx = fmaf(vs[0], x[0], fmaf(vs[1], x[1], vs[2] * x[2]));
+        } else {
+            vx = fmaf(vij[0], x[0], fmaf(vij[1], x[1], vij[2] * x[2]));
+        }
         float mu = vx < 0.0f ? __fdividef(hij * vx, fmaf(p.eta2 * hij, hij, r2)) : 0.0f;
         float Q = 0.5f * (ri.rho + rj.rho) * mu * fmaf(-p.alpha * 0.5f, ri.c + rj.c, p.beta * mu);
         float pre = in ? -0.5f * ri.V * rj.V * (ri.P + rj.P + Q) : 0.0f;
@@ -693,6 +750,99 @@ struct HydroStage {
     }
 };
 
+
+using HydroStage = HydroStageT<false>;
+using HydroLimStage = HydroStageT<true>;
+
+// Extras (Sec. 5: the density and state gradients), over gas j including j = i:
+//   rhoR_i = sum_j m_j W^R_ij,   dv_i[3a+b] = sum_j V_j (v_j^a - v_i^a) (grad_i W^R_ij)^b
+// with W^R_ij = A_i (1 + B_i.x_ij) W_ij and grad_i W^R_ij as in the hydro stage.
+struct ExtrasP {
+    const float *m, *v3, *V, *A, *B, *gA, *gB;
+    float *rhoR, *dvg;
+    int64_t n;
+    unsigned long long *count;
+};
+
+struct ExtrasStage {
+    static constexpr bool kPair = false;
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    static constexpr bool kTag = false;
+    using P = ExtrasP;
+    struct __align__(16) Rec {
+        float x, y, z, h;
+        float V, m, vx, vy;
+        float vz, pad0, pad1, pad2;
+    };
+    struct I {
+        float A, B[3], gA[3], gB[9];  // the i particle's corrections (gB[3g+a] = d_g B^a)
+        float rho, crho;              // compensated sum
+        float G[9];
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) {
+        const int64_t n = p.n;
+        return {ps.x, ps.y, ps.z, ps.w, p.V[o], p.m[o], p.v3[o], p.v3[n + o], p.v3[2 * n + o], 0.f, 0.f, 0.f};
+    }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &p, I &s, const Rec &, int64_t, int, int, int32_t o) {
+        const int64_t n = p.n;
+        s.A = p.A[o];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s.B[a] = p.B[a * n + o];
+            s.gA[a] = p.gA[a * n + o];
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            s.gB[a] = p.gB[a * n + o];
+            s.G[a] = 0.f;
+        }
+        s.rho = s.crho = 0.f;
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float x[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};  // x_ij
+        float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float W, dWr;
+        wendland(r2, 0.5f * hs, W, dWr);
+        W = in ? W : 0.0f;
+        dWr = in ? dWr : 0.0f;
+        const float Bx = fmaf(s.B[0], x[0], fmaf(s.B[1], x[1], s.B[2] * x[2]));
+        const float k1 = (1.0f + Bx) * W;
+        kahan_add(s.rho, s.crho, rj.m * (s.A * k1));
+        // grad_i W^R_ij = gA (1 + B.x) W + A (gB.x + B) W + A (1 + B.x) dWr x
+        const float AW = s.A * W, k3 = s.A * (1.0f + Bx) * dWr;
+        float g[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float gBx = fmaf(s.gB[3 * q], x[0], fmaf(s.gB[3 * q + 1], x[1], s.gB[3 * q + 2] * x[2]));
+            g[q] = fmaf(s.gA[q], k1, fmaf(AW, gBx + s.B[q], k3 * x[q]));
+        }
+        const float dv[3] = {rj.V * (rj.vx - ri.vx), rj.V * (rj.vy - ri.vy), rj.V * (rj.vz - ri.vz)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) s.G[3 * a + b] = fmaf(dv[a], g[b], s.G[3 * a + b]);
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
+        p.rhoR[o] = s.rho;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) p.dvg[k * p.n + o] = s.G[k];
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        p.rhoR[o] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) p.dvg[k * p.n + o] = 0.f;
+    }
+};
 
 // Builds the exact neighbour lists of every i-group (count pass, then fill
 // pass): gas pairs (r < h_i + h_j) or gravity pairs (r < r_cut).  A group's
@@ -742,7 +892,7 @@ struct ListStage {
     __device__ static void tag(Rec &r, int img_local, int j_local) {
         r.code = ((uint32_t)img_local << 10) | (uint32_t)j_local;
     }
-    __device__ static void init(const P &p, I &s, const Rec &, int64_t a, int q, int lane) {
+    __device__ static void init(const P &p, I &s, const Rec &, int64_t a, int q, int lane, int32_t) {
         s.c = 0;
         s.u = 0;
         s.cnt = 0;
@@ -816,7 +966,7 @@ __device__ __forceinline__ void tile_group(const LeafView &lv, const typename S:
     const bool act = i < hi;
     const Rec ri = rec[act ? i : g0];
     typename S::I st;
-    S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
+    S::init(p, st, ri, a, (g0 - lo) >> 5, lane, stage_index(lv, act ? i : g0));
     // i-group box and largest h (inactive lanes repeat lane 0's particle)
     float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
     float hm = lv.pos[act ? i : g0].w;
@@ -977,6 +1127,126 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
     }
 }
 
+// The paper's "half-warp" leaf-pair scheme (Sec. 5.3), as autotuner arms for
+// the gravity stages.  Lanes 0-15 hold 16 particles of leaf A, lanes 16-31 16
+// particles of leaf B (shifted into A's frame); in step s lane l and lane
+// 16 + (l ^ s) exchange their particles and each evaluates the interaction on
+// its own particle, so every A-B pair is evaluated once in each direction in
+// the same step.  Each unordered leaf-pair image is visited once (entries with
+// b > a, or b = a with a positive shift, and the leaf with itself); the
+// partial sums of each tile are added to the outputs atomically, so the
+// result is exact up to the order of the FP32 additions.  kEx selects how the
+// partner's particle reaches a lane: 0 register shuffle, 1 shared memory,
+// 2 a second load of the partner's record.
+template <class Rec>
+__device__ __forceinline__ Rec shfl_rec(const Rec &r, int src) {
+    Rec o;
+    const float *a = reinterpret_cast<const float *>(&r);
+    float *b = reinterpret_cast<float *>(&o);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(Rec) / sizeof(float)); ++k) b[k] = __shfl_sync(CRK_FULL_MASK, a[k], src);
+    return o;
+}
+
+__device__ __forceinline__ bool positive_shift(float sx, float sy, float sz) {
+    return sx > 0.f || (sx == 0.f && (sy > 0.f || (sy == 0.f && sz > 0.f)));
+}
+
+template <class S, bool kCount, int kEx>
+__global__ void __launch_bounds__(kThreads) pair_kernel_halfwarp(LeafView lv, typename S::P p,
+                                                                 const typename S::Rec *__restrict__ rec,
+                                                                 double *__restrict__) {
+    using Rec = typename S::Rec;
+    static_assert(!S::kCons && !S::kGasOnly, "half-warp arms: gravity-type stages");
+    __shared__ __align__(16) Rec xbuf[kWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const float rc = S::leaf_cut(p, 0.f, 0.f);
+    __shared__ int64_t leaf_slot;
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
+        const int alo = lv.leaf_start[a], ahi = lv.leaf_start[a + 1];
+        const int nsa = (ahi - alo + 15) >> 4;
+        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+        int t0 = warp;  // tiles are dealt to the block's warps in turn across the leaf's entries
+        for (int e = ib; e < ie; ++e) {
+            const crk_image im = lv.img[e];
+            const int b = im.b;
+            const bool self = b == a && im.sx == 0.f && im.sy == 0.f && im.sz == 0.f;
+            if (b < a || (b == a && !self && !positive_shift(im.sx, im.sy, im.sz))) continue;
+            const int blo = lv.leaf_start[b], bhi = lv.leaf_start[b + 1];
+            const int nsb = (bhi - blo + 15) >> 4;
+            const int ntile = nsa * nsb;
+            int t = t0;
+            for (; t < ntile; t += kWarps) {
+                const int u = t / nsb, v = t - u * nsb;
+                if (self && v < u) continue;
+                const bool diag = self && u == v;  // the same 16 particles in both halves: only A accumulates
+                const int idx = half ? blo + 16 * v + hl : alo + 16 * u + hl;
+                const bool valid = idx < (half ? bhi : ahi);
+                Rec r = rec[valid ? idx : (half ? blo : alo)];
+                if (half) S::shift(r, im.sx, im.sy, im.sz);
+                // slice boxes (valid lanes only), then the whole tile against the cut (warp-uniform)
+                float l0 = valid ? r.x : INFINITY, l1 = valid ? r.y : INFINITY, l2 = valid ? r.z : INFINITY;
+                float h0 = valid ? r.x : -INFINITY, h1 = valid ? r.y : -INFINITY, h2 = valid ? r.z : -INFINITY;
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) {
+                    l0 = fminf(l0, __shfl_xor_sync(CRK_FULL_MASK, l0, o));
+                    l1 = fminf(l1, __shfl_xor_sync(CRK_FULL_MASK, l1, o));
+                    l2 = fminf(l2, __shfl_xor_sync(CRK_FULL_MASK, l2, o));
+                    h0 = fmaxf(h0, __shfl_xor_sync(CRK_FULL_MASK, h0, o));
+                    h1 = fmaxf(h1, __shfl_xor_sync(CRK_FULL_MASK, h1, o));
+                    h2 = fmaxf(h2, __shfl_xor_sync(CRK_FULL_MASK, h2, o));
+                }
+                const float ol0 = __shfl_xor_sync(CRK_FULL_MASK, l0, 16), ol1 = __shfl_xor_sync(CRK_FULL_MASK, l1, 16),
+                            ol2 = __shfl_xor_sync(CRK_FULL_MASK, l2, 16), oh0 = __shfl_xor_sync(CRK_FULL_MASK, h0, 16),
+                            oh1 = __shfl_xor_sync(CRK_FULL_MASK, h1, 16), oh2 = __shfl_xor_sync(CRK_FULL_MASK, h2, 16);
+                const float gx = fmaxf(fmaxf(ol0 - h0, l0 - oh0), 0.f), gy = fmaxf(fmaxf(ol1 - h1, l1 - oh1), 0.f),
+                            gz = fmaxf(fmaxf(ol2 - h2, l2 - oh2), 0.f);
+                // empty halves give NaN/inf gaps: those tiles are skipped too
+                if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= rc * rc * 1.0001f + 1e-6f)) continue;
+                if (!valid) {  // a massless particle outside every cut: contributes exact zeros
+                    r = S::far_dummy(1e15f, 1e15f, 1e15f);
+                }
+                if constexpr (kEx == 1) {
+                    __syncwarp();
+                    xbuf[warp][lane] = r;
+                    __syncwarp();
+                }
+                typename S::I st;
+                S::init(p, st, r, a, 0, lane, 0);
+                const bool acc = valid && !(diag && half);
+#pragma unroll 2
+                for (int s = 0; s < 16; ++s) {
+                    const int pl = half ? (hl ^ s) : 16 + (hl ^ s);
+                    Rec q;
+                    if constexpr (kEx == 0) {
+                        q = shfl_rec(r, pl);
+                    } else if constexpr (kEx == 1) {
+                        q = xbuf[warp][pl];
+                    } else {
+                        const int pi = pl < 16 ? alo + 16 * u + pl : (diag ? alo + 16 * u : blo + 16 * v) + (pl - 16);
+                        const bool pv = pi < (pl < 16 || diag ? ahi : bhi);
+                        if (pv) {
+                            q = rec[pi];
+                            if (pl >= 16 && !diag) S::shift(q, im.sx, im.sy, im.sz);
+                        } else {
+                            q = S::far_dummy(1e15f, 1e15f, 1e15f);
+                        }
+                    }
+                    if (acc) S::template interact<kCount>(p, st, r, q);
+                }
+                if (acc) S::flush(p, st, stage_index(lv, idx));
+                if (kCount) {
+                    int c = acc ? st.cnt - (diag ? 1 : 0) : 0;  // the self pair of a diagonal tile
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
+                    if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+                }
+            }
+            t0 = t - ntile;  // continue the round robin in the next entry
+        }
+    }
+}
+
 // one i-group, tiles (packed sweep where the stage has one)
 template <class S, bool kCount>
 __device__ __forceinline__ void tile_group_any(const LeafView &lv, const typename S::P &p,
@@ -1088,7 +1358,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
             const bool act = i < hi;
             const Rec ri = rec[act ? i : g0];
             typename S::I st;
-            S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
+            S::init(p, st, ri, a, (g0 - lo) >> 5, lane, stage_index(lv, act ? i : g0));
             // group boxes (empty for groups without active lanes) and largest h
             float l0 = act ? ri.x : INFINITY, l1 = act ? ri.y : INFINITY, l2 = act ? ri.z : INFINITY;
             float h0 = act ? ri.x : -INFINITY, h1 = act ? ri.y : -INFINITY, h2 = act ? ri.z : -INFINITY;
@@ -1238,7 +1508,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_ring(LeafView lv, typena
             const bool act = i < hi;
             const Rec ri = rec[act ? i : g0];
             typename S::I st;
-            S::init(p, st, ri, a, (g0 - lo) >> 5, lane);
+            S::init(p, st, ri, a, (g0 - lo) >> 5, lane, stage_index(lv, act ? i : g0));
             float l0 = act ? ri.x : INFINITY, l1 = act ? ri.y : INFINITY, l2 = act ? ri.z : INFINITY;
             float h0 = act ? ri.x : -INFINITY, h1 = act ? ri.y : -INFINITY, h2 = act ? ri.z : -INFINITY;
             float hm = act ? lv.pos[i].w : 0.0f;
@@ -1360,11 +1630,11 @@ struct GasLists {
     int64_t groups;
 };
 
-// j-table entries staged per warp in shared memory (records of at most 32
+// j-table entries staged per warp in shared memory (records of at most 48
 // bytes; the hydro record is too large to stage, its lanes gather directly)
 template <class S>
 __host__ __device__ constexpr int table_cap() {
-    return sizeof(typename S::Rec) <= 32 ? 320 : 0;
+    return sizeof(typename S::Rec) <= 32 ? 320 : (sizeof(typename S::Rec) <= 48 ? 224 : 0);
 }
 
 // Exact neighbour lists, one warp per i-group.  The warp stages the group's
@@ -1434,7 +1704,7 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
         const bool act = i < hi;
         const Rec ri = rec[act ? i : g0];
         typename S::I st;
-        S::init(p, st, ri, a, q, lane);
+        S::init(p, st, ri, a, q, lane, stage_index(lv, act ? i : g0));
         const int c = act ? gl.cnt[i] : 0;
         // indices four rows ahead, so their loads overlap the pair arithmetic
         int k = 0;
@@ -1564,6 +1834,21 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
         else
             list_kernel<S, false><<<(unsigned)grid, kThreads, list_kernel_smem<S, false>(), ctx->stream>>>(v, p, rec, gl,
                                                                                                          part);
+    } else if (ctx->variant[kernel_id] >= CRK_VARIANT_HALFWARP_SHFL && S::kPair) {
+        if constexpr (S::kPair) {
+            S::zero_outputs(p, ctx->stream);
+            const int ex = ctx->variant[kernel_id] - CRK_VARIANT_HALFWARP_SHFL;
+            const unsigned gg = (unsigned)grid;
+            if (p.count) {
+                if (ex == 0) pair_kernel_halfwarp<S, true, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else if (ex == 1) pair_kernel_halfwarp<S, true, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else pair_kernel_halfwarp<S, true, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            } else {
+                if (ex == 0) pair_kernel_halfwarp<S, false, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else if (ex == 1) pair_kernel_halfwarp<S, false, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else pair_kernel_halfwarp<S, false, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            }
+        }
     } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
         if (p.count)
             pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
@@ -1667,6 +1952,30 @@ int crk_hydro(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, co
     HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, dvdt3, dudt, conservation,
              hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count};
     return run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+}
+
+int crk_extras(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *v3, const float *V, const float *A,
+               const float *B, const float *gradA, const float *gradB, float *rho_r, float *dvdx,
+               int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !v3 || !V || !A || !B || !gradA || !gradB || !rho_r || !dvdx))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    ExtrasP p{m, v3, V, A, B, gradA, gradB, rho_r, dvdx, lv->n, (unsigned long long *)pair_count};
+    return run_stage<ExtrasStage>(ctx, lv, p, true, CRK_K_EXTRAS);
+}
+
+int crk_hydro_limited(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m,
+                      const float *v3, const float *u, const float *V, const float *rho, const float *A,
+                      const float *B, const float *gradA, const float *gradB, const float *dvdx, float *dvdt3,
+                      float *dudt, double *conservation, int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !hp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !v3 || !u || !V || !rho || !A || !B || !gradA || !gradB || !dvdx || !dvdt3 || !dudt))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, dvdt3, dudt, conservation,
+             hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count, dvdx};
+    return run_stage<HydroLimStage>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
 }
 
 template <bool kGas>
@@ -1846,34 +2155,14 @@ __global__ void to_korder_kernel(int64_t n, int ncomp, const int32_t *__restrict
 }
 
 
-// Several gathers through two permutations in one pass: column k gets
-// dst[o] = src[perm_sel[o]] (o in the destination order).  One thread loads
-// both permutation entries once and has every column's load in flight.
-constexpr int kMaxPermCols = 40;
-struct PermCol {
-    float *dst;
-    const float *src;
-    int sel;  // 0: first permutation, 1: second
-};
-struct PermCols {
-    PermCol c[kMaxPermCols];
-    int ncol;
-};
-
-__global__ void permute_cols_kernel(int64_t n, const int32_t *__restrict__ p0, const int32_t *__restrict__ p1,
-                                    PermCols cols) {
+// One column through a permutation: dst[o] = src[perm[o]] (o in the
+// destination order).  One column per launch keeps the randomly read source
+// (n floats) about the size of L2, so each 32-byte sector is fetched from DRAM
+// about once; gathering many columns at once thrashes L2 (measured slower).
+__global__ void permute_col_kernel(int64_t n, const int32_t *__restrict__ perm, const float *__restrict__ src,
+                                   float *__restrict__ dst) {
     int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= n) return;
-    const int64_t q0 = p0[o], q1 = p1[o];
-    // every load first: a store through one column could alias a later column's source as far as
-    // the compiler knows, which would serialise the gathers
-    float v[kMaxPermCols];
-#pragma unroll
-    for (int k = 0; k < kMaxPermCols; ++k)
-        if (k < cols.ncol) v[k] = __ldg(cols.c[k].src + (cols.c[k].sel ? q1 : q0));
-#pragma unroll
-    for (int k = 0; k < kMaxPermCols; ++k)
-        if (k < cols.ncol) cols.c[k].dst[o] = v[k];
+    if (o < n) dst[o] = __ldg(src + perm[o]);
 }
 
 __global__ void cotangent_kernel(int64_t n, const float *__restrict__ a_g, const float4 *__restrict__ pos,
@@ -1893,7 +2182,7 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
     if (n == 0) return CRK_OK;
     if (!io->m || !io->v3 || !io->u) return crk_fail(ctx, CRK_EINVAL, "step inputs m, v3, u are required");
     if (gp->r_cut != lv->r_cut_grav) return crk_fail(ctx, CRK_ESTATE, "r_cut differs from the leaves' r_cut_grav");
-    float *buf = (float *)crk_scratch(ctx, 18, sizeof(float) * 48 * (size_t)n);
+    float *buf = (float *)crk_scratch(ctx, 18, sizeof(float) * 58 * (size_t)n);
     if (!buf) return crk_fail(ctx, CRK_ENOMEM, "step scratch");
     float *cur = buf;
     auto take = [&](int k) { float *r = cur; cur += (size_t)k * n; return r; };
@@ -1901,19 +2190,20 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
     float *B_k = take(3), *gA_k = take(3), *gB_k = take(9), *dv_k = take(3), *du_k = take(1), *rhob_k = take(1);
     float *Vb_k = take(1), *gx2_k = take(3), *gm2_k = take(1);
     float *m_g = take(1), *a_g = take(3), *abar_g = take(3), *gx_g = take(3), *gm_g = take(1);
+    float *rhoR_k = take(1), *dvdx_k = take(9);
     cudaStream_t st = ctx->stream;
     const int g = crk_grid(n, 256);
     crk_step_mark(ctx, 0);
     {
         // inputs into the two kernel orders: m, v, u (gas order) and m (gravity order)
-        PermCols in{};
-        auto col = [&](float *dst, const float *src, int sel) { in.c[in.ncol++] = PermCol{dst, src, sel}; };
-        col(m_k, io->m, 0);
-        for (int c = 0; c < 3; ++c) col(v_k + (size_t)c * n, io->v3 + (size_t)c * n, 0);
-        col(u_k, io->u, 0);
-        col(m_g, io->m, 1);
-        permute_cols_kernel<<<g, 256, 0, st>>>(n, lv->kperm, lv->kperm_g, in);
-        ++ctx->launches;
+        auto col = [&](float *dst, const float *src, const int32_t *perm) {
+            permute_col_kernel<<<g, 256, 0, st>>>(n, perm, src, dst);
+            ++ctx->launches;
+        };
+        col(m_k, io->m, lv->kperm);
+        for (int c = 0; c < 3; ++c) col(v_k + (size_t)c * n, io->v3 + (size_t)c * n, lv->kperm);
+        col(u_k, io->u, lv->kperm);
+        col(m_g, io->m, lv->kperm_g);
     }
     CRK_LAUNCH_CHECK(ctx, "step inputs");
     unsigned long long *cnt = (unsigned long long *)io->pair_count;
@@ -1928,8 +2218,16 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
         CorrP p{V_k, A_k, B_k, gA_k, gB_k, io->n_singular, n, nullptr};
         if ((rc = run_stage<CorrStage>(ctx, lv, p, true, CRK_K_CORRECTIONS, nullptr, true))) return rc;
     }
+    if (io->extras) {
+        ExtrasP p{m_k, v_k, V_k, A_k, B_k, gA_k, gB_k, rhoR_k, dvdx_k, n, nullptr};
+        if ((rc = run_stage<ExtrasStage>(ctx, lv, p, true, CRK_K_EXTRAS, nullptr, true))) return rc;
+    }
     crk_step_mark(ctx, 2);
-    {
+    if (io->extras) {
+        HydroP p{m_k, v_k, u_k, V_k, rhoR_k, A_k, B_k, gA_k, gB_k, dv_k, du_k, io->conservation,
+                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr, dvdx_k};
+        if ((rc = run_stage<HydroLimStage>(ctx, lv, p, true, CRK_K_HYDRO, io->conservation, true))) return rc;
+    } else {
         HydroP p{m_k, v_k, u_k, V_k, rho_k, A_k, B_k, gA_k, gB_k, dv_k, du_k, io->conservation,
                  hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr};
         if ((rc = run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, io->conservation, true))) return rc;
@@ -1983,16 +2281,14 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
                 {io->B, B_k, 3, lv->kinv},          {io->gradA, gA_k, 3, lv->kinv},    {io->gradB, gB_k, 9, lv->kinv},
                 {io->dvdt3, dv_k, 3, lv->kinv},     {io->dudt, du_k, 1, lv->kinv},     {io->a3, a_g, 3, lv->kinv_g},
                 {io->gx3_grav, gx_g, 3, lv->kinv_g}, {io->gm_grav, gm_g, 1, lv->kinv_g}, {io->gx3_geom, gx2_k, 3, lv->kinv},
-                {io->gm_geom, gm2_k, 1, lv->kinv}};
-    PermCols oc{};
+                {io->gm_geom, gm2_k, 1, lv->kinv},   {io->extras ? io->rho_r : nullptr, rhoR_k, 1, lv->kinv},
+                {io->extras ? io->dvdx : nullptr, dvdx_k, 9, lv->kinv}};
     for (const Out &o : outs)
         if (o.dst)
-            for (int c = 0; c < o.comp; ++c)
-                oc.c[oc.ncol++] = PermCol{o.dst + (size_t)c * n, o.src + (size_t)c * n, o.perm == lv->kinv_g ? 1 : 0};
-    if (oc.ncol > 0) {
-        permute_cols_kernel<<<g, 256, 0, st>>>(n, lv->kinv, lv->kinv_g, oc);
-        ++ctx->launches;
-    }
+            for (int c = 0; c < o.comp; ++c) {
+                permute_col_kernel<<<g, 256, 0, st>>>(n, o.perm, o.src + (size_t)c * n, o.dst + (size_t)c * n);
+                ++ctx->launches;
+            }
     CRK_LAUNCH_CHECK(ctx, "step outputs");
     crk_step_mark(ctx, 7);
     return CRK_OK;

@@ -112,14 +112,14 @@ void crk_graph_destroy(crk_graph *g) {
 // Autotuner: time every variant of every kernel on these leaves (CUDA events
 // on the context stream, best of `reps` after one warm-up) and keep the
 // fastest.  Variants that need neighbour lists the leaves do not hold are
-// skipped.  ms_out (host, 6 x 5, may be NULL) receives the timings (-1 when
+// skipped.  ms_out (host, 6 x CRK_N_VARIANTS, may be NULL) receives the timings (-1 when
 // skipped), best_out (host, 6, may be NULL) the chosen variants.
 int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io, int reps, float *ms_out, int *best_out) {
     if (!ctx) return CRK_EINVAL;
     if (!lv || !gp || !hp || !io) return crk_fail(ctx, CRK_EINVAL, "null argument");
     if (reps < 1) reps = 1;
-    const int nvar = CRK_VARIANT_RING16 + 1;
+    const int nvar = CRK_N_VARIANTS;
     int keep[6];
     for (int k = 0; k < 6; ++k) keep[k] = ctx->variant[k];
     // inputs of the later kernels come from one full step
@@ -142,6 +142,7 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
         for (int v = 0; v < nvar; ++v) {
             if (ms_out) ms_out[k * nvar + v] = -1.0f;
             if (v == CRK_VARIANT_LISTS && !have_lists) continue;
+            if (v >= CRK_VARIANT_HALFWARP_SHFL && gas) continue;  // half-warp arms: gravity kernels only
             ctx->variant[k] = v;
             float tmin = 1e30f;
             for (int r = 0; r <= reps; ++r) {

@@ -21,13 +21,17 @@ CRK_ESTATE = -5
 CRK_ETIMEOUT = -6
 CRK_ETOOLARGE = -7
 NOALLOC_MAX_PARTICLES = 1 << 21
-KERNELS = {"geometry": 0, "corrections": 1, "hydro": 2, "gravity": 3, "gravity_adjoint": 4, "geometry_adjoint": 5}
+KERNELS = {"geometry": 0, "corrections": 1, "hydro": 2, "gravity": 3, "gravity_adjoint": 4, "geometry_adjoint": 5,
+           "extras": 6}
 VARIANT_LISTS = 0
 VARIANT_TILES = 1
 VARIANT_TILES16 = 2
 VARIANT_TILES8 = 3
 VARIANT_RING16 = 4
-N_VARIANTS = 5
+VARIANT_HALFWARP_SHFL = 5
+VARIANT_HALFWARP_SMEM = 6
+VARIANT_HALFWARP_LOAD = 7
+N_VARIANTS = 8
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
                 -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT", -7: "CRK_ETOOLARGE"}
 
@@ -66,7 +70,8 @@ class crk_batch(ctypes.Structure):
 class crk_step_io(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "m", "v3", "u", "V", "rho", "A", "B", "gradA", "gradB", "dvdt3", "dudt", "conservation", "a3", "abar3",
-        "gx3_grav", "gm_grav", "rhobar", "Vbar", "gx3_geom", "gm_geom", "n_singular", "pair_count")]
+        "gx3_grav", "gm_grav", "rhobar", "Vbar", "gx3_geom", "gm_geom", "n_singular", "pair_count")] + [
+        ("extras", ctypes.c_int), ("rho_r", ctypes.c_void_p), ("dvdx", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -94,6 +99,8 @@ SIGNATURES = {
     "crk_geometry": [_P, _P, _P, _P, _P, _P],
     "crk_corrections": [_P, _P, _P, _P, _P, _P, _P, _P],
     "crk_hydro": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 13,
+    "crk_extras": [_P] * 12,
+    "crk_hydro_limited": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 14,
     "grav_short": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P],
     "grav_short_adjoint": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P, _P],
     "crk_geometry_adjoint": [_P, _P, _P, _P, _P, _P, _P, _P],

@@ -119,7 +119,7 @@ def test_variant_switch(api, ctx):
 
     assert ctx.get_variant("hydro") == 0 and ctx.get_variant("gravity") == 1
     with pytest.raises(N.CrkError):
-        ctx.set_variant("gravity", 7)
+        ctx.set_variant("gravity", N.N_VARIANTS)
     ctx.set_variant("hydro", 1)
     assert ctx.get_variant("hydro") == 1
     ctx.set_variant("hydro", 0)
@@ -147,9 +147,12 @@ def test_error_statuses(api, ctx):
 
 VARIANTS = [0, 1, 2, 3, 4]
 VARIANT_IDS = ["lists", "tiles", "tiles16", "tiles8", "ring16"]
+# the gravity kernels also have the half-warp leaf-pair arms (shuffle, shared memory, second load)
+GRAV_VARIANTS = VARIANTS + [5, 6, 7]
+GRAV_VARIANT_IDS = VARIANT_IDS + ["halfwarp_shfl", "halfwarp_smem", "halfwarp_load"]
 
 
-@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
+@pytest.mark.parametrize("variant", GRAV_VARIANTS, ids=GRAV_VARIANT_IDS)
 @pytest.mark.parametrize("name", ["tiny_mesh", "clustered24", "random1000_leaf7", "random777_mesh3"])
 def test_gravity_parity(api, ctx, name, variant):
     b = box_of(name)
@@ -218,7 +221,7 @@ def test_hydro_chain_parity(api, ctx, name, variant):
     assert int(out["count_geom"].item()) == int(out["count_hydro"].item())
 
 
-@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
+@pytest.mark.parametrize("variant", GRAV_VARIANTS, ids=GRAV_VARIANT_IDS)
 @pytest.mark.parametrize("name", ["clustered12", "clustered24"])
 def test_adjoint_parity(api, ctx, name, variant):
     b = box_of(name)
