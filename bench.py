@@ -387,45 +387,46 @@ EXTRAS_FLOPS_PER_PAIR = {"extras": 103, "hydro_limited": 215, "hydro": 160}
 
 
 def extras_chain(api, ctx, db, stream, peak_tflops, reps=3):
-    """The Extras row after the step: crk_extras and crk_hydro_limited on the same leaves.
-
-    Single calls (caller-order arrays), each timed with CUDA events on the
-    context stream, best of `reps` after one warm-up, beside the plain crk_hydro
-    on the same inputs.  Outside the headline step and its timed region.
+    """The Extras row: the whole step with the Extras chain (crk_extras after the
+    corrections, crk_hydro_limited in place of crk_hydro) against the plain step,
+    on the same leaves, through crk_step_profile (events on the context stream,
+    mean of `reps` steps after a warm-up).  Outside the headline timed region.
     """
+    import ctypes as _ct
+
     import torch
+    from paper_2310_16122_gb300 import native
 
     lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
-    V, rho, _ = api.geometry(ctx, lv, db.m)
-    A, B, gA, gB, _ = api.corrections(ctx, lv, V)
-    rr, G, c = api.extras(ctx, lv, db.m, db.v3, V, A, B, gA, gB, count=True)
-    torch.cuda.synchronize()
-    pairs = int(c.cpu().numpy()[0])
-    calls = {
-        "extras": lambda: api.extras(ctx, lv, db.m, db.v3, V, A, B, gA, gB),
-        "hydro_limited": lambda: api.hydro_limited(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB, G),
-        "hydro": lambda: api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB),
-    }
-    ms = {}
-    for k, f in calls.items():
-        f()
-        best = None
+    out = {}
+    for name, ex in (("plain", False), ("extras", True)):
+        io = api.StepIO(ctx, db, outputs=False, extras=ex)
+        api.step(ctx, lv, db, io, count=True)
+        api.step(ctx, lv, db, io)
+        torch.cuda.synchronize()
+        pairs = int(io.pair_count.cpu().numpy()[1])
+        ctx.check(native.lib().crk_step_profile(ctx.handle, reps))
         for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            f()
-            e1.record(stream)
-            e1.synchronize()
-            t = e0.elapsed_time(e1)
-            best = t if best is None else min(best, t)
-        ms[k] = best
-    tf = {k: EXTRAS_FLOPS_PER_PAIR[k] * pairs / (ms[k] * 1e-3) / 1e12 for k in ms}
-    return {"pairs_per_launch": pairs, "ms": {k: round(v, 4) for k, v in ms.items()},
-            "pairs_per_s": {k: pairs / (v * 1e-3) for k, v in ms.items()},
+            api.step(ctx, lv, db, io)
+        prof = (_ct.c_float * 7)()
+        nprof = _ct.c_int(0)
+        ctx.check(native.lib().crk_step_profile_read(ctx.handle, prof, _ct.byref(nprof)))
+        ctx.check(native.lib().crk_step_profile(ctx.handle, 0))
+        out[name] = {"corrections_interval": float(prof[1]), "hydro_interval": float(prof[2]),
+                     "step": float(sum(prof))}
+    ms_extras = out["extras"]["corrections_interval"] - out["plain"]["corrections_interval"]
+    ms_lim = out["extras"]["hydro_interval"]
+    tf = {"extras": EXTRAS_FLOPS_PER_PAIR["extras"] * pairs / (ms_extras * 1e-3) / 1e12,
+          "hydro_limited": EXTRAS_FLOPS_PER_PAIR["hydro_limited"] * pairs / (ms_lim * 1e-3) / 1e12}
+    return {"pairs_per_launch": pairs,
+            "ms": {"extras": round(ms_extras, 4), "hydro_limited": round(ms_lim, 4),
+                   "hydro": round(out["plain"]["hydro_interval"], 4),
+                   "step_with_extras": round(out["extras"]["step"], 4), "step": round(out["plain"]["step"], 4)},
+            "pairs_per_s": {"extras": pairs / (ms_extras * 1e-3), "hydro_limited": pairs / (ms_lim * 1e-3)},
             "tflops": tf, "frac_of_fp32_peak": {k: v / peak_tflops for k, v in tf.items()},
             "flops_per_pair": EXTRAS_FLOPS_PER_PAIR,
-            "note": "single calls in the caller's order (record gathers through the leaf permutation), "
-                    "best of %d after a warm-up" % reps}
+            "note": "crk_step with and without the Extras chain on the same leaves (kernel-order "
+                    "intermediates); extras = difference of the corrections intervals, mean of %d steps" % reps}
 
 
 def batched_vs_plain(args, local, dist):
