@@ -261,8 +261,12 @@ def main():
     del lv_c
     torch.cuda.synchronize()
     c = io.pair_count.cpu().numpy()
+    sw = io.swept_count.cpu().numpy()
     pairs = {"geometry": int(c[0]), "corrections": int(c[1]), "hydro": int(c[1]), "gravity": int(c[2]),
              "gravity_adjoint": int(c[2]), "geometry_adjoint": int(c[0])}
+    # candidate pair evaluations of the forward kernels (their variants); in-range pairs / candidates
+    swept = {"geometry": int(sw[0]), "hydro": int(sw[1]), "gravity": int(sw[2])}
+    useful = {k: (pairs[k] / v if v else None) for k, v in swept.items()}
     pairs_step = sum(pairs.values())
     for _ in range(args.warmup):
         step()
@@ -339,8 +343,12 @@ def main():
         traffic = tr.get(args.workload, {}).get(dom)
     except Exception:
         pass
+    f_med = float(peaks.get("clocks_under_load", {}).get("sm_mhz_median", f_max))
+    f_run = float(clk.get("sm_mhz") or f_max)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic, "kernel": dom,
+                "frac_at_clock": {f"{f_run:.0f} MHz (median during the timed steps)": achieved / (peak_tflops * f_run / f_max),
+                                  f"{f_med:.0f} MHz (median under a GEMM load)": achieved / (peak_tflops * f_med / f_max)},
                 "peak_basis": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flop x {f_max:.0f} MHz (max SM clock)",
                 "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs_per_launch": pairs[dom],
                 "ms_per_launch": kern[dom]}
@@ -355,7 +363,8 @@ def main():
                        "leaves": n_leaves, "max_leaf": box.max_leaf, "r_cut": box.r_cut,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs (~%.1f GB) larger than L2 (129 MB)" % (h2d / 1e9)},
-            "pairs_per_step": pairs, "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+            "pairs_per_step": pairs, "candidates_per_step": swept, "in_range_fraction": useful,
+            "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
             "variants": variants,
             "autotune_ms": tuning["ms"] if tuning else None,
             "kernels_tflops": all_flops / (kern_ms * 1e-3) / 1e12,

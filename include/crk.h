@@ -269,7 +269,11 @@ int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, con
  * caller's order and layout.  The adjoint cotangents default to the loss
  * sum |a|^2 + sum_gas rho (abar3 = NULL: 2a; rhobar = NULL: 1 on gas); Vbar
  * may be NULL.  pair_count (device int64[3], may be NULL) receives the
- * geometry, hydro and gravity pair counts; n_singular and conservation as for
+ * geometry, hydro and gravity pair counts, and swept_count (read only with
+ * pair_count) the candidate pair evaluations of the same kernels (tiles: every
+ * active lane of a group times every swept candidate; lists: the list
+ * entries), so pair_count/swept_count is the useful fraction of the pair work;
+ * n_singular and conservation as for
  * the single calls.  With extras != 0 the step runs crk_extras after the
  * corrections and crk_hydro_limited in place of crk_hydro, with rho_r as the
  * equation-of-state density (rho then still receives the geometry density). */
@@ -287,6 +291,7 @@ typedef struct {
     int64_t *pair_count;                    /* int64[3], may be NULL */
     int extras;                             /* nonzero: Extras chain (see below) */
     float *rho_r, *dvdx;                    /* Extras outputs, may be NULL */
+    int64_t *swept_count;                   /* int64[3], may be NULL: candidate pair evaluations */
 } crk_step_io;
 
 int crk_step(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,

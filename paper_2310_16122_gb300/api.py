@@ -337,6 +337,7 @@ class StepIO:
         self.gx_grav, self.gm_grav, self.gx_geom, self.gm_geom = e(3, n), e(n), e(3, n), e(n)
         self.n_singular = torch.zeros(1, dtype=torch.int32, device=ctx.device)
         self.pair_count = torch.zeros(3, dtype=torch.int64, device=ctx.device)
+        self.swept_count = torch.zeros(3, dtype=torch.int64, device=ctx.device)
 
     def c(self, count: bool = False) -> N.crk_step_io:
         d, P = self.db, lambda t: t.data_ptr() if t is not None else None
@@ -344,7 +345,7 @@ class StepIO:
                              P(self.gB), P(self.dv), P(self.du), P(self.cons), P(self.acc), None, P(self.gx_grav),
                              P(self.gm_grav), None, None, P(self.gx_geom), P(self.gm_geom), P(self.n_singular),
                              P(self.pair_count) if count else None, 1 if self.extras else 0, P(self.rho_r),
-                             P(self.dvdx))
+                             P(self.dvdx), P(self.swept_count) if count else None)
 
 
 def step(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, count: bool = False) -> None:

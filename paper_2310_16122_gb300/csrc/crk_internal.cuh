@@ -71,6 +71,7 @@ struct crk_nlist {
     int32_t *cnt = nullptr;     // [n] list length per kernel-order position
     uint16_t *list = nullptr;   // per-lane indices into the group's j table, k-major rows of 32
     int32_t *uoff = nullptr;    // [groups + 1] first j-table entry of each group
+    int32_t *unum = nullptr;    // [groups] j-table size of each group
     uint32_t *ucode = nullptr;  // j-table entries: image << 10 | j inside the j-leaf
     int64_t groups = 0, entries = 0, table = 0;
 };

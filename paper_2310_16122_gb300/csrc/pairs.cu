@@ -106,6 +106,7 @@ struct GravP {
     float c[6];
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 struct GravStage {
@@ -213,6 +214,7 @@ struct GravAdjP {
     float c[6];
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 struct GravAdjStage {
@@ -356,6 +358,7 @@ struct GeomP {
     float *V, *rho;
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 struct GeomStage {
@@ -404,6 +407,7 @@ struct GeomAdjP {
     float *gx3, *gm;
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 struct GeomAdjStage {
@@ -463,6 +467,7 @@ struct CorrP {
     int32_t *n_singular;
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 struct CorrStage {
@@ -608,6 +613,7 @@ struct HydroP {
     int64_t n;
     unsigned long long *count;
     const float *dvg;  // limited viscosity: velocity gradient [9][n], dv^a/dx^b at 3a+b
+    unsigned long long *swept;  // counting runs: candidate pair evaluations, may be NULL
 };
 
 struct HydroRec {
@@ -762,6 +768,7 @@ struct ExtrasP {
     float *rhoR, *dvg;
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 struct ExtrasStage {
@@ -850,16 +857,18 @@ struct ExtrasStage {
 // lanes, in the order the sweep meets them), so that a pair kernel stages each
 // j of the group once and every lane reads its j from that table.
 struct ListP {
-    uint16_t *list;                    // fill: per-lane table indices, k-major rows of 32
-    uint32_t *ucode;                   // fill: table entries
+    uint16_t *list;                    // per-lane table indices, k-major rows of 32 (written when non-null)
+    uint32_t *ucode;                   // table entries (written when non-null)
     const int32_t *gstart, *goff, *uoff;
-    int32_t *cnt;                      // count: list length per kernel-order position
-    int32_t *ucnt;                     // count: table size per group
-    int32_t *umax;                     // count: largest table (atomicMax)
-    int fill;
+    int32_t *cnt;                      // list length per kernel-order position (written when non-null)
+    int32_t *ucnt;                     // table size per group (written when non-null)
+    int32_t *umax;                     // largest table (atomicMax), may be null
+    int32_t *overflow;                 // set when a list or a table exceeds its capacity, may be null
+    int cap_rows, cap_table;           // capacity of one lane's list and of one group's table
     float rc2;
     int64_t n;
     unsigned long long *count;
+    unsigned long long *swept;  // counting runs: candidate pair evaluations (tiles and lists), may be NULL
 };
 
 template <bool kGas>
@@ -897,8 +906,8 @@ struct ListStage {
         s.u = 0;
         s.cnt = 0;
         s.grp = p.gstart[a] + q;
-        s.out = p.fill ? p.list + (size_t)p.goff[s.grp] * 32 + lane : nullptr;
-        s.uout = p.fill ? p.ucode + p.uoff[s.grp] : nullptr;
+        s.out = p.list ? p.list + (size_t)p.goff[s.grp] * 32 + lane : nullptr;
+        s.uout = p.ucode ? p.ucode + p.uoff[s.grp] : nullptr;
     }
     // called by all 32 lanes together (the sweep is warp-uniform)
     template <bool kCount>
@@ -917,19 +926,19 @@ struct ListStage {
         const unsigned m = __ballot_sync(CRK_FULL_MASK, in);
         if (m) {
             if (in) {
-                if (s.out) s.out[(size_t)s.c * 32] = (uint16_t)s.u;
+                if (s.out && s.c < p.cap_rows && s.u < p.cap_table) s.out[(size_t)s.c * 32] = (uint16_t)s.u;
                 ++s.c;
             }
-            if (s.uout && (int)(threadIdx.x & 31) == __ffs(m) - 1) s.uout[s.u] = rj.code;
+            if (s.uout && (int)(threadIdx.x & 31) == __ffs(m) - 1 && s.u < p.cap_table) s.uout[s.u] = rj.code;
             ++s.u;
         }
     }
     __device__ static void finish(const P &p, I &s, const Rec &, int32_t, int64_t i) {
-        if (p.fill) return;
-        p.cnt[i] = s.c;
+        if (p.cnt) p.cnt[i] = s.c;
+        if (p.overflow && (s.c > p.cap_rows || s.u > p.cap_table)) atomicOr(p.overflow, 1);
         if ((threadIdx.x & 31) == 0) {  // lane 0 is always active
-            p.ucnt[s.grp] = s.u;
-            atomicMax(p.umax, s.u);
+            if (p.ucnt) p.ucnt[s.grp] = s.u;
+            if (p.umax) atomicMax(p.umax, s.u);
         }
     }
     __device__ static void finish_other(const P &, int32_t) {}
@@ -981,6 +990,7 @@ __device__ __forceinline__ void tile_group(const LeafView &lv, const typename S:
         hm = fmaxf(hm, __shfl_xor_sync(CRK_FULL_MASK, hm, o));
     }
     int cnt = 0;
+    unsigned long long swept = 0;  // counting runs: candidates swept
     for (int e = ib; e < ie; ++e) {
         const crk_image im = lv.img[e];
         const int jlo = lv.leaf_start[im.b];
@@ -1015,6 +1025,7 @@ __device__ __forceinline__ void tile_group(const LeafView &lv, const typename S:
             if (cnt >= 32) {
                 __syncwarp();
                 for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[k]);
+                if (kCount) swept += cnt;
                 cnt = 0;
                 __syncwarp();
             }
@@ -1022,6 +1033,7 @@ __device__ __forceinline__ void tile_group(const LeafView &lv, const typename S:
     }
     __syncwarp();
     for (int k = 0; k < cnt; ++k) S::template interact<kCount>(p, st, ri, buf[k]);
+    if (kCount) swept += cnt;
     __syncwarp();
     if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
     if constexpr (S::kCons) {
@@ -1039,6 +1051,9 @@ __device__ __forceinline__ void tile_group(const LeafView &lv, const typename S:
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
         if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+        // candidate evaluations: every active lane evaluated every swept candidate
+        const unsigned long long na = __popc(__ballot_sync(CRK_FULL_MASK, act));
+        if (lane == 0 && p.swept) atomicAdd(p.swept, swept * na);
     }
 }
 
@@ -1082,6 +1097,7 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
         __syncwarp();
     };
     int cnt = 0;
+    unsigned long long swept = 0;  // counting runs: candidates swept
     for (int e = ib; e < ie; ++e) {
         const crk_image im = lv.img[e];
         const int jlo = lv.leaf_start[im.b];
@@ -1113,17 +1129,21 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
             cnt += __popc(m);
             if (cnt >= 32) {
                 sweep(cnt);
+                if (kCount) swept += cnt;
                 cnt = 0;
             }
         }
     }
     sweep(cnt);
+    if (kCount) swept += cnt;
     if (act) S::finish2(p, st, lv.korder ? i : lv.kperm[i]);
     if (kCount) {
         int c = act ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
         if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+        const unsigned long long na = __popc(__ballot_sync(CRK_FULL_MASK, act));
+        if (lane == 0 && p.swept) atomicAdd(p.swept, swept * na);
     }
 }
 
@@ -1624,7 +1644,7 @@ __global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, 
 struct GasLists {
     const int32_t *gstart, *goff, *cnt;
     const uint16_t *list;
-    const int32_t *uoff;
+    const int32_t *uoff, *unum;
     const uint32_t *ucode;
     const int32_t *gleaf;
     int64_t groups;
@@ -1673,7 +1693,7 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
             __syncwarp();
         }
         const uint32_t *U = gl.ucode + gl.uoff[grp];
-        const int nu = gl.uoff[grp + 1] - gl.uoff[grp];
+        const int nu = gl.unum[grp];
         // table entry -> shifted record of j
         auto fetch = [&](uint32_t code) -> Rec {
             float4 t;
@@ -1735,9 +1755,14 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
         }
         if (kCount) {
             int cn = act ? st.cnt - 1 : 0;
+            int sw = c;  // candidate evaluations: the list entries
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+                sw += __shfl_xor_sync(CRK_FULL_MASK, sw, o);
+            }
             if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+            if (lane == 0 && p.swept && sw) atomicAdd(p.swept, (unsigned long long)sw);
         }
     }
     if constexpr (S::kCons) {
@@ -1755,6 +1780,21 @@ size_t list_kernel_smem() {
         set = true;
     }
     return bytes;
+}
+
+// capacities of the one-pass gas lists (adaptive h keeps a gas particle near 58 neighbours;
+// the largest lane list and group table seen in the clustered workloads are ~95 and ~360)
+constexpr int kGasListCapRows = 128;
+constexpr int kGasTableCap = 512;
+
+// fixed-capacity list and table offsets: goff[g] = g capr, uoff[g] = g capt
+__global__ void strided_offsets_kernel(int64_t m, int capr, int capt, int32_t *__restrict__ goff,
+                                       int32_t *__restrict__ uoff) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < m) {
+        goff[g] = (int32_t)(g * capr);
+        uoff[g] = (int32_t)(g * capt);
+    }
 }
 
 // groups of each leaf, and the leaf of each group
@@ -1826,8 +1866,9 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
                gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue, korder ? 1 : 0};
     if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
+    if (p.swept) CRK_CUDA(ctx, cudaMemsetAsync(p.swept, 0, sizeof(unsigned long long), ctx->stream));
     if (lists) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.ucode, nls.gleaf, nls.groups};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.unum, nls.ucode, nls.gleaf, nls.groups};
         if (p.count)
             list_kernel<S, true><<<(unsigned)grid, kThreads, list_kernel_smem<S, true>(), ctx->stream>>>(v, p, rec, gl,
                                                                                                        part);
@@ -2008,45 +2049,85 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     const GroupTable gt{gstart, gleaf, ngroups};
     const unsigned ggrid = (unsigned)((ngroups + kWarps - 1) / kWarps > 0 ? (ngroups + kWarps - 1) / kWarps : 1);
     const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
-    int32_t *ucnt = (int32_t *)crk_scratch(ctx, 9, sizeof(int32_t) * (size_t)(ngroups + 1));
-    if (!ucnt) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
-    CRK_CUDA(ctx, cudaMemsetAsync(ucnt, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
-    CRK_CUDA(ctx, cudaMemsetAsync(tot + 4, 0, sizeof(int32_t), st));
+    int32_t *ucnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+    if (!ucnt) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
     gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
-    ListP pc{nullptr, nullptr, gstart, nullptr, nullptr, cnt, ucnt, tot + 4, 0, rc2, n, nullptr};
-    pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pc, rec, gt, nullptr);
-    ctx->launches += 3;
-    CRK_LAUNCH_CHECK(ctx, "neighbour counts");
-    int32_t *goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
-    int32_t *uoff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
-    int32_t *gk = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(ngroups + 1));
-    if (!goff || !uoff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
-    CRK_CUDA(ctx, cudaMemsetAsync(gk, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
-    list_group_k_kernel<<<(unsigned)nl, kThreads, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, kGas, gstart, cnt, gk);
-    ++ctx->launches;
-    rc = crk_exclusive_scan_i32(ctx, gk, goff, ngroups + 1, tot + 1);
-    if (rc) return rc;
-    rc = crk_exclusive_scan_i32(ctx, ucnt, uoff, ngroups + 1, tot + 2);
-    if (rc) return rc;
-    int32_t sizes[5] = {0, 0, 0, 0, 0};
-    CRK_CUDA(ctx, cudaMemcpyAsync(sizes, tot, sizeof(sizes), cudaMemcpyDeviceToHost, st));
-    CRK_CUDA(ctx, cudaStreamSynchronize(st));
-    const int32_t rows = sizes[1], umax = sizes[4];
-    const int64_t tsize = (int64_t)(uint32_t)sizes[2];
-    // table indices are 16-bit, and the offsets 32-bit: without lists the kernels use tiles
-    if (umax > 65535 || rows < 0 || sizes[2] < 0) {
-        if (ctx->trace) fprintf(stderr, "[crk] %s lists skipped (largest group table %d)\n", kGas ? "gas" : "gravity", umax);
-        return CRK_OK;
+    ctx->launches += 2;
+    int32_t *goff = nullptr, *uoff = nullptr;
+    uint16_t *list = nullptr;
+    uint32_t *ucode = nullptr;
+    int64_t entries = 0, tsize = 0;
+    // Gas lists: one pass into fixed capacities (a lane's list and a group's table), which the
+    // adaptive smoothing lengths keep well above the largest counts; the exact two-pass build
+    // (count, scan, fill) runs only if something overflowed.
+    const int capr = kGasListCapRows, capt = kGasTableCap;
+    bool done = false;
+    if (kGas && (int64_t)ngroups * capt < 2147483647LL) {
+        goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+        uoff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+        list = (uint16_t *)crk_leaves_alloc(ctx, lv, sizeof(uint16_t) * (size_t)ngroups * capr * 32);
+        ucode = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)ngroups * capt);
+        if (!goff || !uoff || !list || !ucode) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
+        strided_offsets_kernel<<<crk_grid(ngroups + 1, 256), 256, 0, st>>>(ngroups + 1, capr, capt, goff, uoff);
+        CRK_CUDA(ctx, cudaMemsetAsync(tot + 5, 0, sizeof(int32_t), st));
+        ListP pf{list, ucode, gstart, goff, uoff, cnt, ucnt, nullptr, tot + 5, capr, capt, rc2, n, nullptr};
+        pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
+        ctx->launches += 2;
+        CRK_LAUNCH_CHECK(ctx, "neighbour lists");
+        int32_t ovf = 1;
+        CRK_CUDA(ctx, cudaMemcpyAsync(&ovf, tot + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CRK_CUDA(ctx, cudaStreamSynchronize(st));
+        if (ovf == 0) {
+            done = true;
+            entries = (int64_t)ngroups * capr * 32;
+            tsize = (int64_t)ngroups * capt;
+        } else if (ctx->trace) {
+            fprintf(stderr, "[crk] gas lists: a list or table exceeded its capacity, exact build\n");
+        }
     }
-    const int64_t entries = (int64_t)rows * 32;
-    uint16_t *list = (uint16_t *)crk_leaves_alloc(ctx, lv, sizeof(uint16_t) * (size_t)(entries > 0 ? entries : 1));
-    uint32_t *ucode = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(tsize > 0 ? tsize : 1));
-    if (!list || !ucode)
-        return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
-    ListP pf{list, ucode, gstart, goff, uoff, cnt, nullptr, nullptr, 1, rc2, n, nullptr};
-    pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
-    ++ctx->launches;
-    CRK_LAUNCH_CHECK(ctx, "neighbour lists");
+    if (!done) {
+        CRK_CUDA(ctx, cudaMemsetAsync(ucnt, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
+        CRK_CUDA(ctx, cudaMemsetAsync(tot + 4, 0, sizeof(int32_t), st));
+        ListP pc{nullptr, nullptr, gstart, nullptr, nullptr, cnt, ucnt, tot + 4, nullptr, 2147483647, 2147483647,
+                 rc2, n, nullptr};
+        pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pc, rec, gt, nullptr);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "neighbour counts");
+        goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+        uoff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+        int32_t *gk = (int32_t *)crk_scratch(ctx, 8, sizeof(int32_t) * (size_t)(ngroups + 1));
+        if (!goff || !uoff || !gk) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
+        CRK_CUDA(ctx, cudaMemsetAsync(gk, 0, sizeof(int32_t) * (size_t)(ngroups + 1), st));
+        list_group_k_kernel<<<(unsigned)nl, kThreads, 0, st>>>(nl, lv->leaf_start, lv->leaf_ngas, kGas, gstart, cnt,
+                                                               gk);
+        ++ctx->launches;
+        rc = crk_exclusive_scan_i32(ctx, gk, goff, ngroups + 1, tot + 1);
+        if (rc) return rc;
+        rc = crk_exclusive_scan_i32(ctx, ucnt, uoff, ngroups + 1, tot + 2);
+        if (rc) return rc;
+        int32_t sizes[5] = {0, 0, 0, 0, 0};
+        CRK_CUDA(ctx, cudaMemcpyAsync(sizes, tot, sizeof(sizes), cudaMemcpyDeviceToHost, st));
+        CRK_CUDA(ctx, cudaStreamSynchronize(st));
+        const int32_t rows = sizes[1], umax = sizes[4];
+        tsize = (int64_t)(uint32_t)sizes[2];
+        // table indices are 16-bit, and the offsets 32-bit: without lists the kernels use tiles
+        if (umax > 65535 || rows < 0 || sizes[2] < 0) {
+            if (ctx->trace)
+                fprintf(stderr, "[crk] %s lists skipped (largest group table %d)\n", kGas ? "gas" : "gravity", umax);
+            return CRK_OK;
+        }
+        entries = (int64_t)rows * 32;
+        list = (uint16_t *)crk_leaves_alloc(ctx, lv, sizeof(uint16_t) * (size_t)(entries > 0 ? entries : 1));
+        ucode = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)(tsize > 0 ? tsize : 1));
+        if (!list || !ucode)
+            return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation (%lld entries)", (long long)entries);
+        ListP pf{list, ucode, gstart, goff, uoff, nullptr, nullptr, nullptr, nullptr, 2147483647, 2147483647,
+                 rc2, n, nullptr};
+        pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "neighbour lists");
+    }
+    out.unum = ucnt;
     out.uoff = uoff;
     out.ucode = ucode;
     out.table = tsize;
@@ -2125,7 +2206,7 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.ucode, nls.gleaf, nls.groups};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.unum, nls.ucode, nls.gleaf, nls.groups};
         const int64_t lgrid = (nls.groups + kWarps - 1) / kWarps;
         list_kernel<GravStage, false><<<(unsigned)(lgrid > 0 ? lgrid : 1), kThreads,
                                         list_kernel_smem<GravStage, false>(), ctx->stream>>>(v, p, rec, gl, nullptr);
@@ -2207,9 +2288,10 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
     }
     CRK_LAUNCH_CHECK(ctx, "step inputs");
     unsigned long long *cnt = (unsigned long long *)io->pair_count;
+    unsigned long long *swc = cnt ? (unsigned long long *)io->swept_count : nullptr;
     int rc;
     {
-        GeomP p{m_k, V_k, rho_k, n, cnt ? cnt + 0 : nullptr};
+        GeomP p{m_k, V_k, rho_k, n, cnt ? cnt + 0 : nullptr, swc ? swc + 0 : nullptr};
         if ((rc = run_stage<GeomStage>(ctx, lv, p, true, CRK_K_GEOMETRY, nullptr, true))) return rc;
     }
     crk_step_mark(ctx, 1);
@@ -2225,11 +2307,13 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
     crk_step_mark(ctx, 2);
     if (io->extras) {
         HydroP p{m_k, v_k, u_k, V_k, rhoR_k, A_k, B_k, gA_k, gB_k, dv_k, du_k, io->conservation,
-                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr, dvdx_k};
+                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr, dvdx_k,
+                 swc ? swc + 1 : nullptr};
         if ((rc = run_stage<HydroLimStage>(ctx, lv, p, true, CRK_K_HYDRO, io->conservation, true))) return rc;
     } else {
         HydroP p{m_k, v_k, u_k, V_k, rho_k, A_k, B_k, gA_k, gB_k, dv_k, du_k, io->conservation,
-                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr};
+                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, cnt ? cnt + 1 : nullptr, nullptr,
+                 swc ? swc + 1 : nullptr};
         if ((rc = run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, io->conservation, true))) return rc;
     }
     crk_step_mark(ctx, 3);
@@ -2242,6 +2326,7 @@ int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp
         for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
         p.n = n;
         p.count = cnt ? cnt + 2 : nullptr;
+        p.swept = swc ? swc + 2 : nullptr;
         if ((rc = run_stage<GravStage>(ctx, lv, p, false, CRK_K_GRAVITY, nullptr, true))) return rc;
     }
     crk_step_mark(ctx, 4);

@@ -71,7 +71,8 @@ class crk_step_io(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "m", "v3", "u", "V", "rho", "A", "B", "gradA", "gradB", "dvdt3", "dudt", "conservation", "a3", "abar3",
         "gx3_grav", "gm_grav", "rhobar", "Vbar", "gx3_geom", "gm_geom", "n_singular", "pair_count")] + [
-        ("extras", ctypes.c_int), ("rho_r", ctypes.c_void_p), ("dvdx", ctypes.c_void_p)]
+        ("extras", ctypes.c_int), ("rho_r", ctypes.c_void_p), ("dvdx", ctypes.c_void_p),
+        ("swept_count", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p

@@ -93,6 +93,9 @@ def test_batched_step_matches_per_box(setup):
         assert rel_l2(acc[sl], ref["acc"]) <= 2e-5
         assert rel_l2(dv[sl][gas], ref["dv"][gas]) <= 2e-5
     assert counts[1] == tot_h and counts[2] == tot_g
+    # candidate evaluations bound the in-range pairs from above (tiles sweep more, lists add the self pair)
+    swept = io.swept_count.cpu().numpy()
+    assert np.all(swept >= counts) and np.all(swept > 0)
 
 
 def test_step_graph_replay(setup):
