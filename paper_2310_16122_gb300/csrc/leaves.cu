@@ -560,18 +560,29 @@ template <bool kFill>
 __device__ int leaf_images(const float *__restrict__ bbox, int64_t a, int64_t b, double L, double cut2,
                            crk_image *__restrict__ out) {
     const float *A = bbox + 6 * a, *B = bbox + 6 * b;
-    if (clearly_apart(A, B, (float)L, (float)sqrt(cut2))) return 0;
+    const float Lf = (float)L, cutf = (float)sqrt(cut2) + 1e-5f * Lf + 1e-6f;
+    if (clearly_apart(A, B, Lf, (float)sqrt(cut2))) return 0;
+    // Per axis, only the shifts whose own gap is inside the cut can give an image: the FP64
+    // sum of squares is never below one of its (non-negative) terms.  An FP32 gap with a margin
+    // above its rounding skips the FP64 work for the far shifts (FP64 is slow on this GPU).
     double g[3][3];
-    for (int q = 0; q < 3; ++q) {
-        g[q][0] = axis_gap_shift(A[q], A[3 + q], B[q], B[3 + q], -L);
-        g[q][1] = axis_gap_shift(A[q], A[3 + q], B[q], B[3 + q], 0.0);
-        g[q][2] = axis_gap_shift(A[q], A[3 + q], B[q], B[3 + q], L);
-    }
+    int keep[3][3], nk[3] = {0, 0, 0};
+    for (int q = 0; q < 3; ++q)
+        for (int k = 0; k < 3; ++k) {
+            const float sf = (float)(k - 1) * Lf;
+            const float g32 = fmaxf(fmaxf((B[q] + sf) - A[3 + q], (A[q] - B[3 + q]) - sf), 0.0f);
+            if (g32 > cutf) continue;
+            const double gd = axis_gap_shift(A[q], A[3 + q], B[q], B[3 + q], (double)(k - 1) * L);
+            if (!(__dmul_rn(gd, gd) < cut2)) continue;
+            g[q][nk[q]] = gd;
+            keep[q][nk[q]++] = k;
+        }
     int cnt = 0;
-    for (int ix = 0; ix < 3; ++ix)
-        for (int iy = 0; iy < 3; ++iy)
-            for (int iz = 0; iz < 3; ++iz) {
-                double d2 = sum_sq(g[0][ix], g[1][iy], g[2][iz]);
+    for (int jx = 0; jx < nk[0]; ++jx)
+        for (int jy = 0; jy < nk[1]; ++jy)
+            for (int jz = 0; jz < nk[2]; ++jz) {
+                const int ix = keep[0][jx], iy = keep[1][jy], iz = keep[2][jz];
+                double d2 = sum_sq(g[0][jx], g[1][jy], g[2][jz]);
                 if (d2 < cut2) {
                     if (kFill) {
                         crk_image im;

@@ -106,15 +106,23 @@ __global__ void radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, 
     if (threadIdx.x < kRadix) counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
+// One LSD pass over a tile: stable tile-local ranks by digit (per-thread
+// counts in digit-major, thread-minor order, scanned), the tile sorted by
+// digit in shared memory, then written out in order so that each digit's run
+// goes to consecutive global positions (coalesced stores).
 __global__ void radix_scatter_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
                                      uint32_t *__restrict__ kout, int32_t *__restrict__ vout, int64_t n, int shift,
                                      const int32_t *__restrict__ offsets, int64_t nb) {
-    __shared__ int32_t cnt[kRadix * kSortThreads];  // digit-major, thread-minor
+    static_assert(kRadix * kSortThreads <= 2 * kSortTile, "counters fit the staging buffer");
+    __shared__ int32_t sm[2 * kSortTile];  // first the counters, then the digit-sorted tile (keys, values)
+    int32_t *cnt = sm;                     // digit-major, thread-minor
     __shared__ int32_t wt[32];
     __shared__ int32_t goff[kRadix];
+    __shared__ int32_t dstart[kRadix];
     const int t = threadIdx.x;
     if (t < kRadix) goff[t] = offsets[(int64_t)t * nb + blockIdx.x];
-    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)t * kSortItems;  // blocked: thread-contiguous
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)t * kSortItems;  // blocked: thread-contiguous
     uint32_t key[kSortItems];
     int32_t val[kSortItems];
     int dig[kSortItems];
@@ -149,21 +157,37 @@ __global__ void radix_scatter_kernel(const uint32_t *__restrict__ kin, const int
         cnt[t * kSortItems + k] = e;
         e += loc[k];
     }
-    __shared__ int32_t dstart[kRadix];
     __syncthreads();
-    // cnt now holds prefixes in digit-major order, i.e. they include the counts
-    // of all smaller digits in this tile; dstart[d] is the tile-local start of d
+    // cnt now holds prefixes in digit-major order (they include the counts of all smaller
+    // digits in this tile); dstart[d] is the tile-local start of digit d
     if (t < kRadix) dstart[t] = cnt[t * kSortThreads];
-    __syncthreads();
+    __syncthreads();     // dstart read before thread 0 advances its counters
+    int rr[kSortItems];  // tile-local sorted position of each item
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        int d = dig[k];
+        const int d = dig[k];
+        rr[k] = -1;
         if (d < 0) continue;
-        int32_t r = cnt[d * kSortThreads + t];
-        cnt[d * kSortThreads + t] = r + 1;  // only this thread touches its own counter
-        int64_t pos = (int64_t)goff[d] + (r - dstart[d]);
-        kout[pos] = key[k];
-        vout[pos] = val[k];
+        rr[k] = cnt[d * kSortThreads + t];
+        cnt[d * kSortThreads + t] = rr[k] + 1;  // only this thread touches its own counter
+    }
+    __syncthreads();  // counters read: the buffer now takes the sorted tile
+    uint32_t *skey = reinterpret_cast<uint32_t *>(sm);
+    int32_t *sval = sm + kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+        if (rr[k] >= 0) {
+            skey[rr[k]] = key[k];
+            sval[rr[k]] = val[k];
+        }
+    __syncthreads();
+    const int m = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
+    for (int i = t; i < m; i += kSortThreads) {
+        const uint32_t kk = skey[i];
+        const int d = (int)((kk >> shift) & (kRadix - 1));
+        const int64_t pos = (int64_t)goff[d] + (i - dstart[d]);
+        kout[pos] = kk;
+        vout[pos] = sval[i];
     }
 }
 
