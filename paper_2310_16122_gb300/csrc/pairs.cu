@@ -276,9 +276,11 @@ struct GravAdjStage {
         float2 bx, by, bz, pad;
     };
     struct I2 {
-        float2 nx, ny, nz;     // -x_i, broadcast
+        float2 nx, ny, nz;         // -x_i, broadcast
         float2 mi, nbx, nby, nbz;  // m_i, -abar_i, broadcast
-        float2 gx, gy, gz, sg;  // sg accumulates g (abar_j . d); gm = -sg
+        // sum_j g w_j = m_i sum_j g abar_j - abar_i sum_j g m_j (w = m_i abar_j - m_j abar_i), so the
+        // pair loop accumulates the two sums and k d; sg accumulates g (abar_j . d) (gm = -sg)
+        float2 kx, ky, kz, s1x, s1y, s1z, s2, sg;
         int cnt;
     };
     __device__ static void put2(Rec2 *b, int c, const Rec &r) {
@@ -295,7 +297,7 @@ struct GravAdjStage {
         s.nbx = make_float2(-ri.bx, -ri.bx);
         s.nby = make_float2(-ri.by, -ri.by);
         s.nbz = make_float2(-ri.bz, -ri.bz);
-        s.gx = s.gy = s.gz = s.sg = make_float2(0.f, 0.f);
+        s.kx = s.ky = s.kz = s.s1x = s.s1y = s.s1z = s.s2 = s.sg = make_float2(0.f, 0.f);
         s.cnt = 0;
     }
     template <bool kCount>
@@ -311,30 +313,34 @@ struct GravAdjStage {
         np = __ffma2_rn(np, r2, make_float2(-p.c[2], -p.c[2]));
         np = __ffma2_rn(np, r2, make_float2(-p.c[1], -p.c[1]));
         np = __ffma2_rn(np, r2, make_float2(-p.c[0], -p.c[0]));  // -P5
-        const float c5 = -5.0f * p.c[5], c4 = -4.0f * p.c[4], c3 = -3.0f * p.c[3], c2 = -2.0f * p.c[2];
+        // -2 P5' with doubled coefficients (scaling by 2 is exact)
+        const float c5 = -10.0f * p.c[5], c4 = -8.0f * p.c[4], c3 = -6.0f * p.c[3], c2 = -4.0f * p.c[2];
         float2 ndp = __ffma2_rn(make_float2(c5, c5), r2, make_float2(c4, c4));
         ndp = __ffma2_rn(ndp, r2, make_float2(c3, c3));
         ndp = __ffma2_rn(ndp, r2, make_float2(c2, c2));
-        ndp = __ffma2_rn(ndp, r2, make_float2(-p.c[1], -p.c[1]));  // -P5'
+        ndp = __ffma2_rn(ndp, r2, make_float2(-2.0f * p.c[1], -2.0f * p.c[1]));
         const bool in0 = r2.x < p.rc2, in1 = r2.y < p.rc2;
         const float2 gv = __fadd2_rn(r3, np);
-        // g' (times 2): 2 (-1.5 r^-5 - P5')
-        const float2 dv = __fmul2_rn(make_float2(2.0f, 2.0f),
-                                     __ffma2_rn(__fmul2_rn(make_float2(-1.5f, -1.5f), r3), ri2, ndp));
+        // 2 g'(s) = 2 (-1.5 r^-5 - P5')
+        const float2 dv = __ffma2_rn(__fmul2_rn(make_float2(-3.0f, -3.0f), r3), ri2, ndp);
         const float2 g = make_float2(in0 ? gv.x : 0.0f, in1 ? gv.y : 0.0f);
         const float2 dg2 = make_float2(in0 ? dv.x : 0.0f, in1 ? dv.y : 0.0f);
-        // w = m_i abar_j - m_j abar_i
-        const float2 wx = __ffma2_rn(s.mi, rj.bx, __fmul2_rn(rj.m, s.nbx));
-        const float2 wy = __ffma2_rn(s.mi, rj.by, __fmul2_rn(rj.m, s.nby));
-        const float2 wz = __ffma2_rn(s.mi, rj.bz, __fmul2_rn(rj.m, s.nbz));
-        const float2 dw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
+        // abar_j . d and -abar_i . d, then d . w = m_i (abar_j . d) - m_j (abar_i . d)
+        const float2 dbj = __ffma2_rn(rj.bx, dx, __ffma2_rn(rj.by, dy, __fmul2_rn(rj.bz, dz)));
+        const float2 ndbi = __ffma2_rn(s.nbx, dx, __ffma2_rn(s.nby, dy, __fmul2_rn(s.nbz, dz)));
+        const float2 dw = __ffma2_rn(s.mi, dbj, __fmul2_rn(rj.m, ndbi));
         const float2 k = __fmul2_rn(dg2, dw);
-        s.gx = __ffma2_rn(g, wx, __ffma2_rn(k, dx, s.gx));
-        s.gy = __ffma2_rn(g, wy, __ffma2_rn(k, dy, s.gy));
-        s.gz = __ffma2_rn(g, wz, __ffma2_rn(k, dz, s.gz));
-        s.sg = __ffma2_rn(g, __ffma2_rn(rj.bx, dx, __ffma2_rn(rj.by, dy, __fmul2_rn(rj.bz, dz))), s.sg);
+        s.kx = __ffma2_rn(k, dx, s.kx);
+        s.ky = __ffma2_rn(k, dy, s.ky);
+        s.kz = __ffma2_rn(k, dz, s.kz);
+        s.s1x = __ffma2_rn(g, rj.bx, s.s1x);
+        s.s1y = __ffma2_rn(g, rj.by, s.s1y);
+        s.s1z = __ffma2_rn(g, rj.bz, s.s1z);
+        s.s2 = __ffma2_rn(g, rj.m, s.s2);
+        s.sg = __ffma2_rn(g, dbj, s.sg);
         if (kCount) s.cnt += (int)in0 + (int)in1;
     }
+    // partial sums of one i from one leaf-pair tile (half-warp arms): added atomically
     __device__ static void flush(const P &p, const I &s, int32_t o) {
         atomicAdd(&p.gx3[o], s.gx);
         atomicAdd(&p.gx3[p.n + o], s.gy);
@@ -346,9 +352,11 @@ struct GravAdjStage {
         cudaMemsetAsync(p.gm, 0, sizeof(float) * p.n, st);
     }
     __device__ static void finish2(const P &p, I2 &s, int32_t o) {
-        p.gx3[o] = s.gx.x + s.gx.y;
-        p.gx3[p.n + o] = s.gy.x + s.gy.y;
-        p.gx3[2 * p.n + o] = s.gz.x + s.gz.y;
+        const float mi = s.mi.x, nbx = s.nbx.x, nby = s.nby.x, nbz = s.nbz.x;
+        const float s2 = s.s2.x + s.s2.y;
+        p.gx3[o] = fmaf(mi, s.s1x.x + s.s1x.y, fmaf(nbx, s2, s.kx.x + s.kx.y));
+        p.gx3[p.n + o] = fmaf(mi, s.s1y.x + s.s1y.y, fmaf(nby, s2, s.ky.x + s.ky.y));
+        p.gx3[2 * p.n + o] = fmaf(mi, s.s1z.x + s.s1z.y, fmaf(nbz, s2, s.kz.x + s.kz.y));
         p.gm[o] = -(s.sg.x + s.sg.y);
     }
 };
