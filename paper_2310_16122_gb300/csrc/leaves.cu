@@ -163,24 +163,18 @@ __device__ __forceinline__ int32_t rank_entry_id(const RankLists &L, const AxisO
     return a == 0 ? o.S[1][r] : (a == 1 ? o.S[2][r] : o.S[0][r]);
 }
 
-__global__ void rank_of_kernel(int64_t n, AxisOrder o, int32_t *__restrict__ R0, int32_t *__restrict__ R1,
-                               int32_t *__restrict__ R2) {
+// R[S[p]] = p: the inverse of one axis order (one axis per launch, so the
+// randomly written array, n ints, stays about the size of L2)
+__global__ void rank_of_kernel(int64_t n, const int32_t *__restrict__ S, int32_t *__restrict__ R) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    R0[o.S[0][p]] = (int32_t)p;
-    R1[o.S[1][p]] = (int32_t)p;
-    R2[o.S[2][p]] = (int32_t)p;
+    if (p < n) R[S[p]] = (int32_t)p;
 }
 
-__global__ void rank_lists_kernel(int64_t n, AxisOrder o, RankListsOut L) {
+// dst[p] = R[S[p]]: one rank column of one axis list (one source array per launch, as above)
+__global__ void rank_column_kernel(int64_t n, const int32_t *__restrict__ S, const int32_t *__restrict__ R,
+                                   int32_t *__restrict__ dst) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int32_t id = o.S[a][p];
-        L.A[a][0][p] = o.R[(a + 1) % 3][id];
-        L.A[a][1][p] = o.R[(a + 2) % 3][id];
-    }
+    if (p < n) dst[p] = __ldg(R + S[p]);
 }
 
 // final member order (list 0) as particle ids
@@ -1208,10 +1202,14 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             tr.mark("axis sorts");
             const AxisOrder ord{{Lc[0], Lc[1], Lc[2]}, {R[0], R[1], R[2]}};
             if (n > 0) {
-                rank_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, ord, R[0], R[1], R[2]);
-                rank_lists_kernel<<<crk_grid(n, 256), 256, 0, st>>>(
-                    n, ord, RankListsOut{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}});
-                ctx->launches += 2;
+                for (int t = 0; t < 3; ++t) rank_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, Lc[t], R[t]);
+                // list a, column c holds the rank along axis (a + 1 + c) % 3
+                for (int t = 0; t < 3; ++t) {
+                    const int a0 = (t + 2) % 3, a1 = (t + 1) % 3;
+                    rank_column_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, Lc[a0], R[t], Ac[a0][0]);
+                    rank_column_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, Lc[a1], R[t], Ac[a1][1]);
+                }
+                ctx->launches += 9;
                 if (box_of) {
                     init_node_of_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, box_of, seg_of_box, node_of);
                     ++ctx->launches;
