@@ -25,6 +25,10 @@ constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCap = 64;                     // per-warp candidate buffer
 constexpr int kGroupImgCap = 128;            // image table of one i-leaf staged per warp in shared memory
+// capacities of the one-pass gas lists (adaptive h keeps a gas particle near 58 neighbours;
+// the largest lane list and group table seen in the clustered workloads are ~95 and ~360)
+constexpr int kGasListCapRows = 128;
+constexpr int kGasTableCap = 512;
 constexpr float kSigmaW = 0.61548156588532f;  // 495 / (256 pi), Wendland C4 3-D normalisation
 
 struct LeafView {
@@ -1665,6 +1669,13 @@ __host__ __device__ constexpr int table_cap() {
     return sizeof(typename S::Rec) <= 32 ? 320 : (sizeof(typename S::Rec) <= 48 ? 224 : 0);
 }
 
+// index rows in flight in list_kernel<S>: 8 for the short pair terms (records of at most 32
+// bytes and few registers), 4 for the long ones
+template <class S>
+__host__ __device__ constexpr int list_ahead() {
+    return (std::is_same<S, GeomStage>::value || std::is_same<S, GeomAdjStage>::value) ? 8 : 4;
+}
+
 // Exact neighbour lists, one warp per i-group.  The warp stages the group's
 // j table in shared memory (each distinct j of the group gathered once,
 // shifted into the i frame), then each lane walks its own list of table
@@ -1734,21 +1745,42 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
         typename S::I st;
         S::init(p, st, ri, a, q, lane, stage_index(lv, act ? i : g0));
         const int c = act ? gl.cnt[i] : 0;
-        // indices four rows ahead, so their loads overlap the pair arithmetic
-        int k = 0;
-        int nx0 = 0 < c ? __ldg(Lp) : 0, nx1 = 1 < c ? __ldg(Lp + 32) : 0, nx2 = 2 < c ? __ldg(Lp + 64) : 0,
-            nx3 = 3 < c ? __ldg(Lp + 96) : 0;
-        for (; k < c; k += 4) {
-            const int i0 = nx0, i1 = nx1, i2 = nx2, i3 = nx3;
-            const uint16_t *Lk = Lp + (size_t)(k + 4) * 32;
-            nx0 = k + 4 < c ? __ldg(Lk) : 0;
-            nx1 = k + 5 < c ? __ldg(Lk + 32) : 0;
-            nx2 = k + 6 < c ? __ldg(Lk + 64) : 0;
-            nx3 = k + 7 < c ? __ldg(Lk + 96) : 0;
-            S::template interact<kCount>(p, st, ri, entry(i0));
-            if (k + 1 < c) S::template interact<kCount>(p, st, ri, entry(i1));
-            if (k + 2 < c) S::template interact<kCount>(p, st, ri, entry(i2));
-            if (k + 3 < c) S::template interact<kCount>(p, st, ri, entry(i3));
+        // indices kAhead rows ahead, so their loads overlap the pair arithmetic (light pair terms
+        // need more rows in flight to cover a DRAM latency)
+        constexpr int kAhead = list_ahead<S>();
+        if constexpr (kAhead == 4) {
+            int k = 0;
+            int nx0 = 0 < c ? __ldg(Lp) : 0, nx1 = 1 < c ? __ldg(Lp + 32) : 0, nx2 = 2 < c ? __ldg(Lp + 64) : 0,
+                nx3 = 3 < c ? __ldg(Lp + 96) : 0;
+            for (; k < c; k += 4) {
+                const int i0 = nx0, i1 = nx1, i2 = nx2, i3 = nx3;
+                const uint16_t *Lk = Lp + (size_t)(k + 4) * 32;
+                nx0 = k + 4 < c ? __ldg(Lk) : 0;
+                nx1 = k + 5 < c ? __ldg(Lk + 32) : 0;
+                nx2 = k + 6 < c ? __ldg(Lk + 64) : 0;
+                nx3 = k + 7 < c ? __ldg(Lk + 96) : 0;
+                S::template interact<kCount>(p, st, ri, entry(i0));
+                if (k + 1 < c) S::template interact<kCount>(p, st, ri, entry(i1));
+                if (k + 2 < c) S::template interact<kCount>(p, st, ri, entry(i2));
+                if (k + 3 < c) S::template interact<kCount>(p, st, ri, entry(i3));
+            }
+        } else {
+            int nx[kAhead];
+#pragma unroll
+            for (int d = 0; d < kAhead; ++d) nx[d] = d < c ? __ldg(Lp + (size_t)d * 32) : 0;
+            for (int k = 0; k < c; k += kAhead) {
+                int cur[kAhead];
+                const uint16_t *Lk = Lp + (size_t)(k + kAhead) * 32;
+#pragma unroll
+                for (int d = 0; d < kAhead; ++d) {
+                    cur[d] = nx[d];
+                    nx[d] = k + kAhead + d < c ? __ldg(Lk + (size_t)d * 32) : 0;
+                }
+                S::template interact<kCount>(p, st, ri, entry(cur[0]));
+#pragma unroll
+                for (int d = 1; d < kAhead; ++d)
+                    if (k + d < c) S::template interact<kCount>(p, st, ri, entry(cur[d]));
+            }
         }
         if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
         if constexpr (S::kCons) {
@@ -1789,11 +1821,6 @@ size_t list_kernel_smem() {
     }
     return bytes;
 }
-
-// capacities of the one-pass gas lists (adaptive h keeps a gas particle near 58 neighbours;
-// the largest lane list and group table seen in the clustered workloads are ~95 and ~360)
-constexpr int kGasListCapRows = 128;
-constexpr int kGasTableCap = 512;
 
 // fixed-capacity list and table offsets: goff[g] = g capr, uoff[g] = g capt
 __global__ void strided_offsets_kernel(int64_t m, int capr, int capt, int32_t *__restrict__ goff,
