@@ -503,10 +503,42 @@ static void grad_WR(const double x[3], double W, double dWr, double A, const dou
     }
 }
 
-int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m, const double *v,
-              const double *u, const double *V, const double *rho, const double *A, const double *B, const double *gA,
-              const double *gB, const double *dvg, double L, double gamma, double alpha, double beta, double eta2,
-              const int64_t *sub, int64_t nsub, int brute, double *dvdt, double *dudt, int64_t *npairs) {
+/* ------------------------------------------------------------------------ */
+/* Compatible energy split (Sec. 5: Acceleration and Energy are separate    */
+/* kernels; Sec. 5.4: each is called twice per timestep).  Paper silent; the */
+/* reading is the compatible differencing of the thermal energy: the work a */
+/* pair's force does on the time-centred velocities v* is returned to the   */
+/* pair as heat,                                                             */
+/*   dE_ij = -f_ij.(v*_i - v*_j)   (= dE_ji, since f_ji = -f_ij),            */
+/* and is shared asymmetrically so that it drives the two particles toward  */
+/* thermal equilibrium (heating favours the colder one, cooling the hotter): */
+/*   w_ij = 1/2 (1 + sgn(dE_ij) (u_j - u_i) / (|u_j - u_i| + (u_i + u_j)/2)) */
+/*   with w_ij = 1/2 when u_i = u_j;  w_ij + w_ji = 1,  0 < w_ij < 1,       */
+/*   m_i du_i/dt = sum_j w_ij dE_ij.                                         */
+/* Summed over particles: sum_i m_i du_i = -sum_i m_i v*_i.dv_i, so a step  */
+/* v1 = v + dt dv/dt with v* = (v + v1)/2 conserves kinetic plus thermal    */
+/* energy exactly.  With u_i = u_j and v* = v it is the equal split.        */
+/*                                                                          */
+/* Signal velocity (the Courant timestep; Sec. 5.1: floating-point atomic    */
+/* max).  Paper silent; Monaghan's pair signal speed over gas j in range,   */
+/* including j = i:                                                          */
+/*   vsig_i = max_j (c_i + c_j - sig_beta min(0, v_ij.x_ij / r_ij))          */
+/*   (the j = i term is 2 c_i).                                              */
+/* ------------------------------------------------------------------------ */
+static double energy_share(double ui, double uj, double dE) {
+    if (ui == uj) return 0.5;
+    double t = (uj - ui) / (fabs(uj - ui) + 0.5 * (ui + uj));
+    return 0.5 * (1.0 + (dE > 0.0 ? t : (dE < 0.0 ? -t : 0.0)));
+}
+
+double orc_energy_share(double ui, double uj, double dE) { return energy_share(ui, uj, dE); }
+
+static int hydro_impl(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m,
+                      const double *v, const double *u, const double *V, const double *rho, const double *A,
+                      const double *B, const double *gA, const double *gB, const double *dvg, const double *vstar,
+                      double sig_beta, double L, double gamma, double alpha, double beta, double eta2,
+                      const int64_t *sub, int64_t nsub, int brute, double *dvdt, double *dudt, double *vsig,
+                      int64_t *npairs) {
     double hmax = max_h_gas(n, species, h);
     if (n < 0 || L <= 0 || !(2.0 * hmax < 0.5 * L)) return ORC_EBOX;
     uint8_t *gmask = gas_mask(n, species);
@@ -517,12 +549,13 @@ int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double
         if (species[i] != 0) {
             for (int c = 0; c < 3; ++c) dvdt[3 * i + c] = 0.0;
             dudt[i] = 0.0;
+            if (vsig) vsig[i] = 0.0;
             continue;
         }
         int64_t nc = cells_candidates(&cl, &pos[3 * i], buf);
         double Pi = (gamma - 1.0) * rho[i] * u[i];
         double ci = sqrt(gamma * (gamma - 1.0) * u[i]);
-        double F[3] = {0.0, 0.0, 0.0}, E = 0.0;
+        double F[3] = {0.0, 0.0, 0.0}, E = 0.0, S = 0.0;
         for (int64_t t = 0; t < nc; ++t) {
             int64_t j = buf[t];
             double x[3];
@@ -560,15 +593,47 @@ int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double
             double f[3];
             for (int c = 0; c < 3; ++c) f[c] = pre * (gi[c] - gj[c]);
             for (int c = 0; c < 3; ++c) F[c] += f[c];
-            E += -0.5 * (vij[0] * f[0] + vij[1] * f[1] + vij[2] * f[2]);
+            if (vstar) {
+                double dE = -((vstar[3 * i] - vstar[3 * j]) * f[0] + (vstar[3 * i + 1] - vstar[3 * j + 1]) * f[1] +
+                              (vstar[3 * i + 2] - vstar[3 * j + 2]) * f[2]);
+                E += energy_share(u[i], u[j], dE) * dE;
+            } else {
+                E += -0.5 * (vij[0] * f[0] + vij[1] * f[1] + vij[2] * f[2]);
+            }
+            if (vsig) {
+                double w = r2 > 0.0 ? (vij[0] * x[0] + vij[1] * x[1] + vij[2] * x[2]) / sqrt(r2) : 0.0;
+                double sij = ci + cj - sig_beta * (w < 0.0 ? w : 0.0);
+                if (sij > S) S = sij;
+            }
         }
         for (int c = 0; c < 3; ++c) dvdt[3 * i + c] = F[c] / m[i];
         dudt[i] = E / m[i];
+        if (vsig) vsig[i] = S;
     });
     cells_free(&cl);
     free(gmask);
     if (npairs) *npairs = pairs;
     return ORC_OK;
+}
+
+int orc_hydro(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m, const double *v,
+              const double *u, const double *V, const double *rho, const double *A, const double *B, const double *gA,
+              const double *gB, const double *dvg, double L, double gamma, double alpha, double beta, double eta2,
+              const int64_t *sub, int64_t nsub, int brute, double *dvdt, double *dudt, int64_t *npairs) {
+    return hydro_impl(n, pos, species, h, m, v, u, V, rho, A, B, gA, gB, dvg, NULL, 0.0, L, gamma, alpha, beta, eta2,
+                      sub, nsub, brute, dvdt, dudt, NULL, npairs);
+}
+
+/* the same pair force with the compatible energy split on v* (vstar, NULL:   */
+/* the equal split on v) and the signal velocity (vsig, may be NULL)          */
+int orc_hydro_compatible(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m,
+                         const double *v, const double *u, const double *V, const double *rho, const double *A,
+                         const double *B, const double *gA, const double *gB, const double *dvg, const double *vstar,
+                         double sig_beta, double L, double gamma, double alpha, double beta, double eta2,
+                         const int64_t *sub, int64_t nsub, int brute, double *dvdt, double *dudt, double *vsig,
+                         int64_t *npairs) {
+    return hydro_impl(n, pos, species, h, m, v, u, V, rho, A, B, gA, gB, dvg, vstar, sig_beta, L, gamma, alpha, beta,
+                      eta2, sub, nsub, brute, dvdt, dudt, vsig, npairs);
 }
 
 /* ------------------------------------------------------------------------ */

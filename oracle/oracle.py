@@ -63,6 +63,12 @@ def lib():
             L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
+            L.orc_hydro_compatible.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                                               _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, _i64,
+                                               ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64]
+            L.orc_energy_share.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.orc_energy_share.restype = ctypes.c_double
             L.orc_extras.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_double,
                                      _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
             L.orc_geometry_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, ctypes.c_double, _i64,
@@ -231,6 +237,91 @@ def hydro(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, sub=None, b
                            ctypes.byref(npairs)),
            "hydro")
     return dv, du, int(npairs.value)
+
+
+def hydro_compatible(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, vstar=None, sig_beta=3.0,
+                     dvg=None, sub=None, brute=False):
+    """The hydro pair force with the compatible energy split and the signal velocity.
+
+    vstar (f64[n,3]): time-centred velocities the pair work is taken on; the
+    work -f_ij.(v*_i - v*_j) is shared by the weights of energy_share (None:
+    the equal split on v).  Returns dv/dt f64[n,3], du/dt f64[n] and vsig
+    f64[n] = max_j (c_i + c_j - sig_beta min(0, v_ij.x_ij/r)) (gas only)."""
+    args = [_f64(a) for a in (V, rho, A, B, gA, gB)]
+    g = _f64(dvg).reshape(I.n, 9) if dvg is not None else None
+    w = _f64(vstar).reshape(I.n, 3) if vstar is not None else None
+    dv = np.zeros((I.n, 3))
+    du = np.zeros(I.n)
+    vsig = np.zeros(I.n)
+    npairs = ctypes.c_int64(0)
+    s, ns = _sub(sub)
+    _check(lib().orc_hydro_compatible(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d),
+                                      _p(I.v, _d), _p(I.u, _d), *[_p(a, _d) for a in args], _p(g, _d), _p(w, _d),
+                                      float(sig_beta), I.L, float(gamma), float(alpha), float(beta), float(eta2),
+                                      _p(s, _i64), ns, int(brute), _p(dv, _d), _p(du, _d), _p(vsig, _d),
+                                      ctypes.byref(npairs)),
+           "hydro_compatible")
+    return dv, du, vsig
+
+
+def energy_share(ui, uj, dE):
+    """The share w_ij of a pair's heat dE that particle i receives (compatible split)."""
+    return float(lib().orc_energy_share(float(ui), float(uj), float(dE)))
+
+
+def timestep(I: Inputs, vsig, cfl, dt_max):
+    """Courant step: dt = min(dt_max, cfl min_i h_i / vsig_i) over gas particles."""
+    gas = (I.species == 0) & (vsig > 0)
+    if not np.any(gas):
+        return float(dt_max)
+    return float(min(dt_max, cfl * np.min(I.h[gas] / vsig[gas])))
+
+
+def _wrap(x, L):
+    y = x - L * np.floor(x / L)
+    return np.where(y >= L, 0.0, y)
+
+
+def _chain(I: Inputs, limited):
+    """Geometry, corrections and (limited) Extras: the inputs of the hydro pair force."""
+    V, rho, _ = geometry(I)
+    A, B, gA, gB, _ = corrections(I, V)
+    dvg = None
+    if limited:
+        rho, dvg = extras(I, V, A, B, gA, gB)
+    return V, rho, A, B, gA, gB, dvg
+
+
+def advance(I: Inputs, gamma, alpha, beta, eta2, cfl, dt_max, sig_beta=3.0, limited=False, gravity_on=False,
+            dt=None):
+    """One two-stage kick-drift step with the compatible energy update.
+
+    Stage 1 at t^n: geometry, corrections (Extras when limited), Acceleration
+    and Energy (v* = v^n) and the Courant step dt (unless given).  Predictor:
+    v_p = v + dt/2 a, u_p = u + dt/2 du, x_p = x + dt/2 v_p.  Stage 2 at the
+    predicted state: the same chain, Acceleration a_p; kick v1 = v + dt a_p;
+    Energy on v* = (v + v1)/2 with the predicted state's forces; u1 = u + dt du;
+    drift x1 = x + dt v*.  Gas feels hydro (+ gravity), dark matter gravity
+    only; h and m stay fixed.  Returns (Inputs at t^n+1, dt)."""
+    hp = (gamma, alpha, beta, eta2)
+    V, rho, A, B, gA, gB, dvg = _chain(I, limited)
+    dv0, du0, vsig = hydro_compatible(I, V, rho, A, B, gA, gB, *hp, vstar=I.v, sig_beta=sig_beta, dvg=dvg)
+    a0 = dv0 + (gravity(I)[0] if gravity_on else 0.0)
+    if dt is None:
+        dt = timestep(I, vsig, cfl, dt_max)
+    vp = I.v + 0.5 * dt * a0
+    up = I.u + 0.5 * dt * du0
+    xp = _wrap(I.pos + 0.5 * dt * vp, I.L)
+    Ip = Inputs(xp, I.species, I.m, I.h, up, vp, I.L, I.r_cut, I.eps, I.poly)
+    V, rho, A, B, gA, gB, dvg = _chain(Ip, limited)
+    dvp, _, _ = hydro_compatible(Ip, V, rho, A, B, gA, gB, *hp, sig_beta=sig_beta, dvg=dvg)
+    ap = dvp + (gravity(Ip)[0] if gravity_on else 0.0)
+    v1 = I.v + dt * ap
+    vstar = 0.5 * (I.v + v1)
+    _, du, _ = hydro_compatible(Ip, V, rho, A, B, gA, gB, *hp, vstar=vstar, sig_beta=sig_beta, dvg=dvg)
+    u1 = I.u + dt * du
+    x1 = _wrap(I.pos + dt * vstar, I.L)
+    return Inputs(x1, I.species, I.m, I.h, u1, v1, I.L, I.r_cut, I.eps, I.poly), float(dt)
 
 
 def extras(I: Inputs, V, A, B, gA, gB, sub=None, brute=False, with_pairs=False):
