@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8, 4 ring16)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Extras-chain measurement")
+    ap.add_argument("--no-advance", action="store_true", help="skip the timestep/integrator measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants")
     ap.add_argument("--batched-boxes", type=int, default=96)
     return ap.parse_args()
@@ -407,6 +408,11 @@ def main():
             line["extras_chain"] = extras_chain(api, ctx, db, stream, peak_tflops)
         except Exception as e:  # reported, never silent
             line["extras_chain"] = {"error": repr(e)}
+    if not args.no_advance:
+        try:
+            line["advance"] = advance_step(api, ctx, db, stream, peak_tflops)
+        except Exception as e:  # reported, never silent
+            line["advance"] = {"error": repr(e)}
     if not args.no_batched:
         try:
             line["batched_vs_plain"] = batched_vs_plain(args, local, dist)
@@ -467,6 +473,66 @@ def extras_chain(api, ctx, db, stream, peak_tflops, reps=3):
             "flops_per_pair": EXTRAS_FLOPS_PER_PAIR,
             "note": "crk_step with and without the Extras chain on the same leaves (kernel-order "
                     "intermediates); extras = difference of the corrections intervals, mean of %d steps" % reps}
+
+
+ADVANCE_FLOPS_PER_PAIR = {"hydro_accel": 168, "hydro_energy": 176}
+
+
+def advance_step(api, ctx, db, stream, peak_tflops, reps=2):
+    """The timestep row: the Acceleration and Energy passes alone on one leaf build, and
+    whole two-stage kick-drift steps (crk_advance: two leaf builds, geometry, corrections,
+    Extras, Acceleration, Energy and gravity at t^n and at the predicted state) on a copy of
+    the workload, timed with CUDA events on the context stream after one warm-up step."""
+    import copy
+
+    import torch
+
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, rho, _ = api.geometry(ctx, lv, db.m)
+    A, B, gA, gB, _ = api.corrections(ctx, lv, V)
+    rr, G, _ = api.extras(ctx, lv, db.m, db.v3, V, A, B, gA, gB)
+    _, _, _, c = api.hydro_accel(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB, G, count=True)
+    torch.cuda.synchronize()
+    pairs = int(c.cpu()[0])
+    ms = {}
+    for name in ("hydro_accel", "hydro_energy"):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for k in range(reps + 1):
+            if k == 1:
+                ev[0].record(stream)
+            if name == "hydro_accel":
+                api.hydro_accel(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB, G)
+            else:
+                api.hydro_energy(ctx, lv, db.hp, db.m, db.v3, db.u, V, rr, A, B, gA, gB, db.v3, G)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        ms[name] = ev[0].elapsed_time(ev[1]) / reps
+    lv.free()
+    del V, rho, A, B, gA, gB, rr, G
+    d = copy.copy(db)
+    for k in ("x", "y", "z", "v3", "u"):
+        setattr(d, k, getattr(db, k).clone())
+    ap = api.AdvanceParams(cfl=0.25, dt_max=1.0, limited=True, gravity=True)
+    cons = torch.zeros(4, dtype=torch.float64, device=db.x.device)
+    api.advance(ctx, d, ap, conservation=cons)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        dt = api.advance(ctx, d, ap, conservation=cons)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    step_ms = ev[0].elapsed_time(ev[1]) / reps
+    tf = {k: ADVANCE_FLOPS_PER_PAIR[k] * pairs / (ms[k] * 1e-3) / 1e12 for k in ms}
+    return {"ms_per_step": round(step_ms, 3), "particles_per_s": db.n / (step_ms * 1e-3), "steps": reps,
+            "dt_last": float(dt.cpu()[0]), "pairs_per_launch": pairs,
+            "ms": {k: round(v, 4) for k, v in ms.items()},
+            "pairs_per_s": {k: pairs / (v * 1e-3) for k, v in ms.items()},
+            "tflops": tf, "frac_of_fp32_peak": {k: v / peak_tflops for k, v in tf.items()},
+            "flops_per_pair": ADVANCE_FLOPS_PER_PAIR,
+            "note": "crk_advance with Extras + limited viscosity and gravity (cfl 0.25), mean of %d steps "
+                    "after one warm-up; each step = two leaf builds + the chain twice + four hydro passes; "
+                    "pass times on one leaf build of the same workload" % reps}
 
 
 def batched_vs_plain(args, local, dist):

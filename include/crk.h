@@ -239,6 +239,81 @@ int crk_hydro_limited(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params
                       const float *B, const float *gradA, const float *gradB, const float *dvdx, float *dvdt3,
                       float *dudt, double *conservation, int64_t *pair_count);
 
+/* Acceleration pass of a timestep (Sec. 5: the momentum derivative; Sec. 5.4:
+ * Acceleration and Energy each run twice per timestep).  The pair force of
+ * crk_hydro (dvdx NULL: Monaghan viscosity) or crk_hydro_limited (dvdx given)
+ * summed into dvdt3[3n] only, plus the signal velocity (the paper prints no
+ * formula; Monaghan's pair signal speed, over gas j in range incl. j = i):
+ *   vsig_i = max_j (c_i + c_j - sig_beta min(0, v_ij.x_ij / r_ij)),
+ * folded into *vsig_h_max = max(*vsig_h_max, max_i vsig_i / h_i) by an atomic
+ * max on the FP32 bit pattern (Sec. 5.1: floating-point atomic max; a
+ * non-negative FP32 value orders like its bits).  vsig_h_max: device uint32
+ * holding FP32 bits, may be NULL; the pass only raises it, so the caller
+ * zeroes it once per step.  conservation (device double[4], may be NULL):
+ * sum m_i dv_i (3) and sum m_i v_i.dv_i.  sig_beta >= 0, else CRK_EINVAL. */
+int crk_hydro_accel(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+                    const float *u, const float *V, const float *rho, const float *A, const float *B,
+                    const float *gradA, const float *gradB, const float *dvdx, float sig_beta, float *dvdt3,
+                    uint32_t *vsig_h_max, double *conservation, int64_t *pair_count);
+
+/* Energy pass (Sec. 5: the internal-energy derivative) with the compatible
+ * split (the paper prints no formula; compatible differencing of the pair
+ * work): the pair force f_ij as in crk_hydro_accel (same v3, u, dvdx), its
+ * work on the time-centred velocities vstar3[3n] returned as heat,
+ *   dE_ij = -f_ij.(v*_i - v*_j),
+ * of which i takes the share
+ *   w_ij = 1/2 (1 + sgn(dE_ij) (u_j - u_i) / (|u_j - u_i| + (u_i + u_j)/2))
+ * (1/2 for u_i = u_j: heating favours the colder particle, cooling the
+ * hotter), m_i du_i/dt = sum_j w_ij dE_ij into dudt[n].  w_ij + w_ji = 1, so
+ * sum m_i du_i = -sum m_i v*_i.dv_i: a step with v* = (v + v1)/2 conserves
+ * kinetic plus thermal energy.  conservation (device double[4], may be
+ * NULL): sum m_i dv_i (3) and sum m_i (v*_i.dv_i + du_i) (zero up to
+ * rounding).  With equal u and vstar3 = v3 this is crk_hydro's dudt. */
+int crk_hydro_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+                     const float *u, const float *V, const float *rho, const float *A, const float *B,
+                     const float *gradA, const float *gradB, const float *dvdx, const float *vstar3, float *dudt,
+                     double *conservation, int64_t *pair_count);
+
+/* Courant timestep from the signal-velocity max of crk_hydro_accel:
+ * *dt = min(dt_max, cfl / q) with q = max_i vsig_i / h_i read from
+ * *vsig_h_max (dt_max when q = 0).  Device in, device out (no host sync);
+ * cfl > 0 and dt_max > 0, else CRK_EINVAL. */
+int crk_timestep(crk_ctx *ctx, const uint32_t *vsig_h_max, float cfl, float dt_max, float *dt);
+
+/* Parameters of crk_advance.  cfl, dt_max: the Courant step; dt_fixed > 0
+ * replaces it; sig_beta as in crk_hydro_accel; limited != 0: Extras and the
+ * limited viscosity with rho_r as the equation-of-state density (else the
+ * Monaghan viscosity on the geometry density); gravity != 0: grav_short is
+ * added to the kicks of every species (dark matter feels gravity only). */
+typedef struct {
+    float cfl;
+    float dt_max;
+    float dt_fixed;
+    float sig_beta;
+    int limited;
+    int gravity;
+} crk_advance_params;
+
+/* One two-stage kick-drift timestep with the compatible energy update (the
+ * paper prints no integrator; Sec. 5.4 calls Acceleration and Energy twice
+ * per step).  Stage 1 at t^n: leaves, geometry, corrections (Extras),
+ * Acceleration (with the signal velocity), Energy on v* = v, gravity; the
+ * Courant dt; the predictor v_p = v + dt/2 a, u_p = u + dt/2 du,
+ * x_p = x + dt/2 v_p.  Stage 2 at the predicted state: leaves, the same chain,
+ * Acceleration a_p; the kick v1 = v + dt a_p; Energy on v* = (v + v1)/2;
+ * u1 = u + dt du; the drift x1 = x + dt v* wrapped into [0, box).
+ * Device arrays in the caller's order: x, y, z, v3[3n], u updated in place;
+ * species, h, m held fixed.  dt: device float (out).  conservation (device
+ * double[4], may be NULL): the final Energy pass' balance.  n_singular
+ * (device int32, may be NULL): singular corrections over both stages.  The
+ * two leaf builds read back their sizes (host syncs); everything else stays
+ * on the context stream.  Errors as crk_build_leaves and the single calls;
+ * CRK_ESTATE when gravity is on and gp->r_cut != lp->r_cut_grav. */
+int crk_advance(crk_ctx *ctx, int64_t n, float box, float *x, float *y, float *z, const uint8_t *species,
+                const float *h, const float *m, float *v3, float *u, const crk_leaf_params *lp,
+                const crk_hydro_params *hp, const crk_grav_params *gp, const crk_advance_params *ap, float *dt,
+                double *conservation, int32_t *n_singular);
+
 /* Short-range gravity (Sec. 3.1), G = 1, all species:
  *   a_i = sum_{j != i, r < r_c} m_j (x_j - x_i) g(r^2).
  * Input m[n]; output a3[3n]. */

@@ -216,6 +216,90 @@ def hydro_limited(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A
     return dv, du, cons, c
 
 
+def hydro_accel(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A, B, gA, gB, dvdx=None,
+                sig_beta: float = 3.0, vsig_h=None, count=False):
+    """Acceleration pass: dv/dt and the signal-velocity max (vsig_h: int32[1] holding FP32 bits of
+    max_i vsig_i / h_i, raised in place; a zeroed one is made when None)."""
+    n = lv.n
+    dv = ctx.empty(3, n)
+    if vsig_h is None:
+        vsig_h = torch.zeros(1, dtype=torch.int32, device=ctx.device)
+    cons = torch.zeros(4, dtype=torch.float64, device=ctx.device)
+    c = _count(ctx, count)
+    hpc = hp.c()
+    ctx.check(N.lib().crk_hydro_accel(ctx.handle, lv.handle, ctypes.byref(hpc), _f32(m, "m", n),
+                                      _f32(v3, "v3", 3 * n), _f32(u, "u", n), _f32(V, "V", n), _f32(rho, "rho", n),
+                                      _f32(A, "A", n), _f32(B, "B", 3 * n), _f32(gA, "gradA", 3 * n),
+                                      _f32(gB, "gradB", 9 * n), _f32(dvdx, "dvdx", 9 * n) if dvdx is not None else None,
+                                      float(sig_beta), dv.data_ptr(), vsig_h.data_ptr(), cons.data_ptr(),
+                                      c.data_ptr() if c is not None else None))
+    return dv, vsig_h, cons, c
+
+
+def hydro_energy(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A, B, gA, gB, vstar3, dvdx=None,
+                 count=False):
+    """Energy pass with the compatible split of the pair work on the time-centred velocities vstar3."""
+    n = lv.n
+    du = ctx.empty(n)
+    cons = torch.zeros(4, dtype=torch.float64, device=ctx.device)
+    c = _count(ctx, count)
+    hpc = hp.c()
+    ctx.check(N.lib().crk_hydro_energy(ctx.handle, lv.handle, ctypes.byref(hpc), _f32(m, "m", n),
+                                       _f32(v3, "v3", 3 * n), _f32(u, "u", n), _f32(V, "V", n), _f32(rho, "rho", n),
+                                       _f32(A, "A", n), _f32(B, "B", 3 * n), _f32(gA, "gradA", 3 * n),
+                                       _f32(gB, "gradB", 9 * n),
+                                       _f32(dvdx, "dvdx", 9 * n) if dvdx is not None else None,
+                                       _f32(vstar3, "vstar3", 3 * n), du.data_ptr(), cons.data_ptr(),
+                                       c.data_ptr() if c is not None else None))
+    return du, cons, c
+
+
+def timestep(ctx: Context, vsig_h, cfl: float, dt_max: float):
+    """Courant step dt = min(dt_max, cfl / max_i vsig_i/h_i) as a device float[1]."""
+    dt = ctx.empty(1)
+    if vsig_h.dtype != torch.int32 or not vsig_h.is_cuda:
+        raise TypeError("vsig_h must be the CUDA int32 tensor of hydro_accel")
+    ctx.check(N.lib().crk_timestep(ctx.handle, vsig_h.data_ptr(), float(cfl), float(dt_max), dt.data_ptr()))
+    return dt
+
+
+@dataclass
+class AdvanceParams:
+    cfl: float = 0.25
+    dt_max: float = 1.0
+    dt_fixed: float = 0.0
+    sig_beta: float = 3.0
+    limited: bool = False
+    gravity: bool = False
+
+    def c(self) -> N.crk_advance_params:
+        return N.crk_advance_params(self.cfl, self.dt_max, self.dt_fixed, self.sig_beta, int(self.limited),
+                                    int(self.gravity))
+
+
+def advance(ctx: Context, db: "DeviceBox", ap: AdvanceParams, conservation=None, n_singular=None):
+    """One two-stage kick-drift step of db in place (x, y, z, v3, u); returns dt as a device float[1]."""
+    n = db.n
+    dt = ctx.empty(1)
+    if conservation is not None and (conservation.dtype != torch.float64 or conservation.numel() < 4):
+        raise TypeError("conservation must be a CUDA float64 tensor of 4")
+    if n_singular is not None and n_singular.dtype != torch.int32:
+        raise TypeError("n_singular must be a CUDA int32 tensor")
+    lpc = N.crk_leaf_params(int(db.lp.mode), int(db.lp.cells_per_side), int(db.lp.max_leaf), float(db.lp.r_cut_grav))
+    hpc, gpc, apc = db.hp.c(), db.gp.c(), ap.c()
+    if n and (db.species.dtype != torch.uint8 or not db.species.is_cuda or db.species.numel() != n):
+        raise TypeError("species must be a CUDA uint8 tensor of length n")
+    arrs = [(db.x, "x", n), (db.y, "y", n), (db.z, "z", n)]
+    ptrs = [_f32(t, nm, k) if n else None for t, nm, k in arrs]
+    ctx.check(N.lib().crk_advance(ctx.handle, n, float(db.L), *ptrs, db.species.data_ptr() if n else None,
+                                  _f32(db.h, "h", n) if n else None, _f32(db.m, "m", n) if n else None,
+                                  _f32(db.v3, "v3", 3 * n) if n else None, _f32(db.u, "u", n) if n else None,
+                                  ctypes.byref(lpc), ctypes.byref(hpc), ctypes.byref(gpc), ctypes.byref(apc),
+                                  dt.data_ptr(), conservation.data_ptr() if conservation is not None else None,
+                                  n_singular.data_ptr() if n_singular is not None else None))
+    return dt
+
+
 def grav_short(ctx: Context, lv: Leaves, gp: GravParams, m, count=False):
     n = lv.n
     a = ctx.empty(3, n)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcrk.so")
-SOURCES = ["api.cu", "scan.cu", "leaves.cu", "pairs.cu", "step.cu"]
+SOURCES = ["api.cu", "scan.cu", "leaves.cu", "pairs.cu", "step.cu", "advance.cu"]
 HEADERS = ["crk_internal.cuh", os.path.join("..", "..", "include", "crk.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -116,6 +116,7 @@ struct GravP {
 struct GravStage {
     static constexpr bool kGasOnly = false;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = true;
     using P = GravP;
     struct Rec {
         float x, y, z, m;
@@ -224,6 +225,7 @@ struct GravAdjP {
 struct GravAdjStage {
     static constexpr bool kGasOnly = false;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = true;
     using P = GravAdjP;
     struct __align__(16) Rec {
         float x, y, z, m;
@@ -378,6 +380,7 @@ struct GeomStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = true;
     using P = GeomP;
     struct Rec {
         float x, y, z, h;
@@ -427,6 +430,7 @@ struct GeomAdjStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = true;
     using P = GeomAdjP;
     struct __align__(16) Rec {
         float x, y, z, h;
@@ -487,6 +491,7 @@ struct CorrStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = true;
     using P = CorrP;
     struct __align__(16) Rec {
         float x, y, z, h;
@@ -626,6 +631,9 @@ struct HydroP {
     unsigned long long *count;
     const float *dvg;  // limited viscosity: velocity gradient [9][n], dv^a/dx^b at 3a+b
     unsigned long long *swept;  // counting runs: candidate pair evaluations, may be NULL
+    const float *vstar;         // Energy pass: time-centred velocities [3][n]
+    unsigned int *vsig_h;       // Acceleration pass: atomic max of vsig_i / h_i (FP32 bits), may be NULL
+    float sig_beta;             // Acceleration pass: vsig_ij = c_i + c_j - sig_beta min(0, v_ij.x_ij / r)
 };
 
 struct HydroRec {
@@ -641,19 +649,38 @@ struct HydroRecLim : HydroRec {
     float G[9];  // velocity gradient, dv^a/dx^b at 3a+b
     float pad2[3];
 };
+template <class Base>
+struct HydroRecVstar : Base {
+    float wx, wy, wz, u;  // time-centred velocity v* and specific internal energy
+};
 
 // kLim: the viscosity sees both velocities reconstructed linearly to the pair
 // midpoint, s = (dv) x, with the van Leer limiter
 // phi = 4 r/(1+r)^2, r = (x.s_i)/(x.s_j), written 4 a_i a_j/(a_i + a_j)^2 for
 // a_i a_j > 0 (else 0): the same value without a division by a_j alone.
-template <bool kLim>
+//
+// kPass (Sec. 5: Acceleration and Energy; Sec. 5.4: each runs twice a step):
+//   kHydroBoth    dv/dt and du/dt with the equal split of the pair work on v;
+//   kHydroAccel   dv/dt only, plus the signal velocity
+//                 vsig_i = max_j (c_i + c_j - sig_beta min(0, v_ij.x_ij / r))
+//                 (j = i gives 2 c_i), folded into one FP32 atomic max of
+//                 vsig_i / h_i (Sec. 5.1: floating-point atomic max);
+//   kHydroEnergy  du/dt with the compatible split: the pair heat
+//                 dE_ij = -f_ij.(v*_i - v*_j) goes to i with the share
+//                 w_ij = 1/2 (1 + sgn(dE) (u_j - u_i) / (|u_j - u_i| + (u_i + u_j)/2))
+//                 (1/2 when u_i = u_j), so that sum_i m_i du_i = -sum_i f_i.v*_i.
+constexpr int kHydroBoth = 0, kHydroAccel = 1, kHydroEnergy = 2;
+
+template <bool kLim, int kPass = kHydroBoth>
 struct HydroStageT {
     static constexpr bool kPair = false;
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = true;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = kPass == kHydroBoth;  // the step passes: lists and tiles only
     using P = HydroP;
-    struct __align__(16) Rec : std::conditional_t<kLim, HydroRecLim, HydroRec> {};
+    using Base = std::conditional_t<kLim, HydroRecLim, HydroRec>;
+    struct __align__(16) Rec : std::conditional_t<kPass == kHydroEnergy, HydroRecVstar<Base>, Base> {};
     struct I {
         float fx, fy, fz, e;
         int cnt;
@@ -677,6 +704,10 @@ struct HydroStageT {
         if constexpr (kLim) {
             for (int k = 0; k < 9; ++k) r.G[k] = p.dvg[k * n + o];
             r.pad2[0] = r.pad2[1] = r.pad2[2] = 0.f;
+        }
+        if constexpr (kPass == kHydroEnergy) {
+            r.wx = p.vstar[o]; r.wy = p.vstar[n + o]; r.wz = p.vstar[2 * n + o];
+            r.u = u;
         }
         return r;
     }
@@ -739,38 +770,72 @@ struct HydroStageT {
         s.fx += f[0];
         s.fy += f[1];
         s.fz += f[2];
-        s.e = fmaf(-0.5f, fmaf(vij[0], f[0], fmaf(vij[1], f[1], vij[2] * f[2])), s.e);
+        if constexpr (kPass == kHydroBoth) {
+            s.e = fmaf(-0.5f, fmaf(vij[0], f[0], fmaf(vij[1], f[1], vij[2] * f[2])), s.e);
+        } else if constexpr (kPass == kHydroAccel) {
+            // approach speed on the true velocities (the limiter shapes only the viscosity)
+            const float w = fmaf(vij[0], x[0], fmaf(vij[1], x[1], vij[2] * x[2])) * (r2 > 0.0f ? rsqrtf(r2) : 0.0f);
+            const float vs = fmaf(-p.sig_beta, fminf(w, 0.0f), ri.c + rj.c);
+            s.e = in ? fmaxf(s.e, vs) : s.e;
+        } else {
+            const float dE = -fmaf(ri.wx - rj.wx, f[0], fmaf(ri.wy - rj.wy, f[1], (ri.wz - rj.wz) * f[2]));
+            const float du = rj.u - ri.u;
+            // (u_j - u_i) / (|u_j - u_i| + (u_i + u_j)/2): the same magnitude for i and j, opposite sign
+            const float t = du != 0.0f ? __fdividef(du, fabsf(du) + 0.5f * (ri.u + rj.u)) : 0.0f;
+            const float w = 0.5f + 0.5f * (dE > 0.0f ? t : -t);
+            s.e = fmaf(w, dE, s.e);
+        }
         if (kCount) s.cnt += in;
     }
     __device__ static void finish(const P &p, I &s, const Rec &ri, int32_t o, int64_t) {
         float mi = p.m[o];
-        float dvx = s.fx / mi, dvy = s.fy / mi, dvz = s.fz / mi, du = s.e / mi;
-        p.dv3[o] = dvx;
-        p.dv3[p.n + o] = dvy;
-        p.dv3[2 * p.n + o] = dvz;
-        p.du[o] = du;
+        if constexpr (kPass != kHydroEnergy) {
+            p.dv3[o] = s.fx / mi;
+            p.dv3[p.n + o] = s.fy / mi;
+            p.dv3[2 * p.n + o] = s.fz / mi;
+        }
+        if constexpr (kPass != kHydroAccel) p.du[o] = s.e / mi;
+        if constexpr (kPass == kHydroAccel) {
+            if (p.vsig_h) {
+                // vsig / h >= 0: its FP32 bit pattern orders like the value; one atomic per
+                // converged set of lanes
+                const unsigned q = __float_as_uint(__fdividef(s.e, ri.h));
+                const unsigned mask = __activemask();
+                const unsigned qm = __reduce_max_sync(mask, q);
+                if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(p.vsig_h, qm);
+            }
+        }
     }
-    // FP64 conservation terms of one gas particle: m dv (3) and m (v.dv + du)
+    // FP64 conservation terms of one gas particle: m dv (3) and m (v.dv + du), with
+    // v = v* in the Energy pass (the compatible balance) and du = 0 in the Acceleration pass
     __device__ static void cons_terms(const P &p, const I &s, const Rec &ri, int32_t o, double c[4]) {
         double mi = (double)p.m[o];
         double dvx = (double)(s.fx / p.m[o]), dvy = (double)(s.fy / p.m[o]), dvz = (double)(s.fz / p.m[o]);
-        double du = (double)(s.e / p.m[o]);
+        double du = kPass == kHydroAccel ? 0.0 : (double)(s.e / p.m[o]);
+        double wx = ri.vx, wy = ri.vy, wz = ri.vz;
+        if constexpr (kPass == kHydroEnergy) { wx = ri.wx; wy = ri.wy; wz = ri.wz; }
         c[0] = mi * dvx;
         c[1] = mi * dvy;
         c[2] = mi * dvz;
-        c[3] = mi * ((double)ri.vx * dvx + (double)ri.vy * dvy + (double)ri.vz * dvz + du);
+        c[3] = mi * (wx * dvx + wy * dvy + wz * dvz + du);
     }
     __device__ static void finish_other(const P &p, int32_t o) {
-        p.dv3[o] = 0.f;
-        p.dv3[p.n + o] = 0.f;
-        p.dv3[2 * p.n + o] = 0.f;
-        p.du[o] = 0.f;
+        if constexpr (kPass != kHydroEnergy) {
+            p.dv3[o] = 0.f;
+            p.dv3[p.n + o] = 0.f;
+            p.dv3[2 * p.n + o] = 0.f;
+        }
+        if constexpr (kPass != kHydroAccel) p.du[o] = 0.f;
     }
 };
 
 
 using HydroStage = HydroStageT<false>;
 using HydroLimStage = HydroStageT<true>;
+template <bool kLim>
+using HydroAccelStage = HydroStageT<kLim, kHydroAccel>;
+template <bool kLim>
+using HydroEnergyStage = HydroStageT<kLim, kHydroEnergy>;
 
 // Extras (Sec. 5: the density and state gradients), over gas j including j = i:
 //   rhoR_i = sum_j m_j W^R_ij,   dv_i[3a+b] = sum_j V_j (v_j^a - v_i^a) (grad_i W^R_ij)^b
@@ -788,6 +853,7 @@ struct ExtrasStage {
     static constexpr bool kGasOnly = true;
     static constexpr bool kCons = false;
     static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = true;
     using P = ExtrasP;
     struct __align__(16) Rec {
         float x, y, z, h;
@@ -1910,42 +1976,49 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
         else
             list_kernel<S, false><<<(unsigned)grid, kThreads, list_kernel_smem<S, false>(), ctx->stream>>>(v, p, rec, gl,
                                                                                                          part);
-    } else if (ctx->variant[kernel_id] >= CRK_VARIANT_HALFWARP_SHFL && S::kPair) {
-        if constexpr (S::kPair) {
-            S::zero_outputs(p, ctx->stream);
-            const int ex = ctx->variant[kernel_id] - CRK_VARIANT_HALFWARP_SHFL;
-            const unsigned gg = (unsigned)grid;
-            if (p.count) {
-                if (ex == 0) pair_kernel_halfwarp<S, true, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                else if (ex == 1) pair_kernel_halfwarp<S, true, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                else pair_kernel_halfwarp<S, true, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-            } else {
-                if (ex == 0) pair_kernel_halfwarp<S, false, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                else if (ex == 1) pair_kernel_halfwarp<S, false, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                else pair_kernel_halfwarp<S, false, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-            }
-        }
-    } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
+    } else if constexpr (!S::kAllVariants) {  // built for lists and tiles only
         if (p.count)
-            pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
         else
-            pair_kernel_sub<S, 16, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-    } else if (ctx->variant[kernel_id] == CRK_VARIANT_RING16 && !S::kCons) {
-        if constexpr (!S::kCons) {
-            if (p.count)
-                pair_kernel_ring<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-            else
-                pair_kernel_ring<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-        }
-    } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES8) {
-        if (p.count)
-            pair_kernel_sub<S, 8, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-        else
-            pair_kernel_sub<S, 8, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-    } else if (p.count) {
-        pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
     } else {
-        pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        if (ctx->variant[kernel_id] >= CRK_VARIANT_HALFWARP_SHFL && S::kPair) {
+            if constexpr (S::kPair) {
+                S::zero_outputs(p, ctx->stream);
+                const int ex = ctx->variant[kernel_id] - CRK_VARIANT_HALFWARP_SHFL;
+                const unsigned gg = (unsigned)grid;
+                if (p.count) {
+                    if (ex == 0) pair_kernel_halfwarp<S, true, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                    else if (ex == 1) pair_kernel_halfwarp<S, true, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                    else pair_kernel_halfwarp<S, true, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                } else {
+                    if (ex == 0) pair_kernel_halfwarp<S, false, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                    else if (ex == 1) pair_kernel_halfwarp<S, false, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                    else pair_kernel_halfwarp<S, false, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                }
+            }
+        } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
+            if (p.count)
+                pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            else
+                pair_kernel_sub<S, 16, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        } else if (ctx->variant[kernel_id] == CRK_VARIANT_RING16 && !S::kCons) {
+            if constexpr (!S::kCons) {
+                if (p.count)
+                    pair_kernel_ring<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else
+                    pair_kernel_ring<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            }
+        } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES8) {
+            if (p.count)
+                pair_kernel_sub<S, 8, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            else
+                pair_kernel_sub<S, 8, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        } else if (p.count) {
+            pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        } else {
+            pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        }
     }
     if (cons) cons_reduce_kernel<<<1, 256, 0, ctx->stream>>>(part, grid, cons);
     ctx->launches += 2 + (cons ? 1 : 0);
@@ -2052,6 +2125,38 @@ int crk_hydro_limited(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params
     HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, dvdt3, dudt, conservation,
              hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count, dvdx};
     return run_stage<HydroLimStage>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+}
+
+int crk_hydro_accel(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+                    const float *u, const float *V, const float *rho, const float *A, const float *B,
+                    const float *gradA, const float *gradB, const float *dvdx, float sig_beta, float *dvdt3,
+                    uint32_t *vsig_h_max, double *conservation, int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !hp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !v3 || !u || !V || !rho || !A || !B || !gradA || !gradB || !dvdt3))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    if (!(sig_beta >= 0.0f)) return crk_fail(ctx, CRK_EINVAL, "sig_beta must be >= 0");
+    HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, dvdt3, nullptr, conservation,
+             hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count, dvdx};
+    p.vsig_h = vsig_h_max;
+    p.sig_beta = sig_beta;
+    if (dvdx) return run_stage<HydroAccelStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+    return run_stage<HydroAccelStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+}
+
+int crk_hydro_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+                     const float *u, const float *V, const float *rho, const float *A, const float *B,
+                     const float *gradA, const float *gradB, const float *dvdx, const float *vstar3, float *dudt,
+                     double *conservation, int64_t *pair_count) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !hp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !v3 || !u || !V || !rho || !A || !B || !gradA || !gradB || !vstar3 || !dudt))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, nullptr, dudt, conservation,
+             hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count, dvdx};
+    p.vstar = vstar3;
+    if (dvdx) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+    return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
 }
 
 template <bool kGas>

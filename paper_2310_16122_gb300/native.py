@@ -67,6 +67,11 @@ class crk_batch(ctypes.Structure):
                 ("box_start", ctypes.POINTER(ctypes.c_int64)), ("box_side", ctypes.POINTER(ctypes.c_float))]
 
 
+class crk_advance_params(ctypes.Structure):
+    _fields_ = [("cfl", ctypes.c_float), ("dt_max", ctypes.c_float), ("dt_fixed", ctypes.c_float),
+                ("sig_beta", ctypes.c_float), ("limited", ctypes.c_int), ("gravity", ctypes.c_int)]
+
+
 class crk_step_io(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "m", "v3", "u", "V", "rho", "A", "B", "gradA", "gradB", "dvdt3", "dudt", "conservation", "a3", "abar3",
@@ -102,6 +107,13 @@ SIGNATURES = {
     "crk_hydro": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 13,
     "crk_extras": [_P] * 12,
     "crk_hydro_limited": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 14,
+    "crk_hydro_accel": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 10 + [ctypes.c_float] + [_P] * 4,
+    "crk_hydro_energy": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 14,
+    "crk_timestep": [_P, _P, ctypes.c_float, ctypes.c_float, _P],
+    "crk_advance": [_P, _I64, ctypes.c_float] + [_P] * 8 + [ctypes.POINTER(crk_leaf_params),
+                                                           ctypes.POINTER(crk_hydro_params),
+                                                           ctypes.POINTER(crk_grav_params),
+                                                           ctypes.POINTER(crk_advance_params), _P, _P, _P],
     "grav_short": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P],
     "grav_short_adjoint": [_P, _P, ctypes.POINTER(crk_grav_params), _P, _P, _P, _P],
     "crk_geometry_adjoint": [_P, _P, _P, _P, _P, _P, _P, _P],

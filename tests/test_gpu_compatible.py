@@ -1,0 +1,207 @@
+"""Acceleration / Energy passes, the Courant timestep and the kick-drift step on GB300.
+
+The GPU passes run on the GPU's own upstream values (geometry, corrections,
+Extras); the oracle runs its own FP64 chain on the same seeded inputs.  Gates:
+dv E <= 2e-5 and du E <= 5e-5 (the hydro gates); the signal-velocity max and
+dt to 1e-5 relative (an FP32 max of FP32 pair speeds); one whole step: the
+changes of x, v and u over the step E <= 2e-4 (they are differences of FP32
+states rounded to their ulp, a few 1e-5 of the change itself, after two leaf
+builds and four hydro passes).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2310_16122_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+HP = (W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.sqrt(np.sum((a - b) ** 2) / max(np.sum(b * b), 1e-300)))
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2310_16122_gb300 import api as A
+    from paper_2310_16122_gb300.build import build_library
+
+    build_library()
+    return A
+
+
+def two_temperature(b, seed, lo=0.6, hi=1.8):
+    rng = np.random.default_rng(seed)
+    gas = b.species == 0
+    hot = rng.random(b.n) < 0.5
+    b.u = np.where(gas, np.where(hot, hi, lo), 0.0).astype(np.float32)
+    return b
+
+
+BOXES = {
+    "clustered12": lambda: two_temperature(W.clustered_box(12, 1, 61), 1),
+    "clustered24": lambda: two_temperature(W.clustered_box(24, 11, 62), 2),
+    "random777_mesh3": lambda: two_temperature(W.random_box(777, 13.0, 0.4, 63, h=2.0, leaf_mode=0, cells=3), 3),
+}
+
+
+def gpu_upstream(api, ctx, db, lv, limited):
+    V, rho, _ = api.geometry(ctx, lv, db.m)
+    A, B, gA, gB, _ = api.corrections(ctx, lv, V)
+    dvdx = None
+    if limited:
+        rho, dvdx, _ = api.extras(ctx, lv, db.m, db.v3, V, A, B, gA, gB)
+    return V, rho, A, B, gA, gB, dvdx
+
+
+def oracle_upstream(I, limited):
+    V, rho, _ = O.geometry(I)
+    A, B, gA, gB, _ = O.corrections(I, V)
+    dvg = None
+    if limited:
+        rho, dvg = O.extras(I, V, A, B, gA, gB)
+    return V, rho, A, B, gA, gB, dvg
+
+
+@pytest.mark.parametrize("name", list(BOXES))
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("limited", [False, True])
+def test_accel_and_energy_passes_match_oracle(api, name, variant, limited):
+    b = BOXES[name]()
+    ctx = api.Context(0)
+    for k in ("hydro", "extras"):
+        ctx.set_variant(k, variant)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, rho, A, B, gA, gB, dvdx = gpu_upstream(api, ctx, db, lv, limited)
+    dv, vsig_h, cons_a, _ = api.hydro_accel(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, dvdx)
+    rng = np.random.default_rng(17)
+    vstar = (np.stack([b.vx, b.vy, b.vz]) + rng.normal(0.0, 0.02, (3, b.n))).astype(np.float32)
+    vstar[:, b.species != 0] = 0.0
+    vs_t = torch.as_tensor(vstar, device=db.v3.device)
+    du, cons_e, _ = api.hydro_energy(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, vs_t, dvdx)
+    torch.cuda.synchronize()
+    g_dv, g_du = dv.cpu().numpy().T, du.cpu().numpy()
+    g_q = float(vsig_h.cpu().numpy().view(np.float32)[0])
+
+    I = O.from_box(b)
+    oV, orho, oA, oB, ogA, ogB, odvg = oracle_upstream(I, limited)
+    o_dv, _, o_vsig = O.hydro_compatible(I, oV, orho, oA, oB, ogA, ogB, *HP, vstar=I.v, dvg=odvg)
+    _, o_du, _ = O.hydro_compatible(I, oV, orho, oA, oB, ogA, ogB, *HP, vstar=vstar.T.astype(np.float64), dvg=odvg)
+    gas = b.species == 0
+    e_dv, e_du = rel_l2(g_dv[gas], o_dv[gas]), rel_l2(g_du[gas], o_du[gas])
+    o_q = float(np.max(o_vsig[gas] / I.h[gas]))
+    print(name, variant, limited, f"dv {e_dv:.2e} du {e_du:.2e} q {abs(g_q / o_q - 1):.2e}")
+    assert e_dv <= 2e-5 and e_du <= 5e-5
+    assert abs(g_q / o_q - 1.0) <= 1e-5
+    assert np.all(g_dv[~gas] == 0) and np.all(g_du[~gas] == 0)
+    # the compatible balance: sum m (v*.dv + du) = 0 up to FP32 rounding
+    c = cons_e.cpu().numpy()
+    scale = float(np.sum(np.abs(b.m[gas] * g_du[gas])) + np.sum(np.abs(b.m[gas, None] * vstar.T[gas] * g_dv[gas])))
+    assert abs(c[3]) < 1e-5 * scale
+    mom = float(np.sum(np.abs(b.m[gas, None] * g_dv[gas])))
+    assert np.max(np.abs(cons_a.cpu().numpy()[:3])) < 1e-5 * mom
+
+
+def test_accel_energy_reduce_to_hydro(api):
+    """Equal u and v* = v: the two passes give crk_hydro's dv and du."""
+    b = W.clustered_box(16, 3, 64)
+    b.u = np.where(b.species == 0, 1.2, 0.0).astype(np.float32)
+    ctx = api.Context(0)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, rho, A, B, gA, gB, _ = gpu_upstream(api, ctx, db, lv, False)
+    dv0, du0, _, _ = api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB)
+    dv1, _, _, _ = api.hydro_accel(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB)
+    du1, _, _ = api.hydro_energy(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, db.v3)
+    torch.cuda.synchronize()
+    assert rel_l2(dv1.cpu().numpy(), dv0.cpu().numpy()) <= 1e-6
+    assert rel_l2(du1.cpu().numpy(), du0.cpu().numpy()) <= 1e-6
+
+
+def test_timestep_from_signal_max(api):
+    ctx = api.Context(0)
+    q = torch.tensor([np.float32(4.0)], device="cuda").view(torch.int32).clone()
+    dt = api.timestep(ctx, q, 0.3, 10.0)
+    z = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dt0 = api.timestep(ctx, z, 0.3, 0.7)
+    dt1 = api.timestep(ctx, q, 0.3, 0.05)
+    torch.cuda.synchronize()
+    assert float(dt.cpu()) == pytest.approx(0.075, rel=1e-7)
+    assert float(dt0.cpu()) == pytest.approx(0.7)
+    assert float(dt1.cpu()) == pytest.approx(0.05)
+
+
+def _state(db):
+    return dict(x=np.stack([db.x.cpu().numpy(), db.y.cpu().numpy(), db.z.cpu().numpy()], 1).astype(np.float64),
+                v=db.v3.cpu().numpy().T.astype(np.float64), u=db.u.cpu().numpy().astype(np.float64))
+
+
+@pytest.mark.parametrize("limited,gravity", [(False, False), (True, False), (False, True)])
+def test_advance_matches_oracle_step(api, limited, gravity):
+    b = two_temperature(W.clustered_box(12, 1, 65), 4)
+    rng = np.random.default_rng(5)
+    gas = b.species == 0
+    for c in ("vx", "vy", "vz"):
+        setattr(b, c, np.where(gas, rng.normal(0.0, 0.2, b.n), 0.0).astype(np.float32))
+    ctx = api.Context(0)
+    db = api.DeviceBox(b)
+    s0 = _state(db)
+    ap = api.AdvanceParams(cfl=0.25, dt_max=1.0, limited=limited, gravity=gravity)
+    cons = torch.zeros(4, dtype=torch.float64, device="cuda")
+    nsing = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dt = api.advance(ctx, db, ap, conservation=cons, n_singular=nsing)
+    torch.cuda.synchronize()
+    s1 = _state(db)
+    g_dt = float(dt.cpu())
+    assert int(nsing.cpu()) == 0
+
+    I = O.from_box(b)
+    J, o_dt = O.advance(I, *HP, cfl=0.25, dt_max=1.0, limited=limited, gravity_on=gravity)
+    assert g_dt == pytest.approx(o_dt, rel=1e-5)
+    L = b.L
+    dx_g = s1["x"] - s0["x"]
+    dx_g -= L * np.rint(dx_g / L)
+    dx_o = J.pos - I.pos
+    dx_o -= L * np.rint(dx_o / L)
+    e = dict(dx=rel_l2(dx_g, dx_o), dv=rel_l2(s1["v"] - s0["v"], J.v - I.v), du=rel_l2(s1["u"] - s0["u"], J.u - I.u))
+    print(limited, gravity, {k: f"{v:.2e}" for k, v in e.items()}, g_dt)
+    assert e["dx"] <= 2e-4 and e["dv"] <= 2e-4 and e["du"] <= 2e-4
+    if not gravity:
+        # kinetic + thermal energy is conserved by the compatible update (up to FP32 state rounding)
+        E = lambda s: 0.5 * np.sum(b.m[:, None] * s["v"] ** 2) + np.sum(b.m * s["u"])
+        moved = abs(np.sum(b.m * (s1["u"] - s0["u"])))
+        assert abs(E(s1) - E(s0)) < 2e-3 * moved + 1e-7 * E(s0)
+        c = cons.cpu().numpy()
+        assert abs(c[3]) < 1e-4 * moved / g_dt
+
+
+def test_advance_edge_cases(api):
+    ctx = api.Context(0)
+    ap = api.AdvanceParams(cfl=0.25, dt_max=0.3)
+    # no particles: dt = dt_max, nothing else happens
+    e = W.random_box(0, 10.0, 0.5, 66)
+    db = api.DeviceBox(e)
+    dt = api.advance(ctx, db, ap)
+    # dark matter only, gravity on: dt = dt_max (no signal speed), particles move under gravity alone
+    b = W.random_box(300, 12.0, 0.0, 67)
+    dbd = api.DeviceBox(b)
+    ap_g = api.AdvanceParams(cfl=0.25, dt_max=0.05, gravity=True)
+    dtd = api.advance(ctx, dbd, ap_g)
+    torch.cuda.synchronize()
+    assert float(dt.cpu()) == pytest.approx(0.3)
+    assert float(dtd.cpu()) == pytest.approx(0.05)
+    I = O.from_box(b)
+    J, o_dt = O.advance(I, *HP, cfl=0.25, dt_max=0.05, gravity_on=True)
+    v1 = dbd.v3.cpu().numpy().T
+    assert rel_l2(v1 - I.v, J.v - I.v) <= 1e-4
+    # bad parameters fail loudly
+    from paper_2310_16122_gb300 import native as N
+    with pytest.raises(N.CrkError):
+        api.advance(ctx, dbd, api.AdvanceParams(cfl=0.0))
