@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Extras-chain measurement")
     ap.add_argument("--no-advance", action="store_true", help="skip the timestep/integrator measurement")
+    ap.add_argument("--advance-only", action="store_true",
+                    help="run only the timestep/integrator measurement (--steps steps) and print it")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants")
     ap.add_argument("--batched-boxes", type=int, default=96)
     return ap.parse_args()
@@ -233,6 +235,17 @@ def main():
     db = api.DeviceBox(box, device=f"cuda:{local}")
     gas = (db.species == 0).float()
     stream = ctx.stream
+    if args.advance_only:
+        # the timestep row alone (for kernel launch lists of crk_advance); not the headline line
+        try:
+            f_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0))
+        except Exception:
+            f_max = 2070.0
+        peak = torch.cuda.get_device_properties(local).multi_processor_count * 128 * 2 * f_max * 1e6 / 1e12
+        if rank == 0:
+            print(json.dumps({"workload": box.name, "n": box.n, "advance": advance_step(api, ctx, db, stream, peak,
+                                                                                         reps=args.steps)}))
+        return
 
     # the step's outputs: accelerations, energy rates and both adjoints; the intermediates
     # (V, rho, A, B, dA, dB) stay in the library's kernel order
@@ -531,8 +544,9 @@ def advance_step(api, ctx, db, stream, peak_tflops, reps=2):
             "tflops": tf, "frac_of_fp32_peak": {k: v / peak_tflops for k, v in tf.items()},
             "flops_per_pair": ADVANCE_FLOPS_PER_PAIR,
             "note": "crk_advance with Extras + limited viscosity and gravity (cfl 0.25), mean of %d steps "
-                    "after one warm-up; each step = two leaf builds + the chain twice + four hydro passes; "
-                    "pass times on one leaf build of the same workload" % reps}
+                    "after one warm-up; each step = two leaf builds + the chain twice + four hydro passes, "
+                    "in the kernel orders; ms/pairs_per_s/tflops are the passes as single C-ABI calls on "
+                    "one leaf build (caller-order inputs: gathers and scatters included)" % reps}
 
 
 def batched_vs_plain(args, local, dist):

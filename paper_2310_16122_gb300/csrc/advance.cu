@@ -28,11 +28,25 @@ __global__ void timestep_kernel(const uint32_t *__restrict__ vsig_h_max, float c
     *dt = d;
 }
 
+// The accelerations and du come from the stage in the library's kernel orders:
+// hydro dv and du in the gas order (position kinv[o] for particle o), gravity
+// in the gravity order (kinv_g[o]).
+struct StageOut {
+    const float *dv, *ag, *du;
+    const int32_t *kinv, *kinv_g;
+    int64_t n;
+    __device__ float acc(int c, int64_t o) const {
+        float a = dv[c * n + kinv[o]];
+        if (ag) a += ag[c * n + kinv_g[o]];
+        return a;
+    }
+    __device__ float dudt(int64_t o) const { return du[kinv[o]]; }
+};
+
 // predictor: v_p = v + dt/2 a, u_p = u + dt/2 du, x_p = x + dt/2 v_p (a = hydro + gravity)
 __global__ void predict_kernel(int64_t n, float L, const float *__restrict__ dtp, const float *__restrict__ x,
                                const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ v3,
-                               const float *__restrict__ u, const float *__restrict__ a3,
-                               const float *__restrict__ ag3, const float *__restrict__ du, float *__restrict__ xp,
+                               const float *__restrict__ u, StageOut so, float *__restrict__ xp,
                                float *__restrict__ yp, float *__restrict__ zp, float *__restrict__ vp3,
                                float *__restrict__ up) {
     const float h = 0.5f * *dtp;
@@ -41,40 +55,39 @@ __global__ void predict_kernel(int64_t n, float L, const float *__restrict__ dtp
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float a = a3[c * n + i];
-            if (ag3) a += ag3[c * n + i];
-            const float v = fmaf(h, a, v3[c * n + i]);
+            const float v = fmaf(h, so.acc(c, i), v3[c * n + i]);
             vp3[c * n + i] = v;
             posp[c][i] = wrap_add(pos[c][i], h * v, L);
         }
-        up[i] = fmaf(h, du[i], u[i]);
+        up[i] = fmaf(h, so.dudt(i), u[i]);
     }
 }
 
 // kick: v1 = v + dt a_p (in place), v* = (v + v1)/2
-__global__ void kick_kernel(int64_t n, const float *__restrict__ dtp, float *__restrict__ v3,
-                            const float *__restrict__ a3, const float *__restrict__ ag3, float *__restrict__ vs3) {
+__global__ void kick_kernel(int64_t n, const float *__restrict__ dtp, float *__restrict__ v3, StageOut so,
+                            float *__restrict__ vs3) {
     const float dt = *dtp;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x) {
-        float a = a3[i];
-        if (ag3) a += ag3[i];
-        const float v0 = v3[i];
-        const float v1 = fmaf(dt, a, v0);
-        v3[i] = v1;
-        vs3[i] = 0.5f * (v0 + v1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v0 = v3[c * n + i];
+            const float v1 = fmaf(dt, so.acc(c, i), v0);
+            v3[c * n + i] = v1;
+            vs3[c * n + i] = 0.5f * (v0 + v1);
+        }
     }
 }
 
 // final update: u1 = u + dt du, x1 = x + dt v* (wrapped)
 __global__ void drift_kernel(int64_t n, float L, const float *__restrict__ dtp, float *__restrict__ x,
                              float *__restrict__ y, float *__restrict__ z, const float *__restrict__ vs3,
-                             float *__restrict__ u, const float *__restrict__ du) {
+                             float *__restrict__ u, StageOut so) {
     const float dt = *dtp;
     float *pos[3] = {x, y, z};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) pos[c][i] = wrap_add(pos[c][i], dt * vs3[c * n + i], L);
-        u[i] = fmaf(dt, du[i], u[i]);
+        u[i] = fmaf(dt, so.dudt(i), u[i]);
     }
 }
 
@@ -89,36 +102,16 @@ int elementwise_grid(const crk_ctx *ctx, int64_t n) {
     return g < cap ? g : cap;
 }
 
-// per-particle state of one step, one float column of n each
-enum Col {
-    kV, kRho, kA, kB, kGA = kB + 3, kGB = kGA + 3, kRhoR = kGB + 9, kDvdx, kAcc = kDvdx + 9, kAccG = kAcc + 3,
-    kDu = kAccG + 3, kXp = kDu + 1, kVp = kXp + 3, kUp = kVp + 3, kVs = kUp + 1, kCols = kVs + 3
+// the stage's kernel-order columns, then the caller-order predicted state and v*
+enum Col : int {
+    kXp = crk_stage_cols::count, kVp = kXp + 3, kUp = kVp + 3, kVs = kUp + 1, kCols = kVs + 3
 };
 
-struct Chain {
-    const crk_leaves *lv;
-    const float *v3, *u;  // the state the forces see
-    float *col;           // state columns
-    int64_t n;
-    float *c(int k) const { return col + (size_t)k * n; }
-};
-
-// geometry, corrections and (limited) Extras of one stage; returns the EOS density column
-int forces_upstream(crk_ctx *ctx, const Chain &s, const float *m, int limited, int32_t *n_singular,
-                    const float **rho_eos, const float **dvdx) {
-    int rc;
-    if ((rc = crk_geometry(ctx, s.lv, m, s.c(kV), s.c(kRho), nullptr))) return rc;
-    if ((rc = crk_corrections(ctx, s.lv, s.c(kV), s.c(kA), s.c(kB), s.c(kGA), s.c(kGB), n_singular))) return rc;
-    *rho_eos = s.c(kRho);
-    *dvdx = nullptr;
-    if (limited) {
-        if ((rc = crk_extras(ctx, s.lv, m, s.v3, s.c(kV), s.c(kA), s.c(kB), s.c(kGA), s.c(kGB), s.c(kRhoR),
-                             s.c(kDvdx), nullptr)))
-            return rc;
-        *rho_eos = s.c(kRhoR);
-        *dvdx = s.c(kDvdx);
-    }
-    return CRK_OK;
+StageOut stage_out(const crk_leaves *lv, const float *w, int gravity) {
+    namespace K = crk_stage_cols;
+    const int64_t n = lv->n;
+    return StageOut{w + (size_t)K::dv * n, gravity ? w + (size_t)K::ag * n : nullptr, w + (size_t)K::du * n,
+                    lv->kinv, lv->kinv_g, n};
 }
 
 }  // namespace
@@ -171,49 +164,38 @@ int crk_advance(crk_ctx *ctx, int64_t n, float box, float *x, float *y, float *z
     {
         crk_particles pt{x, y, z, species, n, box};
         if ((rc = crk_build_leaves(ctx, &pt, h, lp, &lv))) return rc;
-        Chain s{lv, v3, u, col, n};
-        const float *rho_eos, *dvdx;
-        rc = forces_upstream(ctx, s, m, ap->limited, nsing, &rho_eos, &dvdx);
-        if (!rc)
-            rc = crk_hydro_accel(ctx, lv, hp, m, v3, u, C(kV), rho_eos, C(kA), C(kB), C(kGA), C(kGB), dvdx,
-                                 ap->sig_beta, C(kAcc), vsig, nullptr, nullptr);
-        if (!rc)
-            rc = crk_hydro_energy(ctx, lv, hp, m, v3, u, C(kV), rho_eos, C(kA), C(kB), C(kGA), C(kGB), dvdx, v3,
-                                  C(kDu), nullptr, nullptr);
-        if (!rc && ap->gravity) rc = grav_short(ctx, lv, gp, m, C(kAccG), nullptr);
+        rc = crk_stage_forces(ctx, lv, gp, hp, ap->limited, ap->gravity, ap->sig_beta, m, v3, u, vsig, nsing, col);
+        if (!rc) rc = crk_stage_energy(ctx, lv, hp, ap->limited, nullptr, col, nullptr);
+        if (!rc) {
+            timestep_kernel<<<1, 32, 0, ctx->stream>>>(vsig, ap->cfl, ap->dt_max, ap->dt_fixed, dt);
+            predict_kernel<<<grid, 256, 0, ctx->stream>>>(n, box, dt, x, y, z, v3, u, stage_out(lv, col, ap->gravity),
+                                                          C(kXp), C(kXp + 1), C(kXp + 2), C(kVp), C(kUp));
+            ctx->launches += 2;
+            rc = crk_check_cuda(ctx, cudaGetLastError(), "predictor");
+        }
         crk_leaves_free(ctx, lv);
         if (rc) return rc;
     }
-    timestep_kernel<<<1, 32, 0, ctx->stream>>>(vsig, ap->cfl, ap->dt_max, ap->dt_fixed, dt);
-    predict_kernel<<<grid, 256, 0, ctx->stream>>>(n, box, dt, x, y, z, v3, u, C(kAcc), ap->gravity ? C(kAccG) : nullptr,
-                                                  C(kDu), C(kXp), C(kXp + 1), C(kXp + 2), C(kVp), C(kUp));
-    ctx->launches += 2;
-    CRK_LAUNCH_CHECK(ctx, "predictor");
     // ---- stage 2 at the predicted state: Acceleration, kick, Energy on v* = (v + v1)/2, drift
     {
         crk_particles pt{C(kXp), C(kXp + 1), C(kXp + 2), species, n, box};
         if ((rc = crk_build_leaves(ctx, &pt, h, lp, &lv))) return rc;
-        Chain s{lv, C(kVp), C(kUp), col, n};
-        const float *rho_eos, *dvdx;
-        rc = forces_upstream(ctx, s, m, ap->limited, nsing + 1, &rho_eos, &dvdx);
-        if (!rc)
-            rc = crk_hydro_accel(ctx, lv, hp, m, C(kVp), C(kUp), C(kV), rho_eos, C(kA), C(kB), C(kGA), C(kGB), dvdx,
-                                 ap->sig_beta, C(kAcc), nullptr, nullptr, nullptr);
-        if (!rc && ap->gravity) rc = grav_short(ctx, lv, gp, m, C(kAccG), nullptr);
+        rc = crk_stage_forces(ctx, lv, gp, hp, ap->limited, ap->gravity, ap->sig_beta, m, C(kVp), C(kUp), nullptr,
+                              nsing + 1, col);
         if (!rc) {
-            kick_kernel<<<grid, 256, 0, ctx->stream>>>(n, dt, v3, C(kAcc), ap->gravity ? C(kAccG) : nullptr, C(kVs));
+            kick_kernel<<<grid, 256, 0, ctx->stream>>>(n, dt, v3, stage_out(lv, col, ap->gravity), C(kVs));
             ++ctx->launches;
             rc = crk_check_cuda(ctx, cudaGetLastError(), "kick");
         }
-        if (!rc)
-            rc = crk_hydro_energy(ctx, lv, hp, m, C(kVp), C(kUp), C(kV), rho_eos, C(kA), C(kB), C(kGA), C(kGB), dvdx,
-                                  C(kVs), C(kDu), conservation, nullptr);
+        if (!rc) rc = crk_stage_energy(ctx, lv, hp, ap->limited, C(kVs), col, conservation);
+        if (!rc) {
+            drift_kernel<<<grid, 256, 0, ctx->stream>>>(n, box, dt, x, y, z, C(kVs), u, stage_out(lv, col, ap->gravity));
+            ++ctx->launches;
+            rc = crk_check_cuda(ctx, cudaGetLastError(), "drift");
+        }
         crk_leaves_free(ctx, lv);
         if (rc) return rc;
     }
-    drift_kernel<<<grid, 256, 0, ctx->stream>>>(n, box, dt, x, y, z, C(kVs), u, C(kDu));
-    ++ctx->launches;
-    CRK_LAUNCH_CHECK(ctx, "drift");
     if (n_singular) {
         sum_counts_kernel<<<1, 32, 0, ctx->stream>>>(nsing, n_singular);
         ++ctx->launches;

@@ -127,6 +127,24 @@ void crk_rcb_shape_free(crk_ctx *ctx);
 int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas);
 int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
                    const crk_step_io *io);
+// One stage of crk_advance in the library's kernel orders.  The work array
+// holds crk_stage_cols::count columns of n floats: the state permuted into
+// the gas kernel order (m, v, u), m in the gravity order, the chain's
+// intermediates, the accelerations dv (gas order) and ag (gravity order), du
+// and v* (gas order).
+namespace crk_stage_cols {
+enum : int {
+    m = 0, v = 1, u = 4, mg = 5, V = 6, rho = 7, A = 8, B = 9, gA = 12, gB = 15, rhoR = 24, dvdx = 25, dv = 34,
+    du = 37, ag = 38, vs = 41, count = 44
+};
+}
+// geometry, corrections, (Extras), Acceleration with the signal-velocity max and (gravity)
+int crk_stage_forces(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+                     int limited, int gravity, float sig_beta, const float *m, const float *v3, const float *u,
+                     uint32_t *vsig_h, int32_t *n_singular, float *work);
+// Energy on v* (caller order; NULL: v* = v) with the intermediates of the last crk_stage_forces
+int crk_stage_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, int limited,
+                     const float *vstar3, float *work, double *conservation);
 // records event k (0..7) of the current profiled step, if profiling is on
 void crk_step_mark(crk_ctx *ctx, int k);
 

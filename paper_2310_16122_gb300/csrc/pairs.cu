@@ -2397,6 +2397,87 @@ __global__ void cotangent_kernel(int64_t n, const float *__restrict__ a_g, const
 
 }  // namespace
 
+int crk_stage_forces(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
+                     int limited, int gravity, float sig_beta, const float *m, const float *v3, const float *u,
+                     uint32_t *vsig_h, int32_t *n_singular, float *w) {
+    namespace K = crk_stage_cols;
+    const int64_t n = lv->n;
+    if (n == 0) return CRK_OK;
+    auto C = [&](int k) { return w + (size_t)k * n; };
+    cudaStream_t st = ctx->stream;
+    const int g = crk_grid(n, 256);
+    auto col = [&](float *dst, const float *src, const int32_t *perm) {
+        permute_col_kernel<<<g, 256, 0, st>>>(n, perm, src, dst);
+        ++ctx->launches;
+    };
+    col(C(K::m), m, lv->kperm);
+    for (int c = 0; c < 3; ++c) col(C(K::v) + (size_t)c * n, v3 + (size_t)c * n, lv->kperm);
+    col(C(K::u), u, lv->kperm);
+    if (gravity) col(C(K::mg), m, lv->kperm_g);
+    CRK_LAUNCH_CHECK(ctx, "stage inputs");
+    int rc;
+    {
+        GeomP p{C(K::m), C(K::V), C(K::rho), n, nullptr, nullptr};
+        if ((rc = run_stage<GeomStage>(ctx, lv, p, true, CRK_K_GEOMETRY, nullptr, true))) return rc;
+    }
+    {
+        if (n_singular) CRK_CUDA(ctx, cudaMemsetAsync(n_singular, 0, sizeof(int32_t), st));
+        CorrP p{C(K::V), C(K::A), C(K::B), C(K::gA), C(K::gB), n_singular, n, nullptr};
+        if ((rc = run_stage<CorrStage>(ctx, lv, p, true, CRK_K_CORRECTIONS, nullptr, true))) return rc;
+    }
+    if (limited) {
+        ExtrasP p{C(K::m), C(K::v), C(K::V), C(K::A), C(K::B), C(K::gA), C(K::gB), C(K::rhoR), C(K::dvdx), n, nullptr};
+        if ((rc = run_stage<ExtrasStage>(ctx, lv, p, true, CRK_K_EXTRAS, nullptr, true))) return rc;
+    }
+    {
+        HydroP p{C(K::m), C(K::v), C(K::u), C(K::V), C(limited ? K::rhoR : K::rho), C(K::A), C(K::B), C(K::gA),
+                 C(K::gB), C(K::dv), nullptr, nullptr, hp->gamma, hp->alpha, hp->beta, hp->eta2, n, nullptr,
+                 limited ? C(K::dvdx) : nullptr};
+        p.vsig_h = vsig_h;
+        p.sig_beta = sig_beta;
+        if (limited) rc = run_stage<HydroAccelStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, nullptr, true);
+        else rc = run_stage<HydroAccelStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, nullptr, true);
+        if (rc) return rc;
+    }
+    if (gravity) {
+        if (gp->r_cut != lv->r_cut_grav) return crk_fail(ctx, CRK_ESTATE, "r_cut differs from the leaves' r_cut_grav");
+        GravP p{};
+        p.m = C(K::mg);
+        p.a3 = C(K::ag);
+        p.rc2 = gp->r_cut * gp->r_cut;
+        p.eps2 = gp->eps * gp->eps;
+        for (int k = 0; k < 6; ++k) p.c[k] = gp->poly[k];
+        p.n = n;
+        if ((rc = run_stage<GravStage>(ctx, lv, p, false, CRK_K_GRAVITY, nullptr, true))) return rc;
+    }
+    return CRK_OK;
+}
+
+int crk_stage_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, int limited,
+                     const float *vstar3, float *w, double *conservation) {
+    namespace K = crk_stage_cols;
+    const int64_t n = lv->n;
+    if (n == 0) return CRK_OK;
+    auto C = [&](int k) { return w + (size_t)k * n; };
+    const float *vs = C(K::v);
+    if (vstar3) {
+        const int g = crk_grid(n, 256);
+        for (int c = 0; c < 3; ++c) {
+            permute_col_kernel<<<g, 256, 0, ctx->stream>>>(n, lv->kperm, vstar3 + (size_t)c * n,
+                                                           C(K::vs) + (size_t)c * n);
+            ++ctx->launches;
+        }
+        CRK_LAUNCH_CHECK(ctx, "stage v*");
+        vs = C(K::vs);
+    }
+    HydroP p{C(K::m), C(K::v), C(K::u), C(K::V), C(limited ? K::rhoR : K::rho), C(K::A), C(K::B), C(K::gA),
+             C(K::gB), nullptr, C(K::du), conservation, hp->gamma, hp->alpha, hp->beta, hp->eta2, n, nullptr,
+             limited ? C(K::dvdx) : nullptr};
+    p.vstar = vs;
+    if (limited) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation, true);
+    return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation, true);
+}
+
 int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
                    const crk_step_io *io) {
     const int64_t n = lv->n;
