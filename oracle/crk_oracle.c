@@ -970,3 +970,372 @@ int orc_mark_neighbours(int64_t n, const double *pos, const uint8_t *species, co
     free(gm);
     return ORC_OK;
 }
+
+/* ======================================================================== */
+/* Reverse mode of Corrections and of the hydro pair force (not in the     */
+/* paper; the adjoints extend the gravity and geometry ones to the rest of  */
+/* the forward chain).  Hand-written FP64 reverse mode of the forward       */
+/* formulas above, pinned by central differences in tests/.                 */
+/* ======================================================================== */
+
+/* W, (dW/dr)/r and (d[(dW/dr)/r]/dr)/r of the Wendland C4 kernel:          */
+/*   ddWr = 495/(256 pi h^7) 35 (1 - q/2)^4, so that grad (dWr) = ddWr x.   */
+static void wendland2(double r, double h, double *W, double *dWr, double *ddWr) {
+    double q = r / h;
+    if (q >= 2.0) { *W = 0.0; *dWr = 0.0; *ddWr = 0.0; return; }
+    wendland(r, h, W, dWr);
+    double t = 1.0 - 0.5 * q;
+    double h7 = h * h * h * h * h * h * h;
+    *ddWr = 495.0 / (256.0 * PI) / h7 * 35.0 * t * t * t * t;
+}
+
+void orc_wendland2(int64_t n, const double *r, const double *h, double *W, double *dWr, double *ddWr) {
+    for (int64_t i = 0; i < n; ++i) wendland2(r[i], h[i], &W[i], &dWr[i], &ddWr[i]);
+}
+
+/* moments of particle i (the sums of orc_corrections) */
+typedef struct {
+    double m0, m1[3], m2[3][3], dm0[3], dm1[3][3], dm2[3][3][3]; /* dm1[g][a], dm2[g][a][b] */
+} Moments;
+
+/* Cotangents of the moments from those of A, B, gA, gB (closed-form        */
+/* reverse of orc_corrections' per-particle step; M = m2 is symmetric, so   */
+/* M^-1 is too).                                                             */
+static int moments_bar(const Moments *mo, double Abar, const double *Bbar_in, const double *gAbar,
+                       const double *gBbar, Moments *mb) {
+    memset(mb, 0, sizeof(*mb));
+    double det = det3(mo->m2);
+    double tr = mo->m2[0][0] + mo->m2[1][1] + mo->m2[2][2];
+    if (!(det > 1e-12 * tr * tr * tr)) return 1;
+    double Mi[3][3];
+    inv3(mo->m2, det, Mi);
+    double B[3], Bbar[3], Mibar[3][3] = {{0}};
+    for (int a = 0; a < 3; ++a) B[a] = -(Mi[a][0] * mo->m1[0] + Mi[a][1] * mo->m1[1] + Mi[a][2] * mo->m1[2]);
+    double A = 1.0 / (mo->m0 + B[0] * mo->m1[0] + B[1] * mo->m1[1] + B[2] * mo->m1[2]);
+    for (int a = 0; a < 3; ++a) Bbar[a] = Bbar_in[a];
+    double Atot = Abar;
+    for (int g = 0; g < 3; ++g) {
+        /* gB[g][a] = -(Mi t_g)_a with t_g = dm1[g] + dm2[g] B */
+        double t[3], tb[3], K = mo->dm0[g];
+        for (int a = 0; a < 3; ++a) {
+            t[a] = mo->dm1[g][a];
+            for (int b = 0; b < 3; ++b) t[a] += mo->dm2[g][a][b] * B[b];
+            K += 2.0 * B[a] * mo->dm1[g][a];
+            for (int b = 0; b < 3; ++b) K += B[a] * mo->dm2[g][a][b] * B[b];
+        }
+        const double *gb = &gBbar[3 * g];
+        for (int a = 0; a < 3; ++a) tb[a] = -(Mi[a][0] * gb[0] + Mi[a][1] * gb[1] + Mi[a][2] * gb[2]);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Mibar[a][b] += -gb[a] * t[b];
+        for (int a = 0; a < 3; ++a) {
+            mb->dm1[g][a] += tb[a];
+            for (int b = 0; b < 3; ++b) {
+                mb->dm2[g][a][b] += tb[a] * B[b];
+                Bbar[b] += tb[a] * mo->dm2[g][a][b];
+            }
+        }
+        /* gA[g] = -A^2 K_g, K_g = dm0[g] + 2 B.dm1[g] + B^T dm2[g] B */
+        double Kb = -A * A * gAbar[g];
+        Atot += -2.0 * A * K * gAbar[g];
+        mb->dm0[g] += Kb;
+        for (int a = 0; a < 3; ++a) {
+            mb->dm1[g][a] += 2.0 * B[a] * Kb;
+            Bbar[a] += 2.0 * mo->dm1[g][a] * Kb;
+            for (int b = 0; b < 3; ++b) {
+                Bbar[a] += (mo->dm2[g][a][b] + mo->dm2[g][b][a]) * B[b] * Kb;
+                mb->dm2[g][a][b] += B[a] * B[b] * Kb;
+            }
+        }
+    }
+    /* A = 1/(m0 + B.m1) */
+    double denb = -A * A * Atot;
+    mb->m0 += denb;
+    for (int a = 0; a < 3; ++a) {
+        Bbar[a] += mo->m1[a] * denb;
+        mb->m1[a] += B[a] * denb;
+    }
+    /* B = -Mi m1 */
+    for (int a = 0; a < 3; ++a) {
+        mb->m1[a] += -(Mi[0][a] * Bbar[0] + Mi[1][a] * Bbar[1] + Mi[2][a] * Bbar[2]);
+        for (int b = 0; b < 3; ++b) Mibar[a][b] += -Bbar[a] * mo->m1[b];
+    }
+    /* Mi = M^-1: Mbar = -Mi^T Mibar Mi^T */
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < 3; ++c)
+                for (int d = 0; d < 3; ++d) s += Mi[c][a] * Mibar[c][d] * Mi[b][d];
+            mb->m2[a][b] = -s;
+        }
+    return 0;
+}
+
+/* The moment terms of one pair weighted by moment cotangents mb (the V_j   */
+/* factor left out): T(x) = S0(x) W + S1(x) dWr, with                        */
+/*   S0 = m0b + m1b.x + x^T m2b x + sum_a dm1b[a][a]                         */
+/*        + sum_ab dm2b[a][a][b] x_b + sum_ab dm2b[b][a][b] x_a               */
+/*   S1 = dm0b.x + sum_ga dm1b[g][a] x_a x_g + sum_gab dm2b[g][a][b] x_a x_b x_g */
+/* and its gradient in x (grad W = dWr x, grad dWr = ddWr x).               */
+static double moment_term(const Moments *mb, const double x[3], double W, double dWr, double ddWr, double grad[3]) {
+    double S0 = mb->m0, S1 = 0.0, gS0[3] = {0, 0, 0}, gS1[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        S0 += mb->m1[a] * x[a] + mb->dm1[a][a];
+        gS0[a] += mb->m1[a];
+        S1 += mb->dm0[a] * x[a];
+        gS1[a] += mb->dm0[a];
+        for (int b = 0; b < 3; ++b) {
+            S0 += mb->m2[a][b] * x[a] * x[b];
+            gS0[a] += mb->m2[a][b] * x[b];
+            gS0[b] += mb->m2[a][b] * x[a];
+            S0 += mb->dm2[a][a][b] * x[b] + mb->dm2[b][a][b] * x[a];
+            gS0[b] += mb->dm2[a][a][b];
+            gS0[a] += mb->dm2[b][a][b];
+            /* dm1b[g = a][a' = b] x_b x_a */
+            S1 += mb->dm1[a][b] * x[b] * x[a];
+            gS1[b] += mb->dm1[a][b] * x[a];
+            gS1[a] += mb->dm1[a][b] * x[b];
+            for (int c = 0; c < 3; ++c) {
+                /* dm2b[g = a][b][c] x_b x_c x_a */
+                double w = mb->dm2[a][b][c];
+                S1 += w * x[b] * x[c] * x[a];
+                gS1[a] += w * x[b] * x[c];
+                gS1[b] += w * x[a] * x[c];
+                gS1[c] += w * x[a] * x[b];
+            }
+        }
+    }
+    for (int p = 0; p < 3; ++p) grad[p] = gS0[p] * W + S0 * dWr * x[p] + gS1[p] * dWr + S1 * ddWr * x[p];
+    return S0 * W + S1 * dWr;
+}
+
+/* Reverse mode of orc_corrections for the cotangents Abar[n], Bbar[3n],     */
+/* gAbar[3n], gBbar[9n] (layouts of its outputs): the gradient of            */
+/*   L = sum_i Abar_i A_i + Bbar_i.B_i + gAbar_i.gA_i + gBbar_i:gB_i          */
+/* in the positions (xbar[3n]) and volumes (Vbar[n]).  Pair (i, j) enters i's */
+/* moments as V_j t(x_ij), so                                                 */
+/*   xbar_k = sum_j V_j grad T_k(x_kj) - V_k grad T_j(x_jk),                  */
+/*   Vbar_k = sum_j T_j(x_jk)   (j = k included),                            */
+/* with T_i the moment terms weighted by i's moment cotangents.  A singular  */
+/* particle contributes nothing and is counted.                              */
+int orc_corrections_adjoint(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *V,
+                            double L, const double *Abar, const double *Bbar, const double *gAbar, const double *gBbar,
+                            double *xbar, double *Vbar, int64_t *nsing) {
+    double hmax = max_h_gas(n, species, h);
+    if (n < 0 || L <= 0 || !(2.0 * hmax < 0.5 * L)) return ORC_EBOX;
+    uint8_t *gmask = gas_mask(n, species);
+    CellList cl;
+    if (cells_build(&cl, n, pos, gmask, L, 2.0 * hmax > 0 ? 2.0 * hmax : L, 0)) { free(gmask); return ORC_ENOMEM; }
+    Moments *mb = (Moments *)calloc((size_t)(n > 0 ? n : 1), sizeof(Moments));
+    const int64_t *nosub = NULL;
+    int64_t pairs = 0, singular = 0;
+    /* pass 1: every particle's moments and their cotangents */
+    FOR_EACH_I(nosub, 0, n, {
+        if (species[i] != 0) continue;
+        int64_t nc = cells_candidates(&cl, &pos[3 * i], buf);
+        Moments mo;
+        memset(&mo, 0, sizeof(mo));
+        for (int64_t t = 0; t < nc; ++t) {
+            int64_t j = buf[t];
+            double x[3];
+            min_image(&pos[3 * i], &pos[3 * j], L, x);
+            double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            double hij = 0.5 * (h[i] + h[j]);
+            if (!(r2 < 4.0 * hij * hij)) continue;
+            double W, dWr;
+            wendland(sqrt(r2), hij, &W, &dWr);
+            double Vj = V[j];
+            mo.m0 += Vj * W;
+            for (int a = 0; a < 3; ++a) {
+                mo.m1[a] += Vj * W * x[a];
+                for (int b = 0; b < 3; ++b) mo.m2[a][b] += Vj * W * x[a] * x[b];
+            }
+            for (int g = 0; g < 3; ++g) {
+                mo.dm0[g] += Vj * dWr * x[g];
+                for (int a = 0; a < 3; ++a) {
+                    mo.dm1[g][a] += Vj * ((a == g ? W : 0.0) + x[a] * dWr * x[g]);
+                    for (int b = 0; b < 3; ++b)
+                        mo.dm2[g][a][b] +=
+                            Vj * ((a == g ? x[b] * W : 0.0) + (b == g ? x[a] * W : 0.0) + x[a] * x[b] * dWr * x[g]);
+                }
+            }
+        }
+        if (moments_bar(&mo, Abar[i], &Bbar[3 * i], &gAbar[3 * i], &gBbar[9 * i], &mb[i])) {
+            _Pragma("omp atomic") ++singular;
+        }
+    });
+    /* pass 2: gather over pairs */
+    FOR_EACH_I(nosub, 0, n, {
+        for (int c = 0; c < 3; ++c) xbar[3 * i + c] = 0.0;
+        Vbar[i] = 0.0;
+        if (species[i] != 0) continue;
+        int64_t nc = cells_candidates(&cl, &pos[3 * i], buf);
+        for (int64_t t = 0; t < nc; ++t) {
+            int64_t j = buf[t];
+            double x[3], xm[3];
+            min_image(&pos[3 * i], &pos[3 * j], L, x); /* x_ij */
+            double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            double hij = 0.5 * (h[i] + h[j]);
+            if (!(r2 < 4.0 * hij * hij)) continue;
+            double W, dWr, ddWr;
+            wendland2(sqrt(r2), hij, &W, &dWr, &ddWr);
+            for (int c = 0; c < 3; ++c) xm[c] = -x[c];
+            double gi[3], gj[3];
+            moment_term(&mb[i], x, W, dWr, ddWr, gi);
+            double Tj = moment_term(&mb[j], xm, W, dWr, ddWr, gj);
+            for (int c = 0; c < 3; ++c) xbar[3 * i + c] += V[j] * gi[c] - V[i] * gj[c];
+            Vbar[i] += Tj;
+        }
+    });
+    (void)pairs;
+    cells_free(&cl);
+    free(gmask);
+    free(mb);
+    if (nsing) *nsing = singular;
+    return ORC_OK;
+}
+
+/* d G / d y contracted with c, for G_q(y) = gA_q (1 + B.y) W + A ((gB y)_q +  */
+/* B_q) W + A (1 + B.y) dWr y_q (the corrected-kernel gradient of orc_hydro, */
+/* (gB y)_q = sum_a gB[3q+a] y_a, W and dWr taken at |y|): out_p =           */
+/* sum_q c_q dG_q/dy_p; and the cotangents of G's parameters, added to       */
+/* Ab, Bb[3], gAb[3], gBb[9] (any of them may be NULL).                      */
+static void grad_WR_vjp(const double y[3], double W, double dWr, double ddWr, double A, const double *B,
+                        const double *gA, const double *gB, const double c[3], double out[3], double *Ab, double *Bb,
+                        double *gAb, double *gBb) {
+    double By = B[0] * y[0] + B[1] * y[1] + B[2] * y[2];
+    double cy = c[0] * y[0] + c[1] * y[1] + c[2] * y[2];
+    double cgA = c[0] * gA[0] + c[1] * gA[1] + c[2] * gA[2];
+    double gBy[3], cgBy = 0.0, cB = c[0] * B[0] + c[1] * B[1] + c[2] * B[2];
+    for (int q = 0; q < 3; ++q) {
+        gBy[q] = gB[3 * q] * y[0] + gB[3 * q + 1] * y[1] + gB[3 * q + 2] * y[2];
+        cgBy += c[q] * gBy[q];
+    }
+    for (int p = 0; p < 3; ++p) {
+        double gBtc = c[0] * gB[p] + c[1] * gB[3 + p] + c[2] * gB[6 + p];
+        out[p] = B[p] * (W * cgA + A * dWr * cy) + y[p] * (cgA * (1.0 + By) * dWr + A * dWr * (cgBy + cB) +
+                                                         A * (1.0 + By) * ddWr * cy) +
+                 A * W * gBtc + A * (1.0 + By) * dWr * c[p];
+    }
+    if (gAb)
+        for (int q = 0; q < 3; ++q) gAb[q] += c[q] * (1.0 + By) * W;
+    if (Ab) *Ab += W * (cgBy + cB) + (1.0 + By) * dWr * cy;
+    if (Bb)
+        for (int a = 0; a < 3; ++a) Bb[a] += y[a] * (W * cgA + A * dWr * cy) + A * W * c[a];
+    if (gBb)
+        for (int q = 0; q < 3; ++q)
+            for (int a = 0; a < 3; ++a) gBb[3 * q + a] += c[q] * A * W * y[a];
+}
+
+/* Reverse mode of orc_hydro (Monaghan viscosity, equal split) for the        */
+/* cotangents dvbar[3n], dubar[n] of dv/dt and du/dt, with every input of the */
+/* pair force independent: out xbar[3n], vbar[3n], ubar[n], mbar[n],          */
+/* Vbar[n], rhobar[n], Abar[n], Bbar[3n], gAbar[3n], gBbar[9n].  With        */
+/* a_i = dvbar_i/m_i and b_i = dubar_i/m_i the loss is a sum over unordered   */
+/* pairs i != j of l_ij = (a_i - a_j).f_ij + (b_i + b_j) e_ij,               */
+/* e_ij = -1/2 v_ij.f_ij (f_ji = -f_ij, e_ji = e_ij; the self pair has        */
+/* f_ii = 0 for every value of i's inputs), so particle k's cotangents are   */
+/* the sums over its neighbours of dl_kj/d(k's inputs), plus                  */
+/* mbar_k = -(a_k.F_k + b_k E_k)/m_k from dv = F/m and du = E/m.             */
+int orc_hydro_adjoint(int64_t n, const double *pos, const uint8_t *species, const double *h, const double *m,
+                      const double *v, const double *u, const double *V, const double *rho, const double *A,
+                      const double *B, const double *gA, const double *gB, double L, double gamma, double alpha,
+                      double beta, double eta2, const double *dvbar, const double *dubar, double *xbar, double *vbar,
+                      double *ubar, double *mbar, double *Vbar, double *rhobar, double *Abar, double *Bbar,
+                      double *gAbar, double *gBbar) {
+    double hmax = max_h_gas(n, species, h);
+    if (n < 0 || L <= 0 || !(2.0 * hmax < 0.5 * L)) return ORC_EBOX;
+    uint8_t *gmask = gas_mask(n, species);
+    CellList cl;
+    if (cells_build(&cl, n, pos, gmask, L, 2.0 * hmax > 0 ? 2.0 * hmax : L, 0)) { free(gmask); return ORC_ENOMEM; }
+    const int64_t *nosub = NULL;
+    int64_t pairs = 0;
+    FOR_EACH_I(nosub, 0, n, {
+        double xb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, Vb = 0.0, Pb = 0.0, cb = 0.0, rb = 0.0;
+        double Ab = 0.0, Bb[3] = {0, 0, 0}, gAb[3] = {0, 0, 0}, gBb[9] = {0};
+        double F[3] = {0, 0, 0}, E = 0.0;
+        if (species[i] == 0) {
+            int64_t nc = cells_candidates(&cl, &pos[3 * i], buf);
+            double Pi = (gamma - 1.0) * rho[i] * u[i];
+            double ci = sqrt(gamma * (gamma - 1.0) * u[i]);
+            double ai[3] = {dvbar[3 * i] / m[i], dvbar[3 * i + 1] / m[i], dvbar[3 * i + 2] / m[i]};
+            double bi = dubar[i] / m[i];
+            for (int64_t t = 0; t < nc; ++t) {
+                int64_t j = buf[t];
+                if (j == i) continue;
+                double x[3], xm[3];
+                min_image(&pos[3 * i], &pos[3 * j], L, x);
+                double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+                double hij = 0.5 * (h[i] + h[j]);
+                if (!(r2 < 4.0 * hij * hij)) continue;
+                double W, dWr, ddWr;
+                wendland2(sqrt(r2), hij, &W, &dWr, &ddWr);
+                for (int c = 0; c < 3; ++c) xm[c] = -x[c];
+                double gi[3], gj[3];
+                grad_WR(x, W, dWr, A[i], &B[3 * i], &gA[3 * i], &gB[9 * i], gi);
+                grad_WR(xm, W, dWr, A[j], &B[3 * j], &gA[3 * j], &gB[9 * j], gj);
+                double Pj = (gamma - 1.0) * rho[j] * u[j];
+                double cj = sqrt(gamma * (gamma - 1.0) * u[j]);
+                double vij[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
+                double vx = vij[0] * x[0] + vij[1] * x[1] + vij[2] * x[2];
+                double den = r2 + eta2 * hij * hij;
+                double mu = vx < 0.0 ? hij * vx / den : 0.0;
+                double rbar = 0.5 * (rho[i] + rho[j]), cbar = 0.5 * (ci + cj);
+                double Q = rbar * (-alpha * cbar * mu + beta * mu * mu);
+                double Pi_ = Pi + Pj + Q;
+                double pre = -0.5 * V[i] * V[j] * Pi_;
+                double d[3] = {gi[0] - gj[0], gi[1] - gj[1], gi[2] - gj[2]};
+                double aj[3] = {dvbar[3 * j] / m[j], dvbar[3 * j + 1] / m[j], dvbar[3 * j + 2] / m[j]};
+                double s = bi + dubar[j] / m[j];
+                double z[3], D = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    z[c] = ai[c] - aj[c] - 0.5 * s * vij[c];
+                    D += z[c] * d[c];
+                    F[c] += pre * d[c];
+                }
+                E += -0.5 * pre * (vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]);
+                double Pib = -0.5 * V[i] * V[j] * D;
+                Vb += -0.5 * V[j] * Pi_ * D;
+                Pb += Pib;
+                if (vx < 0.0) {
+                    double mub = Pib * rbar * (-alpha * cbar + 2.0 * beta * mu);
+                    rb += Pib * 0.5 * mu * (-alpha * cbar + beta * mu);
+                    cb += Pib * rbar * mu * (-0.5 * alpha);
+                    double vxb = mub * hij / den;
+                    double r2b = -mub * hij * vx / (den * den);
+                    for (int c = 0; c < 3; ++c) {
+                        xb[c] += vxb * vij[c] + 2.0 * r2b * x[c];
+                        vb[c] += vxb * x[c];
+                    }
+                }
+                double dbar[3] = {pre * z[0], pre * z[1], pre * z[2]};
+                for (int c = 0; c < 3; ++c) vb[c] += -0.5 * s * pre * d[c];
+                double o1[3], o2[3];
+                grad_WR_vjp(x, W, dWr, ddWr, A[i], &B[3 * i], &gA[3 * i], &gB[9 * i], dbar, o1, &Ab, Bb, gAb, gBb);
+                grad_WR_vjp(xm, W, dWr, ddWr, A[j], &B[3 * j], &gA[3 * j], &gB[9 * j], dbar, o2, NULL, NULL, NULL,
+                            NULL);
+                for (int c = 0; c < 3; ++c) xb[c] += o1[c] + o2[c];
+            }
+            rb += Pb * (gamma - 1.0) * u[i];
+            double ub = Pb * (gamma - 1.0) * rho[i] + (ci > 0.0 ? cb * gamma * (gamma - 1.0) / (2.0 * ci) : 0.0);
+            ubar[i] = ub;
+            mbar[i] = -(ai[0] * F[0] + ai[1] * F[1] + ai[2] * F[2] + bi * E) / m[i];
+        } else {
+            ubar[i] = 0.0;
+            mbar[i] = 0.0;
+        }
+        for (int c = 0; c < 3; ++c) {
+            xbar[3 * i + c] = xb[c];
+            vbar[3 * i + c] = vb[c];
+            Bbar[3 * i + c] = Bb[c];
+            gAbar[3 * i + c] = gAb[c];
+        }
+        for (int c = 0; c < 9; ++c) gBbar[9 * i + c] = gBb[c];
+        Vbar[i] = Vb;
+        rhobar[i] = rb;
+        Abar[i] = Ab;
+    });
+    (void)pairs;
+    cells_free(&cl);
+    free(gmask);
+    return ORC_OK;
+}

@@ -67,6 +67,12 @@ def lib():
                                                _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double, _i64,
                                                ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64]
+            L.orc_wendland2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d]
+            L.orc_corrections_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _d, _d, _d,
+                                                  _d, _d, _d, _i64]
+            L.orc_hydro_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _d, _d] + [_d] * 10
             L.orc_energy_share.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_energy_share.restype = ctypes.c_double
             L.orc_extras.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_double,
@@ -262,6 +268,46 @@ def hydro_compatible(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, 
                                       ctypes.byref(npairs)),
            "hydro_compatible")
     return dv, du, vsig
+
+
+def wendland2(r, h):
+    """W, (dW/dr)/r and (d[(dW/dr)/r]/dr)/r of the Wendland C4 kernel (support 2h)."""
+    r = _f64(np.atleast_1d(r))
+    h = _f64(np.broadcast_to(h, r.shape))
+    W, dWr, ddWr = np.zeros_like(r), np.zeros_like(r), np.zeros_like(r)
+    lib().orc_wendland2(r.size, _p(r, _d), _p(h, _d), _p(W, _d), _p(dWr, _d), _p(ddWr, _d))
+    return W, dWr, ddWr
+
+
+def corrections_adjoint(I: Inputs, V, Abar, Bbar, gAbar, gBbar):
+    """Gradient of sum Abar A + Bbar.B + gAbar.gA + gBbar:gB (the outputs of corrections, same
+    layouts: B f64[n,3], gA f64[n,3], gB f64[n,9]) in the positions f64[n,3] and volumes f64[n];
+    also the count of singular particles (they contribute nothing)."""
+    a = [_f64(x) for x in (V, Abar, Bbar, gAbar, gBbar)]
+    xbar = np.zeros((I.n, 3))
+    Vbar = np.zeros(I.n)
+    nsing = ctypes.c_int64(0)
+    _check(lib().orc_corrections_adjoint(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(a[0], _d), I.L,
+                                         *[_p(x, _d) for x in a[1:]], _p(xbar, _d), _p(Vbar, _d),
+                                         ctypes.byref(nsing)),
+           "corrections_adjoint")
+    return xbar, Vbar, int(nsing.value)
+
+
+def hydro_adjoint(I: Inputs, V, rho, A, B, gA, gB, gamma, alpha, beta, eta2, dvbar, dubar):
+    """Reverse mode of hydro (Monaghan viscosity, equal split) for the cotangents dvbar f64[n,3],
+    dubar f64[n], with every input of the pair force independent.  Returns a dict of the
+    gradients in x, v (f64[n,3]), u, m, V, rho (f64[n]), A (f64[n]), B, gA (f64[n,3]), gB (f64[n,9])."""
+    a = [_f64(x) for x in (V, rho, A, B, gA, gB, dvbar, dubar)]
+    out = dict(x=np.zeros((I.n, 3)), v=np.zeros((I.n, 3)), u=np.zeros(I.n), m=np.zeros(I.n), V=np.zeros(I.n),
+               rho=np.zeros(I.n), A=np.zeros(I.n), B=np.zeros((I.n, 3)), gA=np.zeros((I.n, 3)),
+               gB=np.zeros((I.n, 9)))
+    _check(lib().orc_hydro_adjoint(I.n, _p(I.pos, _d), _p(I.species, _u8), _p(I.h, _d), _p(I.m, _d), _p(I.v, _d),
+                                   _p(I.u, _d), *[_p(x, _d) for x in a[:6]], I.L, float(gamma), float(alpha),
+                                   float(beta), float(eta2), _p(a[6], _d), _p(a[7], _d),
+                                   *[_p(out[k], _d) for k in ("x", "v", "u", "m", "V", "rho", "A", "B", "gA", "gB")]),
+           "hydro_adjoint")
+    return out
 
 
 def energy_share(ui, uj, dE):
