@@ -488,7 +488,9 @@ def extras_chain(api, ctx, db, stream, peak_tflops, reps=3):
                     "intermediates); extras = difference of the corrections intervals, mean of %d steps" % reps}
 
 
-ADVANCE_FLOPS_PER_PAIR = {"hydro_accel": 168, "hydro_energy": 176}
+# the limited forms (the Extras chain): limited hydro 215 less the equal-split energy term (8), plus the
+# signal speed (9) or the compatible share of the work (17)
+ADVANCE_FLOPS_PER_PAIR = {"hydro_accel": 216, "hydro_energy": 224}
 
 
 def advance_step(api, ctx, db, stream, peak_tflops, reps=2):
