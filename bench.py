@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Extras-chain measurement")
     ap.add_argument("--no-advance", action="store_true", help="skip the timestep/integrator measurement")
+    ap.add_argument("--no-adjoint-chain", action="store_true",
+                    help="skip the corrections/hydro adjoint measurement")
     ap.add_argument("--advance-only", action="store_true",
                     help="run only the timestep/integrator measurement (--steps steps) and print it")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants")
@@ -426,6 +428,11 @@ def main():
             line["advance"] = advance_step(api, ctx, db, stream, peak_tflops)
         except Exception as e:  # reported, never silent
             line["advance"] = {"error": repr(e)}
+    if not args.no_adjoint_chain:
+        try:
+            line["adjoint_chain"] = adjoint_chain(api, ctx, db, stream, peak_tflops)
+        except Exception as e:  # reported, never silent
+            line["adjoint_chain"] = {"error": repr(e)}
     if not args.no_batched:
         try:
             line["batched_vs_plain"] = batched_vs_plain(args, local, dist)
@@ -549,6 +556,58 @@ def advance_step(api, ctx, db, stream, peak_tflops, reps=2):
                     "after one warm-up; each step = two leaf builds + the chain twice + four hydro passes, "
                     "in the kernel orders; ms/pairs_per_s/tflops are the passes as single C-ABI calls on "
                     "one leaf build (caller-order inputs: gathers and scatters included)" % reps}
+
+
+# algorithmic FP32 work per in-range pair (FMA = 2): the corrections preparation sweep is the
+# corrections forward sweep; its per-particle FP64 reverse is not counted
+ADJOINT_FLOPS_PER_PAIR = {"corrections_adjoint_prep": 135, "corrections_adjoint_sweep": 400,
+                          "hydro_adjoint": 480}
+
+
+def adjoint_chain(api, ctx, db, stream, peak_tflops, reps=2):
+    """The adjoint row: crk_hydro_adjoint and crk_corrections_adjoint (its two sweeps) as single
+    C-ABI calls on one leaf build of the workload, random cotangents, CUDA events on the
+    context stream, mean of `reps` calls after a warm-up; outside the headline timed region."""
+    import torch
+
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, rho, _ = api.geometry(ctx, lv, db.m)
+    A, B, gA, gB, _ = api.corrections(ctx, lv, V)
+    _, _, _, c = api.hydro(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB, count=True)
+    torch.cuda.synchronize()
+    pairs = int(c.cpu()[0])
+    gen = torch.Generator(device=db.x.device).manual_seed(7)
+    n = db.n
+    dvbar = torch.randn(3, n, device=db.x.device, generator=gen)
+    dubar = torch.randn(n, device=db.x.device, generator=gen)
+    ms = {}
+
+    def timed(fn):
+        fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            out = fn()
+        ev[1].record(stream)
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps, out
+
+    ms["hydro_adjoint"], g = timed(lambda: api.hydro_adjoint(ctx, lv, db.hp, db.m, db.v3, db.u, V, rho, A, B, gA, gB,
+                                                             dvbar, dubar))
+    ms["corrections_adjoint"], _ = timed(lambda: api.corrections_adjoint(ctx, lv, V, g["A"], g["B"], g["gA"],
+                                                                         g["gB"]))
+    lv.free()
+    fl = ADJOINT_FLOPS_PER_PAIR
+    work = {"hydro_adjoint": fl["hydro_adjoint"] * pairs,
+            "corrections_adjoint": (fl["corrections_adjoint_prep"] + fl["corrections_adjoint_sweep"]) * pairs}
+    tf = {k: work[k] / (ms[k] * 1e-3) / 1e12 for k in ms}
+    return {"pairs_per_launch": pairs, "ms": {k: round(v, 4) for k, v in ms.items()},
+            "pairs_per_s": {k: pairs / (v * 1e-3) for k, v in ms.items()},
+            "tflops": tf, "frac_of_fp32_peak": {k: v / peak_tflops for k, v in tf.items()},
+            "flops_per_pair": fl,
+            "note": "single C-ABI calls on caller-order inputs (gathers and scatters included), random "
+                    "cotangents; corrections_adjoint = preparation sweep (moments + FP64 reverse of the "
+                    "3x3 step) + gradient sweep; mean of %d calls after a warm-up" % reps}
 
 
 def batched_vs_plain(args, local, dist):

@@ -336,6 +336,42 @@ int grav_short_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
 int crk_geometry_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *m, const float *V, const float *rhobar,
                          const float *Vbar, float *gx3, float *gm);
 
+/* Reverse mode of crk_corrections (not in the paper; extends the gravity and
+ * geometry adjoints to the corrections).  For cotangents Abar[n], Bbar[3n],
+ * gradAbar[3n], gradBbar[9n] (the layouts of crk_corrections' outputs) it
+ * returns the gradient of
+ *   L = sum_i Abar_i A_i + Bbar_i.B_i + gradAbar_i.gradA_i + gradBbar_i:gradB_i
+ * in the positions, xbar3[3n], and in the volumes, Vbar[n] (h held fixed; the
+ * leaves are constant).  Pair (i, j) enters i's moments as V_j t(x_ij); each
+ * particle's moment cotangents come from the closed-form reverse of its FP64
+ * 3x3 step (a first sweep recomputes the moments), then
+ *   xbar_i = sum_j V_j grad T_i(x_ij) - V_i grad T_j(x_ji),  Vbar_i = sum_j T_j(x_ji)
+ * with T_i the moment terms weighted by i's cotangents (a second sweep; nothing
+ * per pair is stored).  A singular particle contributes nothing and is
+ * counted in n_singular (device int32, may be NULL).  Outputs overwritten;
+ * dark matter gets 0. */
+int crk_corrections_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *V, const float *Abar,
+                            const float *Bbar, const float *gradAbar, const float *gradBbar, float *xbar3,
+                            float *Vbar, int32_t *n_singular);
+
+/* Reverse mode of crk_hydro (Monaghan viscosity, equal split; not in the
+ * paper) for cotangents dvbar3[3n] of dvdt3 and dubar[n] of dudt, every input
+ * of the pair force held independent: the gradients in the positions
+ * (xbar3[3n]), velocities (vbar3[3n]), u, m, V, rho (ubar, mbar, Vbar, rhobar
+ * [n]) and the corrections (Abar[n], Bbar3[3n], gradAbar3[3n], gradBbar9[9n],
+ * crk_corrections' layouts).  With a_i = dvbar_i/m_i and b_i = dubar_i/m_i the
+ * loss is a sum over unordered pairs of (a_i - a_j).f_ij + (b_i + b_j) e_ij;
+ * each particle gathers the derivative of its pairs' terms in its own inputs
+ * (pair terms recomputed, no atomics).  Chained with crk_corrections_adjoint
+ * and crk_geometry_adjoint it gives the gradient of a loss of dv/dt, du/dt in
+ * the positions and masses through the whole forward chain.  Outputs
+ * overwritten; dark matter gets 0. */
+int crk_hydro_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+                      const float *u, const float *V, const float *rho, const float *A, const float *B,
+                      const float *gradA, const float *gradB, const float *dvbar3, const float *dubar, float *xbar3,
+                      float *vbar3, float *ubar, float *mbar, float *Vbar, float *rhobar, float *Abar, float *Bbar3,
+                      float *gradAbar3, float *gradBbar9);
+
 /* One whole step of the path on one set of leaves, in this order: geometry,
  * corrections, hydro, gravity, gravity adjoint, geometry adjoint.  Inputs m,
  * v3, u (caller order, as for the single calls).  The intermediates stay in

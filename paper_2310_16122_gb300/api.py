@@ -300,6 +300,36 @@ def advance(ctx: Context, db: "DeviceBox", ap: AdvanceParams, conservation=None,
     return dt
 
 
+def corrections_adjoint(ctx: Context, lv: Leaves, V, Abar, Bbar, gAbar, gBbar):
+    """Gradient of sum Abar A + Bbar.B + gAbar.gradA + gBbar:gradB in the positions (3, n) and
+    volumes (n); also the singular count (device int32)."""
+    n = lv.n
+    gx, gV = ctx.empty(3, n), ctx.empty(n)
+    ns = torch.zeros(1, dtype=torch.int32, device=ctx.device)
+    ctx.check(N.lib().crk_corrections_adjoint(ctx.handle, lv.handle, _f32(V, "V", n), _f32(Abar, "Abar", n),
+                                              _f32(Bbar, "Bbar", 3 * n), _f32(gAbar, "gradAbar", 3 * n),
+                                              _f32(gBbar, "gradBbar", 9 * n), gx.data_ptr(), gV.data_ptr(),
+                                              ns.data_ptr()))
+    return gx, gV, ns
+
+
+def hydro_adjoint(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A, B, gA, gB, dvbar, dubar):
+    """Reverse mode of hydro for the cotangents dvbar (3, n), dubar (n): a dict of the gradients in
+    x, v (3, n), u, m, V, rho, A (n), B, gA (3, n) and gB (9, n), every input held independent."""
+    n = lv.n
+    out = dict(x=ctx.empty(3, n), v=ctx.empty(3, n), u=ctx.empty(n), m=ctx.empty(n), V=ctx.empty(n),
+               rho=ctx.empty(n), A=ctx.empty(n), B=ctx.empty(3, n), gA=ctx.empty(3, n), gB=ctx.empty(9, n))
+    hpc = hp.c()
+    ctx.check(N.lib().crk_hydro_adjoint(ctx.handle, lv.handle, ctypes.byref(hpc), _f32(m, "m", n),
+                                        _f32(v3, "v3", 3 * n), _f32(u, "u", n), _f32(V, "V", n), _f32(rho, "rho", n),
+                                        _f32(A, "A", n), _f32(B, "B", 3 * n), _f32(gA, "gradA", 3 * n),
+                                        _f32(gB, "gradB", 9 * n), _f32(dvbar, "dvbar", 3 * n),
+                                        _f32(dubar, "dubar", n),
+                                        *[out[k].data_ptr() for k in ("x", "v", "u", "m", "V", "rho", "A", "B", "gA",
+                                                                      "gB")]))
+    return out
+
+
 def grav_short(ctx: Context, lv: Leaves, gp: GravParams, m, count=False):
     n = lv.n
     a = ctx.empty(3, n)

@@ -1,8 +1,11 @@
 """torch.autograd.Function wrappers whose backward passes are libcrk's hand-written adjoint kernels.
 
-The forward passes call grav_short and crk_geometry; the backward passes call
-grav_short_adjoint and crk_geometry_adjoint, which recompute the pair terms
-(nothing per pair is stored).  Gradients flow to the positions (as a (3, n)
+The forward passes call grav_short, crk_geometry, crk_corrections and
+crk_hydro; the backward passes call grav_short_adjoint, crk_geometry_adjoint,
+crk_corrections_adjoint and crk_hydro_adjoint, which recompute the pair terms
+(nothing per pair is stored).  Chained, geometry -> corrections -> hydro give
+the gradient of a loss of dv/dt, du/dt in the positions, masses, velocities
+and u.  Gradients flow to the positions (as a (3, n)
 tensor) and the masses; h is held fixed and the leaves are treated as
 constant (piecewise constant in the positions, so they carry no gradient).
 
@@ -53,6 +56,60 @@ class CrkGeometry(torch.autograd.Function):
         gx, gm = api.geometry_adjoint(ctx, leaves, m.detach().contiguous(), V, rhobar.contiguous(),
                                       Vbar.contiguous() if Vbar is not None else None)
         return gx, gm, None, None
+
+
+class CrkCorrections(torch.autograd.Function):
+    """(A, B, gradA, gradB) = crk_corrections(positions, V); backward gives dL/dpositions, dL/dV."""
+
+    @staticmethod
+    def forward(fctx, pos3, V, ctx: api.Context, leaves: api.Leaves):
+        A, B, gA, gB, _ = api.corrections(ctx, leaves, V.detach().contiguous())
+        fctx.save_for_backward(V)
+        fctx.crk = (ctx, leaves)
+        return A, B, gA, gB
+
+    @staticmethod
+    def backward(fctx, Abar, Bbar, gAbar, gBbar):
+        (V,) = fctx.saved_tensors
+        ctx, leaves = fctx.crk
+        n = V.numel()
+        z = lambda t, *shape: t.contiguous() if t is not None else torch.zeros(*shape, device=V.device)
+        gx, gV, _ = api.corrections_adjoint(ctx, leaves, V.detach().contiguous(), z(Abar, n), z(Bbar, 3, n),
+                                            z(gAbar, 3, n), z(gBbar, 9, n))
+        return gx, gV, None, None
+
+
+class CrkHydro(torch.autograd.Function):
+    """(dv, du) = crk_hydro(positions, m, v, u, V, rho, A, B, gradA, gradB); backward gives the
+    gradients in every tensor input (the pair terms are recomputed)."""
+
+    @staticmethod
+    def forward(fctx, pos3, m, v3, u, V, rho, A, B, gA, gB, ctx: api.Context, leaves: api.Leaves,
+                hp: api.HydroParams):
+        ins = [t.detach().contiguous() for t in (m, v3, u, V, rho, A, B, gA, gB)]
+        dv, du, _, _ = api.hydro(ctx, leaves, hp, *ins)
+        fctx.save_for_backward(*ins)
+        fctx.crk = (ctx, leaves, hp)
+        return dv, du
+
+    @staticmethod
+    def backward(fctx, dvbar, dubar):
+        ins = fctx.saved_tensors
+        ctx, leaves, hp = fctx.crk
+        n = ins[0].numel()
+        dvbar = dvbar.contiguous() if dvbar is not None else torch.zeros(3, n, device=ins[0].device)
+        dubar = dubar.contiguous() if dubar is not None else torch.zeros(n, device=ins[0].device)
+        g = api.hydro_adjoint(ctx, leaves, hp, *ins, dvbar, dubar)
+        return (g["x"], g["m"], g["v"], g["u"], g["V"], g["rho"], g["A"], g["B"], g["gA"], g["gB"],
+                None, None, None)
+
+
+def corrections(pos3, V, ctx, leaves):
+    return CrkCorrections.apply(pos3, V, ctx, leaves)
+
+
+def hydro(pos3, m, v3, u, V, rho, A, B, gA, gB, ctx, leaves, hp):
+    return CrkHydro.apply(pos3, m, v3, u, V, rho, A, B, gA, gB, ctx, leaves, hp)
 
 
 def gravity(pos3, m, ctx, leaves, gp):

@@ -48,7 +48,7 @@ struct crk_ctx {
     std::string err;
     // growable scratch arena: one buffer per slot
     static const int kSlots = 34;  // leaf build 0-16 and 19-31, radix sort 12-14, scan 15, queue 17, step 18,
-                                   // integrator 32
+                                   // integrator 32, corrections adjoint 33
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     int64_t launches = 0;  // kernels this context has launched

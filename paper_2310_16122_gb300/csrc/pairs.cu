@@ -97,6 +97,21 @@ __device__ __forceinline__ void wendland(float r2, float hij, float &W, float &d
     dWr = n3 * ih2 * t5 * (-14.0f / 3.0f) * (1.0f + 2.5f * q);
 }
 
+// W, (dW/dr)/r and (d[(dW/dr)/r]/dr)/r = 495/(256 pi h^7) 35 (1 - q/2)^4 (zero beyond 2h)
+__device__ __forceinline__ void wendland2(float r2, float hij, float &W, float &dWr, float &ddWr) {
+    float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    float ih = __fdividef(1.0f, hij);
+    float q = r * ih;
+    float t = fmaxf(1.0f - 0.5f * q, 0.0f);
+    float t2 = t * t;
+    float t4 = t2 * t2;
+    float ih2 = ih * ih;
+    float n3 = kSigmaW * ih2 * ih;
+    W = n3 * t4 * t2 * (1.0f + q * (3.0f + q * (35.0f / 12.0f)));
+    dWr = n3 * ih2 * t4 * t * (-14.0f / 3.0f) * (1.0f + 2.5f * q);
+    ddWr = n3 * ih2 * ih2 * 35.0f * t4;
+}
+
 // ------------------------------------------------------------------ stages
 // Each stage defines Rec (one kernel-order record, also the shared-memory
 // entry), gather (build Rec of particle p), box_cut (pruning radius of a
@@ -622,6 +637,265 @@ struct CorrStage {
     }
 };
 
+// Reverse mode of Corrections (not in the paper).  Pair (i, j) enters i's
+// moments as V_j t(x_ij); with i's moment cotangents (from those of A, B, dA,
+// dB by the closed-form reverse of the per-particle step) the weighted terms
+// are T_i(x) = S0_i(x) W + S1_i(x) dWr, S0 a quadratic and S1 a cubic
+// polynomial in x.  The preparation sweep recomputes the moments and writes
+// each particle's 29 polynomial coefficients
+//   [c0, l0 (3), q0 (6: xx xy xz yy yz zz), l1 (3), q1 (6), k (10: xxx xxy xxz
+//    xyy xyz xzz yyy yyz yzz zzz)],
+// S0 = c0 + l0.x + q0(x), S1 = l1.x + q1(x) + k(x); the gradient sweep gathers
+//   xbar_i = sum_j V_j grad T_i(x_ij) - V_i grad T_j(x_ji),
+//   Vbar_i = sum_j T_j(x_ji)          (j = i included).
+constexpr int kCorrCoef = 29;
+
+struct CorrAdjP : CorrP {
+    const float *Abar, *Bbar, *gAbar, *gBbar;  // cotangents: A [n], B [3][n], dA [3][n], dB [9][n] (3g+a)
+    float *coef;                               // out: [29][n] (kernel order when korder, else caller)
+};
+
+struct CorrAdjPrepStage : CorrStage {
+    static constexpr bool kAllVariants = false;
+    using P = CorrAdjP;
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
+        const int64_t n = p.n;
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+        double m0 = (double)s.m0 - (double)s.c0, m1[3], M[3][3];
+        for (int a = 0; a < 3; ++a) m1[a] = (double)s.m1[a] - (double)s.c1[a];
+        for (int q = 0; q < 6; ++q) {
+            double v = (double)s.m2[q] - (double)s.c2[q];
+            M[ia[q]][ib[q]] = v;
+            M[ib[q]][ia[q]] = v;
+        }
+        double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                     M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                     M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        double tr = M[0][0] + M[1][1] + M[2][2];
+        if (!(det > 1e-12 * tr * tr * tr)) {  // singular: contributes nothing
+            for (int k = 0; k < kCorrCoef; ++k) p.coef[k * n + o] = 0.f;
+            if (p.n_singular) atomicAdd(p.n_singular, 1);
+            return;
+        }
+        double Mi[3][3];
+        double id = 1.0 / det;
+        Mi[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) * id;
+        Mi[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) * id;
+        Mi[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) * id;
+        Mi[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) * id;
+        Mi[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) * id;
+        Mi[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) * id;
+        Mi[1][0] = Mi[0][1];
+        Mi[2][0] = Mi[0][2];
+        Mi[2][1] = Mi[1][2];
+        double B[3], Bb[3], Mib[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int a = 0; a < 3; ++a) B[a] = -(Mi[a][0] * m1[0] + Mi[a][1] * m1[1] + Mi[a][2] * m1[2]);
+        double A = 1.0 / (m0 + B[0] * m1[0] + B[1] * m1[1] + B[2] * m1[2]);
+        for (int a = 0; a < 3; ++a) Bb[a] = (double)p.Bbar[a * n + o];
+        double Ab = (double)p.Abar[o];
+        // moment cotangents: dm1b[g][a], dm2b[g][ab] (symmetric in ab, packed as ia/ib)
+        double m0b = 0.0, m1b[3] = {0, 0, 0}, dm0b[3], dm1b[3][3], dm2b[3][6];
+        for (int g = 0; g < 3; ++g) {
+            double dM[3][3], t[3], tb[3], K = (double)s.dm0[g];
+            for (int q = 0; q < 6; ++q) {
+                dM[ia[q]][ib[q]] = s.dm2[6 * g + q];
+                dM[ib[q]][ia[q]] = s.dm2[6 * g + q];
+            }
+            for (int a = 0; a < 3; ++a) {
+                t[a] = (double)s.dm1[3 * g + a] + dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2];
+                K += 2.0 * B[a] * (double)s.dm1[3 * g + a] + B[a] * (dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2]);
+            }
+            double gb[3];
+            for (int a = 0; a < 3; ++a) gb[a] = (double)p.gBbar[(3 * g + a) * n + o];
+            for (int a = 0; a < 3; ++a) tb[a] = -(Mi[a][0] * gb[0] + Mi[a][1] * gb[1] + Mi[a][2] * gb[2]);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) Mib[a][b] -= gb[a] * t[b];
+            const double gAb = (double)p.gAbar[g * n + o];
+            const double Kb = -A * A * gAb;
+            Ab += -2.0 * A * K * gAb;
+            dm0b[g] = Kb;
+            for (int a = 0; a < 3; ++a) {
+                dm1b[g][a] = tb[a] + 2.0 * B[a] * Kb;
+                Bb[a] += tb[0] * dM[0][a] + tb[1] * dM[1][a] + tb[2] * dM[2][a];  // dM symmetric
+                Bb[a] += 2.0 * (double)s.dm1[3 * g + a] * Kb + 2.0 * (dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2]) * Kb;
+            }
+            // dm2b[g][a][b] = tb_a B_b + B_a B_b Kb, summed over (a, b) and (b, a) for a packed
+            // off-diagonal entry (the moment sums are symmetric in ab)
+            for (int q = 0; q < 6; ++q) {
+                const int a = ia[q], b = ib[q];
+                double v = tb[a] * B[b] + B[a] * B[b] * Kb;
+                if (a != b) v += tb[b] * B[a] + B[b] * B[a] * Kb;
+                dm2b[g][q] = v;
+            }
+        }
+        const double denb = -A * A * Ab;
+        m0b += denb;
+        for (int a = 0; a < 3; ++a) {
+            Bb[a] += m1[a] * denb;
+            m1b[a] += B[a] * denb;
+        }
+        for (int a = 0; a < 3; ++a) {
+            m1b[a] -= Mi[0][a] * Bb[0] + Mi[1][a] * Bb[1] + Mi[2][a] * Bb[2];
+            for (int b = 0; b < 3; ++b) Mib[a][b] -= Bb[a] * m1[b];
+        }
+        double m2b[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double v = 0.0;
+                for (int c = 0; c < 3; ++c)
+                    for (int d = 0; d < 3; ++d) v += Mi[c][a] * Mib[c][d] * Mi[b][d];
+                m2b[a][b] = -v;
+            }
+        // polynomial coefficients.  dm2b enters as sum_{g,ab} dm2b[g][ab] (delta_ag x_b W +
+        // delta_bg x_a W + x_a x_b x_g dWr) with the packed (a <= b) entries carrying both orders.
+        double c[kCorrCoef];
+        c[0] = m0b + dm1b[0][0] + dm1b[1][1] + dm1b[2][2];
+        for (int e = 0; e < 3; ++e) c[1 + e] = m1b[e];
+        for (int g = 0; g < 3; ++g)
+            for (int q = 0; q < 6; ++q) {
+                const int a = ia[q], b = ib[q];
+                // delta_ag x_b + delta_bg x_a (for a = b = g: 2 x_a)
+                if (a == g) c[1 + b] += dm2b[g][q];
+                if (b == g) c[1 + a] += dm2b[g][q];
+            }
+        // q0: x^T m2b x as monomials
+        c[4] = m2b[0][0];
+        c[5] = m2b[0][1] + m2b[1][0];
+        c[6] = m2b[0][2] + m2b[2][0];
+        c[7] = m2b[1][1];
+        c[8] = m2b[1][2] + m2b[2][1];
+        c[9] = m2b[2][2];
+        for (int e = 0; e < 3; ++e) c[10 + e] = dm0b[e];
+        // q1: sum_ga dm1b[g][a] x_a x_g
+        c[13] = dm1b[0][0];
+        c[14] = dm1b[0][1] + dm1b[1][0];
+        c[15] = dm1b[0][2] + dm1b[2][0];
+        c[16] = dm1b[1][1];
+        c[17] = dm1b[1][2] + dm1b[2][1];
+        c[18] = dm1b[2][2];
+        // k: sum_{g,ab} dm2b[g][ab] x_g x_a x_b (packed entries already hold both ab orders)
+        for (int e = 0; e < 10; ++e) c[19 + e] = 0.0;
+        for (int g = 0; g < 3; ++g)
+            for (int q = 0; q < 6; ++q) {
+                int t[3] = {g, ia[q], ib[q]};
+                // sort the three axes to find the monomial
+                if (t[0] > t[1]) { int u = t[0]; t[0] = t[1]; t[1] = u; }
+                if (t[1] > t[2]) { int u = t[1]; t[1] = t[2]; t[2] = u; }
+                if (t[0] > t[1]) { int u = t[0]; t[0] = t[1]; t[1] = u; }
+                // index of (t0 <= t1 <= t2) among xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+                const int idx = t[0] == 0 ? (t[1] == 0 ? t[2] : (t[1] == 1 ? 2 + t[2] : 5))
+                                          : (t[0] == 1 ? (t[1] == 1 ? 6 + (t[2] - 1) : 8) : 9);
+                c[19 + idx] += dm2b[g][q];
+            }
+        for (int k = 0; k < kCorrCoef; ++k) p.coef[k * n + o] = (float)c[k];
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        for (int k = 0; k < kCorrCoef; ++k) p.coef[k * p.n + o] = 0.f;
+    }
+};
+
+struct CorrAdjSweepP {
+    const float *V, *coef;
+    float *xbar3, *Vbar;
+    int64_t n;
+    unsigned long long *count;
+    unsigned long long *swept;
+};
+
+// value and gradient of T(x) = S0 W + S1 dWr for coefficients c (layout above)
+__device__ __forceinline__ float corr_term(const float *c, const float x[3], float W, float dWr, float ddWr,
+                                           float g[3]) {
+    const float X = x[0], Y = x[1], Z = x[2];
+    const float q0 = fmaf(c[4] * X, X, fmaf(c[5] * X, Y, fmaf(c[6] * X, Z, fmaf(c[7] * Y, Y, fmaf(c[8] * Y, Z, c[9] * Z * Z)))));
+    const float S0 = c[0] + fmaf(c[1], X, fmaf(c[2], Y, c[3] * Z)) + q0;
+    const float g0x = c[1] + fmaf(2.0f * c[4], X, fmaf(c[5], Y, c[6] * Z));
+    const float g0y = c[2] + fmaf(c[5], X, fmaf(2.0f * c[7], Y, c[8] * Z));
+    const float g0z = c[3] + fmaf(c[6], X, fmaf(c[8], Y, 2.0f * c[9] * Z));
+    const float *k = c + 19;
+    const float XX = X * X, XY = X * Y, XZ = X * Z, YY = Y * Y, YZ = Y * Z, ZZ = Z * Z;
+    const float q1 = fmaf(c[13], XX, fmaf(c[14], XY, fmaf(c[15], XZ, fmaf(c[16], YY, fmaf(c[17], YZ, c[18] * ZZ)))));
+    const float cub = fmaf(k[0] * XX, X, fmaf(k[1] * XX, Y, fmaf(k[2] * XX, Z, fmaf(k[3] * YY, X, fmaf(k[4] * XY, Z,
+                      fmaf(k[5] * ZZ, X, fmaf(k[6] * YY, Y, fmaf(k[7] * YY, Z, fmaf(k[8] * ZZ, Y, k[9] * ZZ * Z)))))))));
+    const float S1 = fmaf(c[10], X, fmaf(c[11], Y, c[12] * Z)) + q1 + cub;
+    const float g1x = c[10] + fmaf(2.0f * c[13], X, fmaf(c[14], Y, c[15] * Z)) +
+                      fmaf(3.0f * k[0], XX, fmaf(2.0f * k[1], XY, fmaf(2.0f * k[2], XZ, fmaf(k[3], YY, fmaf(k[4], YZ, k[5] * ZZ)))));
+    const float g1y = c[11] + fmaf(c[14], X, fmaf(2.0f * c[16], Y, c[17] * Z)) +
+                      fmaf(k[1], XX, fmaf(2.0f * k[3], XY, fmaf(k[4], XZ, fmaf(3.0f * k[6], YY, fmaf(2.0f * k[7], YZ, k[8] * ZZ)))));
+    const float g1z = c[12] + fmaf(c[15], X, fmaf(c[17], Y, 2.0f * c[18] * Z)) +
+                      fmaf(k[2], XX, fmaf(k[4], XY, fmaf(2.0f * k[5], XZ, fmaf(k[7], YY, fmaf(2.0f * k[8], YZ, 3.0f * k[9] * ZZ)))));
+    const float a = fmaf(S0, dWr, S1 * ddWr);
+    g[0] = fmaf(g0x, W, fmaf(g1x, dWr, a * X));
+    g[1] = fmaf(g0y, W, fmaf(g1y, dWr, a * Y));
+    g[2] = fmaf(g0z, W, fmaf(g1z, dWr, a * Z));
+    return fmaf(S0, W, S1 * dWr);
+}
+
+struct CorrAdjStage {
+    static constexpr bool kPair = false;
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = false;
+    using P = CorrAdjSweepP;
+    struct __align__(16) Rec {
+        float x, y, z, h;
+        float V, c[kCorrCoef], pad[2];
+    };
+    struct I {
+        float gx, gy, gz, Vb;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) {
+        Rec r;
+        r.x = ps.x; r.y = ps.y; r.z = ps.z; r.h = ps.w;
+        r.V = p.V[o];
+#pragma unroll
+        for (int k = 0; k < kCorrCoef; ++k) r.c[k] = p.coef[k * p.n + o];
+        r.pad[0] = r.pad[1] = 0.f;
+        return r;
+    }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) {
+        s.gx = s.gy = s.gz = s.Vb = 0.f;
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float x[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};  // x_ij
+        float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float W, dWr, ddWr;
+        wendland2(r2, 0.5f * hs, W, dWr, ddWr);
+        W = in ? W : 0.0f;
+        dWr = in ? dWr : 0.0f;
+        ddWr = in ? ddWr : 0.0f;
+        float gi[3], gj[3];
+        const float xm[3] = {-x[0], -x[1], -x[2]};
+        corr_term(ri.c, x, W, dWr, ddWr, gi);
+        const float Tj = corr_term(rj.c, xm, W, dWr, ddWr, gj);
+        s.gx += rj.V * gi[0] - ri.V * gj[0];
+        s.gy += rj.V * gi[1] - ri.V * gj[1];
+        s.gz += rj.V * gi[2] - ri.V * gj[2];
+        s.Vb += Tj;
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
+        p.xbar3[o] = s.gx;
+        p.xbar3[p.n + o] = s.gy;
+        p.xbar3[2 * p.n + o] = s.gz;
+        p.Vbar[o] = s.Vb;
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        p.xbar3[o] = 0.f;
+        p.xbar3[p.n + o] = 0.f;
+        p.xbar3[2 * p.n + o] = 0.f;
+        p.Vbar[o] = 0.f;
+    }
+};
+
 struct HydroP {
     const float *m, *v3, *u, *V, *rho, *A, *B, *gA, *gB;
     float *dv3, *du;
@@ -716,7 +990,8 @@ struct HydroStageT {
     __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
     __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) { s.fx = s.fy = s.fz = s.e = 0.f; s.cnt = 0; }
     // grad W^R of record r at separation x (x = x_r - x_other): gA (1 + B.x) W + A (gB.x + B) W + A (1 + B.x) dWr x
-    __device__ static void grad_wr(const Rec &r, const float x[3], float W, float dWr, float g[3]) {
+    template <class R>
+    __device__ static void grad_wr(const R &r, const float x[3], float W, float dWr, float g[3]) {
         float Bx = fmaf(r.B[0], x[0], fmaf(r.B[1], x[1], r.B[2] * x[2]));
         float gb[9] = {r.gB0, r.gB1, r.gB[0], r.gB[1], r.gB[2], r.gB[3], r.gB[4], r.gB[5], r.gB[6]};
         float gA[3] = {r.gA0, r.gA1, r.gA2};
@@ -832,6 +1107,198 @@ struct HydroStageT {
 
 using HydroStage = HydroStageT<false>;
 using HydroLimStage = HydroStageT<true>;
+// Reverse mode of the hydro pair force (Monaghan viscosity, equal split; not
+// in the paper) for cotangents dvbar, dubar, with every input independent.
+// With a_i = dvbar_i/m_i, b_i = dubar_i/m_i the loss is a sum over unordered
+// pairs i != j of l_ij = z.f_ij, z = (a_i - a_j) - (b_i + b_j) v_ij / 2
+// (f_ji = -f_ij, e_ji = e_ij; the self pair has f_ii = 0 for all of i's
+// inputs), so each i gathers dl_ij/d(i's inputs) over its neighbours: one-sided,
+// nothing per pair stored, no atomics.  m enters through a and b only:
+// mbar_i = -(a_i.F_i + b_i E_i)/m_i with the recomputed sums F, E.
+struct HydroAdjP {
+    const float *m, *v3, *u, *V, *rho, *A, *B, *gA, *gB, *dvbar3, *dubar;
+    float *xbar3, *vbar3, *ubar, *mbar, *Vbar, *rhobar, *Abar, *Bbar3, *gAbar3, *gBbar9;
+    float gamma, alpha, beta, eta2;
+    int64_t n;
+    unsigned long long *count;
+    unsigned long long *swept;
+};
+
+// sum_q c_q dG_q/dy_p for the corrected-kernel gradient G(y) of a record (see grad_wr), and the
+// cotangents of its A, B, dA, dB when kParams
+template <bool kParams, class R>
+__device__ __forceinline__ void grad_wr_vjp(const R &r, const float y[3], float W, float dWr, float ddWr,
+                                            const float c[3], float out[3], float *Ab, float *Bb, float *gAb,
+                                            float *gBb) {
+    const float gb[9] = {r.gB0, r.gB1, r.gB[0], r.gB[1], r.gB[2], r.gB[3], r.gB[4], r.gB[5], r.gB[6]};
+    const float gA[3] = {r.gA0, r.gA1, r.gA2};
+    const float By = fmaf(r.B[0], y[0], fmaf(r.B[1], y[1], r.B[2] * y[2]));
+    const float cy = fmaf(c[0], y[0], fmaf(c[1], y[1], c[2] * y[2]));
+    const float cgA = fmaf(c[0], gA[0], fmaf(c[1], gA[1], c[2] * gA[2]));
+    const float cB = fmaf(c[0], r.B[0], fmaf(c[1], r.B[1], c[2] * r.B[2]));
+    float cgBy = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cgBy = fmaf(c[q], fmaf(gb[3 * q], y[0], fmaf(gb[3 * q + 1], y[1], gb[3 * q + 2] * y[2])), cgBy);
+    const float opB = 1.0f + By;
+    const float kB = fmaf(W, cgA, r.A * dWr * cy);
+    const float ky = fmaf(cgA * opB, dWr, r.A * fmaf(dWr, cgBy + cB, opB * ddWr * cy));
+    const float AW = r.A * W, kc = r.A * opB * dWr;
+#pragma unroll
+    for (int pp = 0; pp < 3; ++pp) {
+        const float gBtc = fmaf(c[0], gb[pp], fmaf(c[1], gb[3 + pp], c[2] * gb[6 + pp]));
+        out[pp] = fmaf(r.B[pp], kB, fmaf(y[pp], ky, fmaf(AW, gBtc, kc * c[pp])));
+    }
+    if constexpr (kParams) {
+        *Ab += fmaf(W, cgBy + cB, opB * dWr * cy);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            gAb[q] = fmaf(c[q] * opB, W, gAb[q]);
+            Bb[q] = fmaf(y[q], kB, fmaf(AW, c[q], Bb[q]));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gBb[3 * q + a] = fmaf(c[q] * AW, y[a], gBb[3 * q + a]);
+        }
+    }
+}
+
+struct HydroAdjStage {
+    static constexpr bool kPair = false;
+    static constexpr bool kGasOnly = true;
+    static constexpr bool kCons = false;
+    static constexpr bool kTag = false;
+    static constexpr bool kAllVariants = false;
+    using P = HydroAdjP;
+    struct __align__(16) Rec : HydroRec {
+        float ax, ay, az, b;  // dvbar/m, dubar/m
+    };
+    struct I {
+        float xb[3], vb[3], Vb, Pb, cb, rb, Ab, Bb[3], gAb[3], gBb[9], F[3], E;
+        int cnt;
+    };
+    __device__ static Rec gather(const P &p, int32_t o, float4 ps) {
+        const int64_t n = p.n;
+        Rec r;
+        r.x = ps.x; r.y = ps.y; r.z = ps.z; r.h = ps.w;
+        r.vx = p.v3[o]; r.vy = p.v3[n + o]; r.vz = p.v3[2 * n + o];
+        const float rho = p.rho[o], u = p.u[o];
+        r.P = (p.gamma - 1.0f) * rho * u;
+        r.c = sqrtf(p.gamma * (p.gamma - 1.0f) * u);
+        r.rho = rho;
+        r.V = p.V[o];
+        r.A = p.A[o];
+        r.B[0] = p.B[o]; r.B[1] = p.B[n + o]; r.B[2] = p.B[2 * n + o];
+        r.gA0 = p.gA[o]; r.gA1 = p.gA[n + o]; r.gA2 = p.gA[2 * n + o];
+        r.gB0 = p.gB[o]; r.gB1 = p.gB[n + o];
+        for (int k = 0; k < 7; ++k) r.gB[k] = p.gB[(2 + k) * n + o];
+        r.pad = __int_as_float(o);  // particle identity: the self pair is skipped
+        const float im = __fdividef(1.0f, p.m[o]);
+        r.ax = p.dvbar3[o] * im; r.ay = p.dvbar3[n + o] * im; r.az = p.dvbar3[2 * n + o] * im;
+        r.b = p.dubar[o] * im;
+        return r;
+    }
+    __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
+    __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
+    __device__ static void shift(Rec &r, float sx, float sy, float sz) { r.x += sx; r.y += sy; r.z += sz; }
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s.xb[a] = s.vb[a] = s.Bb[a] = s.gAb[a] = s.F[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s.gBb[a] = 0.f;
+        s.Vb = s.Pb = s.cb = s.rb = s.Ab = s.E = 0.f;
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &p, I &s, const Rec &ri, const Rec &rj) {
+        float x[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};  // x_ij
+        float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+        float hs = ri.h + rj.h;
+        const bool in = r2 < hs * hs && __float_as_int(ri.pad) != __float_as_int(rj.pad);
+        float hij = 0.5f * hs;
+        float W, dWr, ddWr;
+        wendland2(r2, hij, W, dWr, ddWr);
+        W = in ? W : 0.0f;  // every term below is then zero
+        dWr = in ? dWr : 0.0f;
+        ddWr = in ? ddWr : 0.0f;
+        float gi[3], gj[3];
+        HydroStage::grad_wr(ri, x, W, dWr, gi);
+        const float xm[3] = {-x[0], -x[1], -x[2]};
+        HydroStage::grad_wr(rj, xm, W, dWr, gj);
+        const float vij[3] = {ri.vx - rj.vx, ri.vy - rj.vy, ri.vz - rj.vz};
+        const float vx = fmaf(vij[0], x[0], fmaf(vij[1], x[1], vij[2] * x[2]));
+        const float den = fmaf(p.eta2 * hij, hij, r2);
+        const bool visc = vx < 0.0f && in;
+        const float mu = visc ? __fdividef(hij * vx, den) : 0.0f;
+        const float rbar = 0.5f * (ri.rho + rj.rho), cbar = 0.5f * (ri.c + rj.c);
+        const float Q = rbar * mu * fmaf(-p.alpha, cbar, p.beta * mu);
+        const float Pi = ri.P + rj.P + Q;
+        const float VV = ri.V * rj.V;
+        const float pre = -0.5f * VV * Pi;
+        const float d[3] = {gi[0] - gj[0], gi[1] - gj[1], gi[2] - gj[2]};
+        const float sb = ri.b + rj.b;
+        const float z[3] = {fmaf(-0.5f * sb, vij[0], ri.ax - rj.ax), fmaf(-0.5f * sb, vij[1], ri.ay - rj.ay),
+                            fmaf(-0.5f * sb, vij[2], ri.az - rj.az)};
+        const float D = fmaf(z[0], d[0], fmaf(z[1], d[1], z[2] * d[2]));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s.F[c] = fmaf(pre, d[c], s.F[c]);
+        s.E = fmaf(-0.5f * pre, fmaf(vij[0], d[0], fmaf(vij[1], d[1], vij[2] * d[2])), s.E);
+        const float Pib = -0.5f * VV * D;
+        s.Vb = fmaf(-0.5f * rj.V * Pi, D, s.Vb);
+        s.Pb += Pib;
+        if (visc) {
+            const float mub = Pib * rbar * fmaf(-p.alpha, cbar, 2.0f * p.beta * mu);
+            s.rb = fmaf(Pib * 0.5f * mu, fmaf(-p.alpha, cbar, p.beta * mu), s.rb);
+            s.cb = fmaf(Pib * rbar * mu, -0.5f * p.alpha, s.cb);
+            const float vxb = __fdividef(mub * hij, den);
+            const float r2b2 = -2.0f * vxb * __fdividef(vx, den);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                s.xb[c] = fmaf(vxb, vij[c], fmaf(r2b2, x[c], s.xb[c]));
+                s.vb[c] = fmaf(vxb, x[c], s.vb[c]);
+            }
+        }
+        const float dbar[3] = {pre * z[0], pre * z[1], pre * z[2]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s.vb[c] = fmaf(-0.5f * sb * pre, d[c], s.vb[c]);
+        float o1[3], o2[3];
+        grad_wr_vjp<true>(ri, x, W, dWr, ddWr, dbar, o1, &s.Ab, s.Bb, s.gAb, s.gBb);
+        grad_wr_vjp<false>(rj, xm, W, dWr, ddWr, dbar, o2, nullptr, nullptr, nullptr, nullptr);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s.xb[c] += o1[c] + o2[c];
+        if (kCount) s.cnt += in;
+    }
+    __device__ static void finish(const P &p, I &s, const Rec &ri, int32_t o, int64_t) {
+        const int64_t n = p.n;
+        const float u = p.u[o], rho = p.rho[o], g1 = p.gamma - 1.0f;
+        const float ub = fmaf(s.Pb * g1, rho, ri.c > 0.0f ? __fdividef(s.cb * p.gamma * g1, 2.0f * ri.c) : 0.0f);
+        const float rb = fmaf(s.Pb * g1, u, s.rb);
+        const float mb = -__fdividef(fmaf(ri.ax, s.F[0], fmaf(ri.ay, s.F[1], fmaf(ri.az, s.F[2], ri.b * s.E))), p.m[o]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            p.xbar3[c * n + o] = s.xb[c];
+            p.vbar3[c * n + o] = s.vb[c];
+            p.Bbar3[c * n + o] = s.Bb[c];
+            p.gAbar3[c * n + o] = s.gAb[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) p.gBbar9[c * n + o] = s.gBb[c];
+        p.ubar[o] = ub;
+        p.mbar[o] = mb;
+        p.Vbar[o] = s.Vb;
+        p.rhobar[o] = rb;
+        p.Abar[o] = s.Ab;
+    }
+    __device__ static void finish_other(const P &p, int32_t o) {
+        const int64_t n = p.n;
+        for (int c = 0; c < 3; ++c) {
+            p.xbar3[c * n + o] = 0.f;
+            p.vbar3[c * n + o] = 0.f;
+            p.Bbar3[c * n + o] = 0.f;
+            p.gAbar3[c * n + o] = 0.f;
+        }
+        for (int c = 0; c < 9; ++c) p.gBbar9[c * n + o] = 0.f;
+        p.ubar[o] = p.mbar[o] = p.Vbar[o] = p.rhobar[o] = p.Abar[o] = 0.f;
+    }
+};
+
 template <bool kLim>
 using HydroAccelStage = HydroStageT<kLim, kHydroAccel>;
 template <bool kLim>
@@ -2157,6 +2624,49 @@ int crk_hydro_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params 
     p.vstar = vstar3;
     if (dvdx) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
     return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+}
+
+int crk_corrections_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *V, const float *Abar,
+                            const float *Bbar, const float *gradAbar, const float *gradBbar, float *xbar3,
+                            float *Vbar, int32_t *n_singular) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!V || !Abar || !Bbar || !gradAbar || !gradBbar || !xbar3 || !Vbar))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    const int64_t n = lv->n;
+    if (n_singular) CRK_CUDA(ctx, cudaMemsetAsync(n_singular, 0, sizeof(int32_t), ctx->stream));
+    if (n == 0) return CRK_OK;
+    float *coef = (float *)crk_scratch(ctx, 33, sizeof(float) * kCorrCoef * (size_t)n);
+    if (!coef) return crk_fail(ctx, CRK_ENOMEM, "adjoint scratch");
+    CorrAdjP p{};
+    p.V = V;
+    p.n_singular = n_singular;
+    p.n = n;
+    p.Abar = Abar;
+    p.Bbar = Bbar;
+    p.gAbar = gradAbar;
+    p.gBbar = gradBbar;
+    p.coef = coef;
+    int rc;
+    if ((rc = run_stage<CorrAdjPrepStage>(ctx, lv, p, true, CRK_K_CORRECTIONS))) return rc;
+    CorrAdjSweepP q{V, coef, xbar3, Vbar, n, nullptr, nullptr};
+    return run_stage<CorrAdjStage>(ctx, lv, q, true, CRK_K_CORRECTIONS);
+}
+
+int crk_hydro_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
+                      const float *u, const float *V, const float *rho, const float *A, const float *B,
+                      const float *gradA, const float *gradB, const float *dvbar3, const float *dubar, float *xbar3,
+                      float *vbar3, float *ubar, float *mbar, float *Vbar, float *rhobar, float *Abar, float *Bbar3,
+                      float *gradAbar3, float *gradBbar9) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !hp) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->n > 0 && (!m || !v3 || !u || !V || !rho || !A || !B || !gradA || !gradB || !dvbar3 || !dubar || !xbar3 ||
+                      !vbar3 || !ubar || !mbar || !Vbar || !rhobar || !Abar || !Bbar3 || !gradAbar3 || !gradBbar9))
+        return crk_fail(ctx, CRK_EINVAL, "null array");
+    HydroAdjP p{m,      v3,     u,     V,     rho,   A,         B,         gradA,     gradB,
+                dvbar3, dubar,  xbar3, vbar3, ubar,  mbar,      Vbar,      rhobar,    Abar,
+                Bbar3,  gradAbar3, gradBbar9, hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, nullptr, nullptr};
+    return run_stage<HydroAdjStage>(ctx, lv, p, true, CRK_K_HYDRO);
 }
 
 template <bool kGas>

@@ -110,6 +110,8 @@ SIGNATURES = {
     "crk_hydro_accel": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 10 + [ctypes.c_float] + [_P] * 4,
     "crk_hydro_energy": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 14,
     "crk_timestep": [_P, _P, ctypes.c_float, ctypes.c_float, _P],
+    "crk_corrections_adjoint": [_P] * 10,
+    "crk_hydro_adjoint": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 21,
     "crk_advance": [_P, _I64, ctypes.c_float] + [_P] * 8 + [ctypes.POINTER(crk_leaf_params),
                                                            ctypes.POINTER(crk_hydro_params),
                                                            ctypes.POINTER(crk_grav_params),
