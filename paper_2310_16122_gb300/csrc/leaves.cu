@@ -394,24 +394,26 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
     return v;
 }
 
-// Shared state of bisect32 (one per block).
-constexpr int kMaxSeg = kMaxLeafCap / 32;
+// Shared state of bisect32 (one per block) for leaves of at most kCap members.
+template <int kCap>
 struct Bisect32 {
-    int16_t a[kMaxLeafCap], b[kMaxLeafCap];  // orders (member slots), double-buffered
-    float cax[kMaxLeafCap];                  // coordinate of the member at each position on its part's axis
-    uint32_t cid[kMaxLeafCap];               // its particle index (ties)
+    static constexpr int kMaxSeg = kCap / 32;
+    int16_t a[kCap], b[kCap];  // orders (member slots), double-buffered
+    float cax[kCap];           // coordinate of the member at each position on its part's axis
+    uint32_t cid[kCap];        // its particle index (ties)
     int lo[kMaxSeg], hi[kMaxSeg], ax[kMaxSeg];
     int nseg, more;
 };
 
-// Bisects positions [0, m) of the order bs.a (member slots; m <= kMaxLeafCap)
+// Bisects positions [0, m) of the order bs.a (member slots; m <= kCap)
 // into groups of 32: each part above 32 is ranked along the longest extent of
 // its members in (coordinate, index) order and split with 32 ceil(g/2) of its
 // g groups of 32 on the left, until every part holds at most 32; then every
 // run of 32 positions starting at a multiple of 32 is an RCB cell (at most
-// ceil(m/32) <= 32 parts, one per lane of warp 0).  All threads call it;
+// ceil(m/32) <= kCap/32 <= 32 parts, one per lane of warp 0).  All threads call it;
 // returns the array (bs.a or bs.b) holding the result in [0, m).
-__device__ int16_t *bisect32(Bisect32 &bs, int m, const float4 *pm, const uint64_t *key) {
+template <int kCap>
+__device__ int16_t *bisect32(Bisect32<kCap> &bs, int m, const float4 *pm, const uint64_t *key) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int16_t *src = bs.a, *dst = bs.b;
     if (threadIdx.x == 0) {
@@ -524,6 +526,9 @@ __device__ int16_t *bisect32(Bisect32 &bs, int m, const float4 *pm, const uint64
 // candidates within r_c of a group's box: at r_c = 3 such cells cut the
 // candidates per in-range pair from ~4.0 to ~3.3 against Z-order groups); and
 // the leaf-relative positions in both kernel orders.
+// kCap: the largest leaf the launch may meet (1024 with blocks of 128 threads; 128 with one
+// warp per block for RCB leaves of at most 128, whose shared arrays then fit 32 blocks per SM).
+template <int kCap>
 __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
                                  const int32_t *__restrict__ members, const float *__restrict__ x,
                                  const float *__restrict__ y, const float *__restrict__ z,
@@ -532,16 +537,16 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
                                  int32_t *__restrict__ leaf_ngas, float *__restrict__ bbox,
                                  float *__restrict__ hmax, float4 *__restrict__ pos, int32_t *__restrict__ kperm_g,
                                  float4 *__restrict__ pos_g, int32_t *__restrict__ err) {
-    __shared__ uint64_t key[kMaxLeafCap], zkey[kMaxLeafCap];
-    __shared__ Bisect32 bs;
-    __shared__ float4 pm[kMaxLeafCap];  // member position and h (0 for dark matter), gathered once
+    __shared__ uint64_t key[kCap], zkey[kCap];
+    __shared__ Bisect32<kCap> bs;
+    __shared__ float4 pm[kCap];  // member position and h (0 for dark matter), gathered once
     __shared__ float red[6][32];
     __shared__ int ngs[32];
     __shared__ float hms[32];
     const int64_t a = blockIdx.x;
     if (a >= n_leaves) return;
     const int lo = leaf_start[a], hi = leaf_start[a + 1], cnt = hi - lo;
-    if (cnt > kMaxLeafCap) {
+    if (cnt > kCap) {
         if (threadIdx.x == 0) atomicAdd(err, 1);
         return;
     }
@@ -1391,10 +1396,15 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         ALLOC(lv->kinv, int32_t, n);
         ALLOC(lv->kinv_g, int32_t, n);
         if (nl > 0) {
-            leaf_data_kernel<<<(unsigned)nl, 128, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
-                                                           p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
-                                                           lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g,
-                                                           flags + 4);
+            if (lp->mode == 1 && shape && shape->max_leaf_size <= 128)
+                leaf_data_kernel<128><<<(unsigned)nl, 32, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
+                                                                   p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
+                                                                   lv->bbox, lv->hmax, lv->pos, lv->kperm_g,
+                                                                   lv->pos_g, flags + 4);
+            else
+                leaf_data_kernel<kMaxLeafCap><<<(unsigned)nl, 128, 0, st>>>(
+                    nl, lv->leaf_start, members, p->x, p->y, p->z, p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
+                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g, flags + 4);
             ++ctx->launches;
         }
         if (n > 0) {
