@@ -2047,6 +2047,133 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_sub(LeafView lv, typenam
 }
 
 
+// Tiles with two 16-particle i-groups per warp for the packed gravity stages
+// (kPair): each half-warp's group (an RCB cell of its leaf) has its own box
+// and its own buffer of field-interleaved candidate pairs, swept two
+// candidates per lane step with f32x2 arithmetic; an odd tail is padded with
+// a massless dummy outside every cut.  A 16-particle cell prunes ~22% more of
+// the candidates than its 32-particle parent at r_c = 3.
+template <class S, bool kCount>
+__global__ void __launch_bounds__(kThreads) pair_kernel_sub_pair(LeafView lv, typename S::P p,
+                                                                 const typename S::Rec *__restrict__ rec,
+                                                                 double *__restrict__ cons_part) {
+    using Rec = typename S::Rec;
+    using Rec2 = typename S::Rec2;
+    constexpr int G = 16, NS = 2;
+    __shared__ __align__(16) Rec2 buf[kWarps][NS][kCap / 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sg = lane / G;
+    const unsigned below = lanemask_lt();
+    (void)cons_part;
+    __shared__ int64_t leaf_slot;
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
+        const int lo = lv.leaf_start[a];
+        const int hi = lv.leaf_start[a + 1];
+        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
+            const int i = g0 + lane;
+            const bool act = i < hi;
+            const Rec ri = rec[act ? i : g0];
+            typename S::I2 st;
+            S::init2(p, st, ri);
+            // group boxes (empty for groups without active lanes)
+            float l0 = act ? ri.x : INFINITY, l1 = act ? ri.y : INFINITY, l2 = act ? ri.z : INFINITY;
+            float h0 = act ? ri.x : -INFINITY, h1 = act ? ri.y : -INFINITY, h2 = act ? ri.z : -INFINITY;
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                l0 = fminf(l0, __shfl_xor_sync(CRK_FULL_MASK, l0, o));
+                l1 = fminf(l1, __shfl_xor_sync(CRK_FULL_MASK, l1, o));
+                l2 = fminf(l2, __shfl_xor_sync(CRK_FULL_MASK, l2, o));
+                h0 = fmaxf(h0, __shfl_xor_sync(CRK_FULL_MASK, h0, o));
+                h1 = fmaxf(h1, __shfl_xor_sync(CRK_FULL_MASK, h1, o));
+                h2 = fmaxf(h2, __shfl_xor_sync(CRK_FULL_MASK, h2, o));
+            }
+            float bl[NS][3], bh[NS][3];
+            float ul0 = INFINITY, ul1 = INFINITY, ul2 = INFINITY, uh0 = -INFINITY, uh1 = -INFINITY, uh2 = -INFINITY;
+#pragma unroll
+            for (int t = 0; t < NS; ++t) {
+                bl[t][0] = __shfl_sync(CRK_FULL_MASK, l0, t * G);
+                bl[t][1] = __shfl_sync(CRK_FULL_MASK, l1, t * G);
+                bl[t][2] = __shfl_sync(CRK_FULL_MASK, l2, t * G);
+                bh[t][0] = __shfl_sync(CRK_FULL_MASK, h0, t * G);
+                bh[t][1] = __shfl_sync(CRK_FULL_MASK, h1, t * G);
+                bh[t][2] = __shfl_sync(CRK_FULL_MASK, h2, t * G);
+                ul0 = fminf(ul0, bl[t][0]); ul1 = fminf(ul1, bl[t][1]); ul2 = fminf(ul2, bl[t][2]);
+                uh0 = fmaxf(uh0, bh[t][0]); uh1 = fmaxf(uh1, bh[t][1]); uh2 = fmaxf(uh2, bh[t][2]);
+            }
+            const float cut = S::leaf_cut(p, 0.0f, 0.0f);
+            const float far = 2.0f * cut + 1.0f;
+            const Rec dummy = S::far_dummy(uh0 + far, uh1 + far, uh2 + far);
+            int cnt[NS] = {0, 0};
+            unsigned long long swept = 0;  // counting runs: candidate evaluations of this lane's group
+            auto sweep = [&]() {
+                // pad odd counts, then every half-warp sweeps its own buffer in pairs
+                if (kCount) swept += (unsigned long long)(sg ? cnt[1] : cnt[0]);
+                if (lane == 0 && (cnt[0] & 1)) S::put2(buf[warp][0], cnt[0], dummy);
+                if (lane == 1 && (cnt[1] & 1)) S::put2(buf[warp][1], cnt[1], dummy);
+#pragma unroll
+                for (int t = 0; t < NS; ++t) cnt[t] = (cnt[t] + 1) & ~1;
+                __syncwarp();
+                const int kmax = max(cnt[0], cnt[1]) >> 1, mine = (sg ? cnt[1] : cnt[0]) >> 1;
+                for (int k = 0; k < kmax; ++k)
+                    if (k < mine) S::template interact2<kCount>(p, st, buf[warp][sg][k]);
+#pragma unroll
+                for (int t = 0; t < NS; ++t) cnt[t] = 0;
+                __syncwarp();
+            };
+            for (int e = ib; e < ie; ++e) {
+                const crk_image im = lv.img[e];
+                const int jlo = lv.leaf_start[im.b];
+                const int jhi = lv.leaf_start[im.b + 1];
+                {
+                    const float *bb = lv.bbox + 6 * (int64_t)im.b;
+                    float gx = fmaxf(fmaxf(im.sx - uh0, ul0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+                    float gy = fmaxf(fmaxf(im.sy - uh1, ul1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+                    float gz = fmaxf(fmaxf(im.sz - uh2, ul2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+                    if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+                }
+                for (int j0 = jlo; j0 < jhi; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool jv = j < jhi;
+                    Rec rj;
+                    if (jv) {
+                        rj = rec[j];
+                        S::shift(rj, im.sx, im.sy, im.sz);
+                    }
+                    bool full = false;
+#pragma unroll
+                    for (int t = 0; t < NS; ++t) {
+                        bool keep = false;
+                        if (jv) {
+                            float dx = fmaxf(fmaxf(bl[t][0] - rj.x, rj.x - bh[t][0]), 0.f);
+                            float dy = fmaxf(fmaxf(bl[t][1] - rj.y, rj.y - bh[t][1]), 0.f);
+                            float dz = fmaxf(fmaxf(bl[t][2] - rj.z, rj.z - bh[t][2]), 0.f);
+                            keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut * cut * 1.0001f + 1e-6f;
+                        }
+                        const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+                        if (keep) S::put2(buf[warp][t], cnt[t] + __popc(m & below), rj);
+                        cnt[t] += __popc(m);
+                        full |= cnt[t] >= 32;
+                    }
+                    if (full) sweep();
+                }
+            }
+            sweep();
+            if (act) S::finish2(p, st, lv.korder ? i : lv.kperm[i]);
+            if (kCount) {
+                int cn = act ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
+                unsigned long long sw = act ? swept : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    cn += __shfl_xor_sync(CRK_FULL_MASK, cn, o);
+                    sw += __shfl_xor_sync(CRK_FULL_MASK, sw, o);
+                }
+                if (lane == 0 && cn) atomicAdd(p.count, (unsigned long long)cn);
+                if (lane == 0 && p.swept) atomicAdd(p.swept, sw);
+            }
+        }
+    }
+}
+
 // Two 16-particle i-groups per warp with balanced sweeps: each half-warp has
 // a ring buffer of candidates; a sweep consumes the same number of entries
 // from both rings (as many as both have ready), so neither half idles while
@@ -2465,10 +2592,17 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
                 }
             }
         } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
-            if (p.count)
-                pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-            else
-                pair_kernel_sub<S, 16, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            if constexpr (S::kPair) {  // gravity stages: packed two-candidate sweeps
+                if (p.count)
+                    pair_kernel_sub_pair<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else
+                    pair_kernel_sub_pair<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            } else {
+                if (p.count)
+                    pair_kernel_sub<S, 16, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                else
+                    pair_kernel_sub<S, 16, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+            }
         } else if (ctx->variant[kernel_id] == CRK_VARIANT_RING16 && !S::kCons) {
             if constexpr (!S::kCons) {
                 if (p.count)
