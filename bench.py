@@ -596,18 +596,24 @@ def adjoint_chain(api, ctx, db, stream, peak_tflops, reps=2):
                                                              dvbar, dubar))
     ms["corrections_adjoint"], _ = timed(lambda: api.corrections_adjoint(ctx, lv, V, g["A"], g["B"], g["gA"],
                                                                          g["gB"]))
+    # the whole chain, forward and reverse, in kernel order
+    ms["chain"], _ = timed(lambda: api.hydro_chain_adjoint(ctx, lv, db, dvbar, dubar, forward=False))
     lv.free()
     fl = ADJOINT_FLOPS_PER_PAIR
     work = {"hydro_adjoint": fl["hydro_adjoint"] * pairs,
             "corrections_adjoint": (fl["corrections_adjoint_prep"] + fl["corrections_adjoint_sweep"]) * pairs}
+    work["chain"] = (24 + 135 + 31) * pairs + work["hydro_adjoint"] + work["corrections_adjoint"]
     tf = {k: work[k] / (ms[k] * 1e-3) / 1e12 for k in ms}
     return {"pairs_per_launch": pairs, "ms": {k: round(v, 4) for k, v in ms.items()},
             "pairs_per_s": {k: pairs / (v * 1e-3) for k, v in ms.items()},
             "tflops": tf, "frac_of_fp32_peak": {k: v / peak_tflops for k, v in tf.items()},
             "flops_per_pair": fl,
-            "note": "single C-ABI calls on caller-order inputs (gathers and scatters included), random "
-                    "cotangents; corrections_adjoint = preparation sweep (moments + FP64 reverse of the "
-                    "3x3 step) + gradient sweep; mean of %d calls after a warm-up" % reps}
+            "note": "hydro_adjoint, corrections_adjoint: single C-ABI calls on caller-order inputs "
+                    "(gathers and scatters included), random cotangents; corrections_adjoint = preparation "
+                    "sweep (moments + FP64 reverse of the 3x3 step) + gradient sweep; chain = "
+                    "crk_hydro_chain_adjoint, geometry -> corrections -> hydro forward and hydro -> "
+                    "corrections -> geometry adjoints in kernel order (work: the forward sweeps 24 + 135, "
+                    "the hydro forward is skipped, geometry adjoint 31); mean of %d calls after a warm-up" % reps}
 
 
 def batched_vs_plain(args, local, dist):

@@ -372,6 +372,26 @@ int crk_hydro_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params
                       float *vbar3, float *ubar, float *mbar, float *Vbar, float *rhobar, float *Abar, float *Bbar3,
                       float *gradAbar3, float *gradBbar9);
 
+/* Forward and reverse pass of the hydro chain on one set of leaves, with
+ * every intermediate in the library's kernel order (as crk_step): geometry,
+ * corrections, hydro (its outputs only when dvdt3 or dudt is given), then
+ * crk_hydro_adjoint, crk_corrections_adjoint and crk_geometry_adjoint chained,
+ * for the cotangents dvbar3[3n], dubar[n] of dv/dt and du/dt.  Returns the
+ * gradient of L = sum dvbar.dv/dt + dubar du/dt in the positions (xbar3[3n])
+ * and masses (mbar[n]) through V, rho and the corrections, and in the
+ * velocities (vbar3[3n]) and u (ubar[n]); every output may be NULL; caller
+ * order and layouts; h held fixed.  n_singular as for crk_corrections. */
+typedef struct {
+    const float *m, *v3, *u;       /* inputs */
+    const float *dvbar3, *dubar;   /* cotangents */
+    float *dvdt3, *dudt;           /* forward outputs, may be NULL */
+    float *xbar3, *mbar, *vbar3, *ubar;  /* gradients, may be NULL */
+    int32_t *n_singular;           /* may be NULL */
+} crk_chain_adjoint_io;
+
+int crk_hydro_chain_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp,
+                            const crk_chain_adjoint_io *io);
+
 /* One whole step of the path on one set of leaves, in this order: geometry,
  * corrections, hydro, gravity, gravity adjoint, geometry adjoint.  Inputs m,
  * v3, u (caller order, as for the single calls).  The intermediates stay in

@@ -330,6 +330,25 @@ def hydro_adjoint(ctx: Context, lv: Leaves, hp: HydroParams, m, v3, u, V, rho, A
     return out
 
 
+def hydro_chain_adjoint(ctx: Context, lv: Leaves, db: "DeviceBox", dvbar, dubar, forward: bool = True):
+    """Forward and reverse pass of geometry -> corrections -> hydro in the library's kernel order:
+    the gradients of sum dvbar.dv + dubar.du in x (3, n), m, v (3, n) and u, plus dv, du when
+    `forward`; also the singular count."""
+    n = lv.n
+    out = dict(x=ctx.empty(3, n), m=ctx.empty(n), v=ctx.empty(3, n), u=ctx.empty(n),
+               n_singular=torch.zeros(1, dtype=torch.int32, device=ctx.device))
+    if forward:
+        out["dv"], out["du"] = ctx.empty(3, n), ctx.empty(n)
+    io = N.crk_chain_adjoint_io(_f32(db.m, "m", n), _f32(db.v3, "v3", 3 * n), _f32(db.u, "u", n),
+                                _f32(dvbar, "dvbar", 3 * n), _f32(dubar, "dubar", n),
+                                out["dv"].data_ptr() if forward else None,
+                                out["du"].data_ptr() if forward else None, out["x"].data_ptr(), out["m"].data_ptr(),
+                                out["v"].data_ptr(), out["u"].data_ptr(), out["n_singular"].data_ptr())
+    hpc = db.hp.c()
+    ctx.check(N.lib().crk_hydro_chain_adjoint(ctx.handle, lv.handle, ctypes.byref(hpc), ctypes.byref(io)))
+    return out
+
+
 def grav_short(ctx: Context, lv: Leaves, gp: GravParams, m, count=False):
     n = lv.n
     a = ctx.empty(3, n)

@@ -47,8 +47,8 @@ struct crk_ctx {
     int num_sms = 0;
     std::string err;
     // growable scratch arena: one buffer per slot
-    static const int kSlots = 34;  // leaf build 0-16 and 19-31, radix sort 12-14, scan 15, queue 17, step 18,
-                                   // integrator 32, corrections adjoint 33
+    static const int kSlots = 35;  // leaf build 0-16 and 19-31, radix sort 12-14, scan 15, queue 17, step 18,
+                                   // integrator 32, corrections adjoint 33, adjoint chain 34
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     int64_t launches = 0;  // kernels this context has launched

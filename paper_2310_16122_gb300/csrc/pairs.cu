@@ -3122,6 +3122,104 @@ int crk_stage_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params 
     return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation, true);
 }
 
+namespace {
+// out[i] = a[i] + b[i] (+ c[i] when c is given), over cols columns of n
+__global__ void add_cols_kernel(int64_t n, int cols, float *__restrict__ out, const float *__restrict__ a,
+                                const float *__restrict__ b, const float *__restrict__ c) {
+    const int64_t total = n * cols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = c ? a[i] + b[i] + c[i] : a[i] + b[i];
+}
+}  // namespace
+
+int crk_hydro_chain_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp,
+                            const crk_chain_adjoint_io *io) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !hp || !io) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    const int64_t n = lv->n;
+    if (io->n_singular) CRK_CUDA(ctx, cudaMemsetAsync(io->n_singular, 0, sizeof(int32_t), ctx->stream));
+    if (n == 0) return CRK_OK;
+    if (!io->m || !io->v3 || !io->u || !io->dvbar3 || !io->dubar) return crk_fail(ctx, CRK_EINVAL, "null array");
+    // kernel-order columns
+    enum : int {
+        cm = 0, cv = 1, cu = 4, cdvb = 5, cdub = 8, cV = 9, crho = 10, cA = 11, cB = 12, cgA = 15, cgB = 18,
+        cdv = 27, cdu = 30, cxh = 31, cvb = 34, cub = 37, cmh = 38, cVh = 39, crhob = 40, cAb = 41, cBb = 42,
+        cgAb = 45, cgBb = 48, ccoef = 57, cxc = ccoef + kCorrCoef, cVc = cxc + 3, cxg = cVc + 1, cmg = cxg + 3,
+        cols = cmg + 1
+    };
+    float *w = (float *)crk_scratch(ctx, 34, sizeof(float) * cols * (size_t)n);
+    if (!w) return crk_fail(ctx, CRK_ENOMEM, "chain scratch");
+    auto C = [&](int k) { return w + (size_t)k * n; };
+    cudaStream_t st = ctx->stream;
+    const int g = crk_grid(n, 256);
+    auto col = [&](float *dst, const float *src, const int32_t *perm) {
+        permute_col_kernel<<<g, 256, 0, st>>>(n, perm, src, dst);
+        ++ctx->launches;
+    };
+    col(C(cm), io->m, lv->kperm);
+    col(C(cu), io->u, lv->kperm);
+    col(C(cdub), io->dubar, lv->kperm);
+    for (int c = 0; c < 3; ++c) {
+        col(C(cv) + (size_t)c * n, io->v3 + (size_t)c * n, lv->kperm);
+        col(C(cdvb) + (size_t)c * n, io->dvbar3 + (size_t)c * n, lv->kperm);
+    }
+    CRK_LAUNCH_CHECK(ctx, "chain inputs");
+    int rc;
+    {
+        GeomP p{C(cm), C(cV), C(crho), n, nullptr, nullptr};
+        if ((rc = run_stage<GeomStage>(ctx, lv, p, true, CRK_K_GEOMETRY, nullptr, true))) return rc;
+    }
+    {
+        CorrP p{C(cV), C(cA), C(cB), C(cgA), C(cgB), io->n_singular, n, nullptr};
+        if ((rc = run_stage<CorrStage>(ctx, lv, p, true, CRK_K_CORRECTIONS, nullptr, true))) return rc;
+    }
+    if (io->dvdt3 || io->dudt) {
+        HydroP p{C(cm), C(cv), C(cu), C(cV), C(crho), C(cA), C(cB), C(cgA), C(cgB), C(cdv), C(cdu), nullptr,
+                 hp->gamma, hp->alpha, hp->beta, hp->eta2, n, nullptr};
+        if ((rc = run_stage<HydroStage>(ctx, lv, p, true, CRK_K_HYDRO, nullptr, true))) return rc;
+    }
+    {
+        HydroAdjP p{C(cm),  C(cv),  C(cu),   C(cV),   C(crho),   C(cA),  C(cB),  C(cgA),     C(cgB),
+                    C(cdvb), C(cdub), C(cxh), C(cvb), C(cub), C(cmh), C(cVh), C(crhob), C(cAb),
+                    C(cBb), C(cgAb), C(cgBb), hp->gamma, hp->alpha, hp->beta, hp->eta2, n, nullptr, nullptr};
+        if ((rc = run_stage<HydroAdjStage>(ctx, lv, p, true, CRK_K_HYDRO, nullptr, true))) return rc;
+    }
+    {
+        CorrAdjP p{};
+        p.V = C(cV);
+        p.n = n;
+        p.Abar = C(cAb);
+        p.Bbar = C(cBb);
+        p.gAbar = C(cgAb);
+        p.gBbar = C(cgBb);
+        p.coef = C(ccoef);
+        if ((rc = run_stage<CorrAdjPrepStage>(ctx, lv, p, true, CRK_K_CORRECTIONS, nullptr, true))) return rc;
+        CorrAdjSweepP q{C(cV), C(ccoef), C(cxc), C(cVc), n, nullptr, nullptr};
+        if ((rc = run_stage<CorrAdjStage>(ctx, lv, q, true, CRK_K_CORRECTIONS, nullptr, true))) return rc;
+    }
+    const int ge = g < 8 * ctx->num_sms ? g : 8 * ctx->num_sms;
+    add_cols_kernel<<<ge, 256, 0, st>>>(n, 1, C(cVh), C(cVh), C(cVc), nullptr);  // Vbar = hydro + corrections
+    ++ctx->launches;
+    {
+        GeomAdjP p{C(cm), C(cV), C(crhob), C(cVh), C(cxg), C(cmg), n, nullptr};
+        if ((rc = run_stage<GeomAdjStage>(ctx, lv, p, true, CRK_K_GEOMETRY_ADJOINT, nullptr, true))) return rc;
+    }
+    add_cols_kernel<<<ge, 256, 0, st>>>(n, 3, C(cxh), C(cxh), C(cxc), C(cxg));  // xbar
+    add_cols_kernel<<<ge, 256, 0, st>>>(n, 1, C(cmh), C(cmh), C(cmg), nullptr);  // mbar
+    ctx->launches += 2;
+    CRK_LAUNCH_CHECK(ctx, "chain sums");
+    struct Out {
+        float *dst;
+        int src, comp;
+    } outs[] = {{io->dvdt3, cdv, 3}, {io->dudt, cdu, 1}, {io->xbar3, cxh, 3},
+                {io->mbar, cmh, 1},  {io->vbar3, cvb, 3}, {io->ubar, cub, 1}};
+    for (const Out &o : outs)
+        if (o.dst)
+            for (int c = 0; c < o.comp; ++c) col(o.dst + (size_t)c * n, C(o.src) + (size_t)c * n, lv->kinv);
+    CRK_LAUNCH_CHECK(ctx, "chain outputs");
+    return CRK_OK;
+}
+
 int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
                    const crk_step_io *io) {
     const int64_t n = lv->n;

@@ -72,6 +72,11 @@ class crk_advance_params(ctypes.Structure):
                 ("sig_beta", ctypes.c_float), ("limited", ctypes.c_int), ("gravity", ctypes.c_int)]
 
 
+class crk_chain_adjoint_io(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in (
+        "m", "v3", "u", "dvbar3", "dubar", "dvdt3", "dudt", "xbar3", "mbar", "vbar3", "ubar", "n_singular")]
+
+
 class crk_step_io(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "m", "v3", "u", "V", "rho", "A", "B", "gradA", "gradB", "dvdt3", "dudt", "conservation", "a3", "abar3",
@@ -111,6 +116,7 @@ SIGNATURES = {
     "crk_hydro_energy": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 14,
     "crk_timestep": [_P, _P, ctypes.c_float, ctypes.c_float, _P],
     "crk_corrections_adjoint": [_P] * 10,
+    "crk_hydro_chain_adjoint": [_P, _P, ctypes.POINTER(crk_hydro_params), ctypes.POINTER(crk_chain_adjoint_io)],
     "crk_hydro_adjoint": [_P, _P, ctypes.POINTER(crk_hydro_params)] + [_P] * 21,
     "crk_advance": [_P, _I64, ctypes.c_float] + [_P] * 8 + [ctypes.POINTER(crk_leaf_params),
                                                            ctypes.POINTER(crk_hydro_params),

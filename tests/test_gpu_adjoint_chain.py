@@ -149,3 +149,34 @@ def test_chain_gradient_through_autograd(api, name):
     errs = {k: rel_l2(got[k][gas], want[k][gas]) for k in want}
     print(name, {k: f"{e:.1e}" for k, e in errs.items()})
     assert max(errs.values()) <= 1e-4, errs
+
+
+def test_fused_chain_equals_autograd_chain(api):
+    """crk_hydro_chain_adjoint (kernel order throughout) against the single calls chained by autograd."""
+    from paper_2310_16122_gb300 import autograd as AG
+
+    b = _box("clustered24")
+    gas = b.species == 0
+    rng = np.random.default_rng(14)
+    dvbar = _t(np.where(gas[:, None], rng.normal(size=(b.n, 3)), 0.0).T)
+    dubar = _t(np.where(gas, rng.normal(size=b.n), 0.0))
+    ctx = api.Context(0)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    fused = api.hydro_chain_adjoint(ctx, lv, db, dvbar, dubar)
+    pos = torch.stack([db.x, db.y, db.z]).requires_grad_(True)
+    m = db.m.clone().requires_grad_(True)
+    v = db.v3.clone().requires_grad_(True)
+    u = db.u.clone().requires_grad_(True)
+    Vg, rhog = AG.geometry(pos, m, ctx, lv)
+    Ag, Bg, gAg, gBg = AG.corrections(pos, Vg, ctx, lv)
+    dv, du = AG.hydro(pos, m, v, u, Vg, rhog, Ag, Bg, gAg, gBg, ctx, lv, db.hp)
+    ((dv * dvbar).sum() + (du * dubar).sum()).backward()
+    torch.cuda.synchronize()
+    assert int(fused["n_singular"].cpu()) == 0
+    # forward outputs: the same kernels on the same pairs in the same order
+    assert torch.equal(fused["dv"], dv.detach()) and torch.equal(fused["du"], du.detach())
+    for k, ref in (("x", pos.grad), ("m", m.grad), ("v", v.grad), ("u", u.grad)):
+        e = rel_l2(fused[k].cpu().numpy(), ref.cpu().numpy())
+        print(k, f"{e:.1e}")
+        assert e <= 1e-6, (k, e)
