@@ -1,4 +1,4 @@
-"""Adjoint path (BASELINE config 3): autograd through grav_short and crk_geometry on GB300.
+"""Adjoint path (gravity and geometry): autograd through grav_short and crk_geometry on GB300.
 
 Loss = sum_i |a_grav,i|^2 + sum_gas rho_i on the clustered 2x32^3 box (25
 halos).  The gradients with respect to positions and masses come from the

@@ -1,4 +1,4 @@
-"""Batched form (BASELINE config 4 pattern): many boxes in one leaf build and one launch per kernel,
+"""Batched form (many independent boxes): many boxes in one leaf build and one launch per kernel,
 the whole step as a CUDA graph, and the kernel-variant autotuner.
 
 Checks: the batched leaves of every box equal the oracle's leaves of that box
