@@ -180,3 +180,38 @@ def test_fused_chain_equals_autograd_chain(api):
         e = rel_l2(fused[k].cpu().numpy(), ref.cpu().numpy())
         print(k, f"{e:.1e}")
         assert e <= 1e-6, (k, e)
+
+
+def test_adjoint_edge_cases(api):
+    """No particles, dark matter only, and a lone gas particle (singular moments, counted)."""
+    ctx = api.Context(0)
+    # no particles: every call succeeds and returns empty outputs
+    db = api.DeviceBox(W.random_box(0, 10.0, 0.5, 91))
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    e = torch.zeros(0, device="cuda")
+    gx, gV, ns = api.corrections_adjoint(ctx, lv, e, e, e.view(3, 0), e.view(3, 0), e.view(9, 0))
+    out = api.hydro_chain_adjoint(ctx, lv, db, e.view(3, 0), e)
+    torch.cuda.synchronize()
+    assert gx.numel() == 0 and int(ns.cpu()) == 0 and out["x"].numel() == 0
+    # dark matter only: the gas chain has nothing to differentiate
+    b = W.random_box(300, 12.0, 0.0, 92)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    rng = np.random.default_rng(3)
+    dvbar, dubar = _t(rng.normal(size=(3, b.n))), _t(rng.normal(size=b.n))
+    out = api.hydro_chain_adjoint(ctx, lv, db, dvbar, dubar)
+    torch.cuda.synchronize()
+    for k in ("x", "m", "v", "u", "dv", "du"):
+        assert torch.count_nonzero(out[k]).item() == 0, k
+    # a lone gas particle: its moment matrix is singular; counted, and the adjoint of the
+    # corrections leaves it out (no NaN in the gradient)
+    b = W.random_box(1, 12.0, 1.0, 93, h=0.5)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    V, _, _ = api.geometry(ctx, lv, db.m)
+    one = torch.ones(1, device="cuda")
+    gx, gV, ns = api.corrections_adjoint(ctx, lv, V, one, torch.ones(3, 1, device="cuda"),
+                                         torch.ones(3, 1, device="cuda"), torch.ones(9, 1, device="cuda"))
+    torch.cuda.synchronize()
+    assert int(ns.cpu()) == 1
+    assert torch.isfinite(gx).all() and torch.isfinite(gV).all()
