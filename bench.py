@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-advance", action="store_true", help="skip the timestep/integrator measurement")
     ap.add_argument("--no-adjoint-chain", action="store_true",
                     help="skip the corrections/hydro adjoint measurement")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the corrections/hydro adjoint measurement (--steps calls each) and print it")
     ap.add_argument("--advance-only", action="store_true",
                     help="run only the timestep/integrator measurement (--steps steps) and print it")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants")
@@ -250,6 +252,17 @@ def main():
     db = api.DeviceBox(box, device=f"cuda:{local}")
     gas = (db.species == 0).float()
     stream = ctx.stream
+    if args.adjoint_only:
+        # the adjoint row alone (for kernel launch lists of the adjoints); not the headline line
+        try:
+            f_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0))
+        except Exception:
+            f_max = 2070.0
+        peak = torch.cuda.get_device_properties(local).multi_processor_count * 128 * 2 * f_max * 1e6 / 1e12
+        if rank == 0:
+            print(json.dumps({"workload": box.name, "n": box.n,
+                              "adjoint_chain": adjoint_chain(api, ctx, db, stream, peak, reps=args.steps)}))
+        return
     if args.advance_only:
         # the timestep row alone (for kernel launch lists of crk_advance); not the headline line
         try:

@@ -738,14 +738,12 @@ struct CorrAdjPrepStage : CorrStage {
             m1b[a] -= Mi[0][a] * Bb[0] + Mi[1][a] * Bb[1] + Mi[2][a] * Bb[2];
             for (int b = 0; b < 3; ++b) Mib[a][b] -= Bb[a] * m1[b];
         }
-        double m2b[3][3];
+        // m2b = -Mi^T Mib Mi^T = -Mi (Mib Mi) (Mi symmetric): two 3x3 products (FP64 is 1/64 rate)
+        double T[3][3], m2b[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int b = 0; b < 3; ++b) T[c][b] = Mib[c][0] * Mi[0][b] + Mib[c][1] * Mi[1][b] + Mib[c][2] * Mi[2][b];
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double v = 0.0;
-                for (int c = 0; c < 3; ++c)
-                    for (int d = 0; d < 3; ++d) v += Mi[c][a] * Mib[c][d] * Mi[b][d];
-                m2b[a][b] = -v;
-            }
+            for (int b = 0; b < 3; ++b) m2b[a][b] = -(Mi[a][0] * T[0][b] + Mi[a][1] * T[1][b] + Mi[a][2] * T[2][b]);
         // polynomial coefficients.  dm2b enters as sum_{g,ab} dm2b[g][ab] (delta_ag x_b W +
         // delta_bg x_a W + x_a x_b x_g dWr) with the packed (a <= b) entries carrying both orders.
         double c[kCorrCoef];
