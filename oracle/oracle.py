@@ -31,14 +31,72 @@ _i32 = ctypes.POINTER(ctypes.c_int32)
 _i64 = ctypes.POINTER(ctypes.c_int64)
 
 
+def compile_c(src: str, out: str) -> str:
+    """gcc a copy of the oracle's C file into a shared library (FP64, OpenMP, no FP contraction)."""
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, OpenMP, no FP contraction)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+        compile_c(SRC, LIB)
     return LIB
+
+
+def bind(L):
+    """Declare the argument and result types of the oracle's exported functions on a loaded CDLL."""
+    L.orc_num_threads.restype = ctypes.c_int
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_wendland.argtypes = [ctypes.c_int64, _d, _d, _d, _d]
+    L.orc_grav_g.argtypes = [ctypes.c_int64, _d, ctypes.c_double, _d, _d, _d]
+    L.orc_gravity.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double, _d,
+                              _i64, ctypes.c_int64, ctypes.c_int, _d, _i64]
+    L.orc_gravity_adjoint.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, _d, _d, _i64, ctypes.c_int64, ctypes.c_int, _d, _d,
+                                      _i64]
+    L.orc_geometry.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
+                               ctypes.c_int, _d, _d, _i64]
+    L.orc_corrections.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
+                                  ctypes.c_int, _d, _d, _d, _d, _i64, _i64]
+    L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
+    L.orc_hydro_compatible.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                                       _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, _i64,
+                                       ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64]
+    L.orc_wendland2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d]
+    L.orc_corrections_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _d, _d, _d,
+                                          _d, _d, _d, _i64]
+    L.orc_hydro_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _d, _d] + [_d] * 10
+    L.orc_energy_share.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.orc_energy_share.restype = ctypes.c_double
+    L.orc_extras.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_double,
+                             _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
+    L.orc_geometry_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, ctypes.c_double, _i64,
+                                       ctypes.c_int64, ctypes.c_int, _d, _d]
+    L.orc_leaves_mesh.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_double, ctypes.c_int, _i32, _i32]
+    L.orc_leaves_rcb.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_int, _i32, _i32, ctypes.c_int64, _i64]
+    L.orc_leaf_pairs.argtypes = [ctypes.c_int64, _i32, _i32, _d, _u8, _d, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_double, _i32, ctypes.c_int64, _i32, _i32, ctypes.c_int64, _i64]
+    L.orc_mark_neighbours.argtypes = [ctypes.c_int64, _d, _u8, _d, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, _u8, _u8]
+    for name in ("orc_mark_neighbours", "orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections",
+                 "orc_hydro", "orc_extras",
+                 "orc_geometry_adjoint", "orc_leaves_mesh", "orc_leaves_rcb", "orc_leaf_pairs"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+def load(path: str):
+    """Load and bind an oracle library built from a (possibly modified) copy of crk_oracle.c."""
+    return bind(ctypes.CDLL(path))
 
 
 def lib():
@@ -46,50 +104,7 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(LIB)
-            L.orc_num_threads.restype = ctypes.c_int
-            L.orc_set_threads.argtypes = [ctypes.c_int]
-            L.orc_wendland.argtypes = [ctypes.c_int64, _d, _d, _d, _d]
-            L.orc_grav_g.argtypes = [ctypes.c_int64, _d, ctypes.c_double, _d, _d, _d]
-            L.orc_gravity.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double, _d,
-                                      _i64, ctypes.c_int64, ctypes.c_int, _d, _i64]
-            L.orc_gravity_adjoint.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_double,
-                                              ctypes.c_double, _d, _d, _i64, ctypes.c_int64, ctypes.c_int, _d, _d,
-                                              _i64]
-            L.orc_geometry.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
-                                       ctypes.c_int, _d, _d, _i64]
-            L.orc_corrections.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _i64, ctypes.c_int64,
-                                          ctypes.c_int, _d, _d, _d, _d, _i64, _i64]
-            L.orc_hydro.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
-                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
-            L.orc_hydro_compatible.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
-                                               _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, _i64,
-                                               ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64]
-            L.orc_wendland2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d]
-            L.orc_corrections_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, ctypes.c_double, _d, _d, _d,
-                                                  _d, _d, _d, _i64]
-            L.orc_hydro_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
-                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                            ctypes.c_double, _d, _d] + [_d] * 10
-            L.orc_energy_share.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
-            L.orc_energy_share.restype = ctypes.c_double
-            L.orc_extras.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_double,
-                                     _i64, ctypes.c_int64, ctypes.c_int, _d, _d, _i64]
-            L.orc_geometry_adjoint.argtypes = [ctypes.c_int64, _d, _u8, _d, _d, _d, _d, ctypes.c_double, _i64,
-                                               ctypes.c_int64, ctypes.c_int, _d, _d]
-            L.orc_leaves_mesh.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_double, ctypes.c_int, _i32, _i32]
-            L.orc_leaves_rcb.argtypes = [ctypes.c_int64, _d, _u8, ctypes.c_int, _i32, _i32, ctypes.c_int64, _i64]
-            L.orc_leaf_pairs.argtypes = [ctypes.c_int64, _i32, _i32, _d, _u8, _d, ctypes.c_double, ctypes.c_int,
-                                         ctypes.c_double, _i32, ctypes.c_int64, _i32, _i32, ctypes.c_int64, _i64]
-            L.orc_mark_neighbours.argtypes = [ctypes.c_int64, _d, _u8, _d, ctypes.c_double, ctypes.c_double,
-                                              ctypes.c_int, _u8, _u8]
-            for name in ("orc_mark_neighbours", "orc_gravity", "orc_gravity_adjoint", "orc_geometry", "orc_corrections",
-                         "orc_hydro", "orc_extras",
-                         "orc_geometry_adjoint", "orc_leaves_mesh", "orc_leaves_rcb", "orc_leaf_pairs"):
-                getattr(L, name).restype = ctypes.c_int
-            _lib = L
+            _lib = load(LIB)
     return _lib
 
 
