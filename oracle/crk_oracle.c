@@ -1070,42 +1070,60 @@ static int moments_bar(const Moments *mo, double Abar, const double *Bbar_in, co
     return 0;
 }
 
-/* The moment terms of one pair weighted by moment cotangents mb (the V_j   */
-/* factor left out): T(x) = S0(x) W + S1(x) dWr, with                        */
-/*   S0 = m0b + m1b.x + x^T m2b x + sum_a dm1b[a][a]                         */
-/*        + sum_ab dm2b[a][a][b] x_b + sum_ab dm2b[b][a][b] x_a               */
-/*   S1 = dm0b.x + sum_ga dm1b[g][a] x_a x_g + sum_gab dm2b[g][a][b] x_a x_b x_g */
-/* and its gradient in x (grad W = dWr x, grad dWr = ddWr x).               */
+/* One pair's moment terms weighted by the moment cotangents mb, and their   */
+/* gradient in the separation x = x_i - x_j, written out term by term from    */
+/* the definitions in orc_corrections (per unit V_j):                          */
+/*   m0: W    m1^a: W x^a    m2^ab: W x^a x^b    dm0_g: dW_g                   */
+/*   dm1_g^a: d_ag W + x^a dW_g                                                */
+/*   dm2_g^ab: d_ag x^b W + d_bg x^a W + x^a x^b dW_g                          */
+/* with dW_g = (dW/dr/r) x_g, so dW/dx_c = dWr x_c and                        */
+/* d(dW_g)/dx_c = ddWr x_c x_g + d_gc dWr, ddWr = (d[(dW/dr)/r]/dr)/r.          */
 static double moment_term(const Moments *mb, const double x[3], double W, double dWr, double ddWr, double grad[3]) {
-    double S0 = mb->m0, S1 = 0.0, gS0[3] = {0, 0, 0}, gS1[3] = {0, 0, 0};
+    double dW[3], gW[3], gdW[3][3];
+    for (int g = 0; g < 3; ++g) {
+        dW[g] = dWr * x[g];
+        gW[g] = dWr * x[g];
+        for (int c = 0; c < 3; ++c) gdW[g][c] = ddWr * x[c] * x[g] + (g == c ? dWr : 0.0);
+    }
+    double T = 0.0;
+    for (int c = 0; c < 3; ++c) grad[c] = 0.0;
+    /* m0 */
+    T += mb->m0 * W;
+    for (int c = 0; c < 3; ++c) grad[c] += mb->m0 * gW[c];
     for (int a = 0; a < 3; ++a) {
-        S0 += mb->m1[a] * x[a] + mb->dm1[a][a];
-        gS0[a] += mb->m1[a];
-        S1 += mb->dm0[a] * x[a];
-        gS1[a] += mb->dm0[a];
+        /* m1^a */
+        T += mb->m1[a] * W * x[a];
+        for (int c = 0; c < 3; ++c) grad[c] += mb->m1[a] * (gW[c] * x[a] + (a == c ? W : 0.0));
         for (int b = 0; b < 3; ++b) {
-            S0 += mb->m2[a][b] * x[a] * x[b];
-            gS0[a] += mb->m2[a][b] * x[b];
-            gS0[b] += mb->m2[a][b] * x[a];
-            S0 += mb->dm2[a][a][b] * x[b] + mb->dm2[b][a][b] * x[a];
-            gS0[b] += mb->dm2[a][a][b];
-            gS0[a] += mb->dm2[b][a][b];
-            /* dm1b[g = a][a' = b] x_b x_a */
-            S1 += mb->dm1[a][b] * x[b] * x[a];
-            gS1[b] += mb->dm1[a][b] * x[a];
-            gS1[a] += mb->dm1[a][b] * x[b];
-            for (int c = 0; c < 3; ++c) {
-                /* dm2b[g = a][b][c] x_b x_c x_a */
-                double w = mb->dm2[a][b][c];
-                S1 += w * x[b] * x[c] * x[a];
-                gS1[a] += w * x[b] * x[c];
-                gS1[b] += w * x[a] * x[c];
-                gS1[c] += w * x[a] * x[b];
+            /* m2^ab */
+            T += mb->m2[a][b] * W * x[a] * x[b];
+            for (int c = 0; c < 3; ++c)
+                grad[c] += mb->m2[a][b] *
+                           (gW[c] * x[a] * x[b] + W * ((a == c ? x[b] : 0.0) + (b == c ? x[a] : 0.0)));
+        }
+    }
+    for (int g = 0; g < 3; ++g) {
+        /* dm0_g */
+        T += mb->dm0[g] * dW[g];
+        for (int c = 0; c < 3; ++c) grad[c] += mb->dm0[g] * gdW[g][c];
+        for (int a = 0; a < 3; ++a) {
+            /* dm1_g^a */
+            T += mb->dm1[g][a] * ((a == g ? W : 0.0) + x[a] * dW[g]);
+            for (int c = 0; c < 3; ++c)
+                grad[c] += mb->dm1[g][a] *
+                           ((a == g ? gW[c] : 0.0) + (a == c ? dW[g] : 0.0) + x[a] * gdW[g][c]);
+            for (int b = 0; b < 3; ++b) {
+                /* dm2_g^ab */
+                const double w = mb->dm2[g][a][b];
+                T += w * ((a == g ? x[b] * W : 0.0) + (b == g ? x[a] * W : 0.0) + x[a] * x[b] * dW[g]);
+                for (int c = 0; c < 3; ++c)
+                    grad[c] += w * ((a == g ? (b == c ? W : 0.0) + x[b] * gW[c] : 0.0) +
+                                    (b == g ? (a == c ? W : 0.0) + x[a] * gW[c] : 0.0) +
+                                    ((a == c ? x[b] : 0.0) + (b == c ? x[a] : 0.0)) * dW[g] + x[a] * x[b] * gdW[g][c]);
             }
         }
     }
-    for (int p = 0; p < 3; ++p) grad[p] = gS0[p] * W + S0 * dWr * x[p] + gS1[p] * dWr + S1 * ddWr * x[p];
-    return S0 * W + S1 * dWr;
+    return T;
 }
 
 /* Reverse mode of orc_corrections for the cotangents Abar[n], Bbar[3n],     */

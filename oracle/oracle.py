@@ -354,7 +354,7 @@ def _chain(I: Inputs, limited):
 
 
 def advance(I: Inputs, gamma, alpha, beta, eta2, cfl, dt_max, sig_beta=3.0, limited=False, gravity_on=False,
-            dt=None):
+            dt=None, fp32_state=False):
     """One two-stage kick-drift step with the compatible energy update.
 
     Stage 1 at t^n: geometry, corrections (Extras when limited), Acceleration
@@ -363,25 +363,35 @@ def advance(I: Inputs, gamma, alpha, beta, eta2, cfl, dt_max, sig_beta=3.0, limi
     predicted state: the same chain, Acceleration a_p; kick v1 = v + dt a_p;
     Energy on v* = (v + v1)/2 with the predicted state's forces; u1 = u + dt du;
     drift x1 = x + dt v*.  Gas feels hydro (+ gravity), dark matter gravity
-    only; h and m stay fixed.  Returns (Inputs at t^n+1, dt)."""
+    only; h and m stay fixed.  Returns (Inputs at t^n+1, dt).
+
+    fp32_state: round the states a single-precision code stores (the predicted
+    v_p, u_p, x_p, then v1, v*, u1, x1) to FP32 where it stores them, so that a
+    comparison with such a code sees its pair arithmetic, not its storage
+    precision; the arithmetic between the stores stays FP64."""
+    r32 = (lambda a: np.asarray(a, np.float32).astype(np.float64)) if fp32_state else (lambda a: a)
+
+    def wrap32(x):
+        y = r32(_wrap(x, I.L))
+        return np.where(y >= I.L, 0.0, y)
     hp = (gamma, alpha, beta, eta2)
     V, rho, A, B, gA, gB, dvg = _chain(I, limited)
     dv0, du0, vsig = hydro_compatible(I, V, rho, A, B, gA, gB, *hp, vstar=I.v, sig_beta=sig_beta, dvg=dvg)
     a0 = dv0 + (gravity(I)[0] if gravity_on else 0.0)
     if dt is None:
         dt = timestep(I, vsig, cfl, dt_max)
-    vp = I.v + 0.5 * dt * a0
-    up = I.u + 0.5 * dt * du0
-    xp = _wrap(I.pos + 0.5 * dt * vp, I.L)
+    vp = r32(I.v + 0.5 * dt * a0)
+    up = r32(I.u + 0.5 * dt * du0)
+    xp = wrap32(I.pos + 0.5 * dt * vp)
     Ip = Inputs(xp, I.species, I.m, I.h, up, vp, I.L, I.r_cut, I.eps, I.poly)
     V, rho, A, B, gA, gB, dvg = _chain(Ip, limited)
     dvp, _, _ = hydro_compatible(Ip, V, rho, A, B, gA, gB, *hp, sig_beta=sig_beta, dvg=dvg)
     ap = dvp + (gravity(Ip)[0] if gravity_on else 0.0)
-    v1 = I.v + dt * ap
-    vstar = 0.5 * (I.v + v1)
+    v1 = r32(I.v + dt * ap)
+    vstar = r32(0.5 * (I.v + v1))
     _, du, _ = hydro_compatible(Ip, V, rho, A, B, gA, gB, *hp, vstar=vstar, sig_beta=sig_beta, dvg=dvg)
-    u1 = I.u + dt * du
-    x1 = _wrap(I.pos + dt * vstar, I.L)
+    u1 = r32(I.u + dt * du)
+    x1 = wrap32(I.pos + dt * vstar)
     return Inputs(x1, I.species, I.m, I.h, u1, v1, I.L, I.r_cut, I.eps, I.poly), float(dt)
 
 
