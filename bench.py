@@ -38,6 +38,11 @@ FLOPS_PER_PAIR = {"geometry": 24, "corrections": 135, "hydro": 160, "gravity": 2
 MUFU_PER_PAIR = {"geometry": 2, "corrections": 2, "hydro": 3, "gravity": 1, "gravity_adjoint": 1,
                  "geometry_adjoint": 2}
 STAGES = ["leaves", "geometry", "corrections", "hydro", "gravity", "gravity_adjoint", "geometry_adjoint"]
+# DRAM bytes (read + write) per launch of a kernel in one launch shape (workload, kernel, variant,
+# depth), from one ncu capture of the current build (dram__bytes_read.sum + dram__bytes_write.sum;
+# the summaries under profiles/ give the commands).  A shape not captured since its kernel last
+# changed has no entry, and the bench line then reports traffic null.
+TRAFFIC = {}
 
 
 def parse():
@@ -50,7 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trace-leaves", action="store_true", help="after timing, print leaf-build phase times")
-    ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8, 4 ring16)")
+    ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8, 4 ring16, 5-7 half-warp, "
+                                                     "8 split8)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Extras-chain measurement")
     ap.add_argument("--no-advance", action="store_true", help="skip the timestep/integrator measurement")
@@ -214,12 +220,46 @@ def cpu_baseline(box, seconds=10.0):
         dt1 = time.perf_counter() - t0
     finally:
         O.set_threads(cores)
-    return {"value": r["pairs"] / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+    return r, s, {"value": r["pairs"] / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"{s.size} random i-particles of the same box through the oracle's sampled chain (geometry "
                       f"on their two-hop gas neighbourhood, corrections one-hop, hydro, gravity on the gravity "
                       f"neighbourhood, gravity adjoint); {r['pairs']} pairs in {dt:.1f} s",
             "one_core": {"value": r1["pairs"] / dt1, "unit": "pairs/s", "cores": 1,
                          "sample": f"{s1.size} of the same particles; {r1['pairs']} pairs in {dt1:.1f} s"}}
+
+
+def error_stats(got, ref):
+    """E = sqrt(sum|d|^2 / sum|ref|^2) and the per-particle e_i = |d_i| / (|ref_i| + 0.01 rms|ref|)."""
+    import numpy as np
+
+    r = np.asarray(ref, np.float64).reshape(len(ref), -1)
+    g = np.asarray(got, np.float64).reshape(len(ref), -1)
+    d = np.linalg.norm(g - r, axis=1)
+    a = np.linalg.norm(r, axis=1)
+    e = d / (a + 0.01 * float(np.sqrt(np.mean(a * a))) + 1e-300)
+    return {"E": float(np.sqrt(np.sum(d * d) / max(np.sum(a * a), 1e-300))), "median": float(np.median(e)),
+            "p99": float(np.percentile(e, 99)), "max": float(e.max()), "n": int(len(e))}
+
+
+def sample_errors(api, ctx, db, box, ref, sample):
+    """Error of every step output against the oracle's sampled chain (the cpu_baseline sample):
+    one untimed crk_step with every intermediate returned, on fresh leaves."""
+    import torch
+
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    io = api.StepIO(ctx, db)
+    api.step(ctx, lv, db, io)
+    torch.cuda.synchronize()
+    gas_s = sample[box.species[sample] == 0]
+    T = lambda t: t.cpu().numpy().T if t.dim() == 2 else t.cpu().numpy()
+    out = {}
+    for k, t in (("acc", io.acc), ("gx", io.gx_grav), ("gm", io.gm_grav)):
+        out[k] = error_stats(T(t)[sample], ref[k][sample])
+    for k, t in (("dv", io.dv), ("du", io.du), ("V", io.V), ("rho", io.rho), ("A", io.A), ("B", io.B),
+                 ("gA", io.gA), ("gB", io.gB)):
+        out[k] = error_stats(T(t)[gas_s], ref[k][gas_s])
+    lv.free()
+    return {"sample": f"{sample.size} particles of the cpu_baseline sample ({gas_s.size} gas)", "outputs": out}
 
 
 def main():
@@ -293,10 +333,11 @@ def main():
     if not args.no_tune and not args.variants:
         # untimed: the autotuner picks each kernel's variant on this workload's leaves
         lv_t = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
-        io_t = api.StepIO(ctx, db)
+        io_t = api.StepIO(ctx, db, extras=True)
         tuning = api.autotune(ctx, lv_t, db, io_t, reps=2)
         del lv_t, io_t
         variants = {k: ctx.get_variant(k) for k in native.KERNELS}
+    launch = {k: dict(zip(("persistent", "depth"), ctx.get_launch(k))) for k in native.KERNELS}
     # counting step (untimed): pair counts of every kernel
     lv_c = step(count=True)
     n_leaves = lv_c.n_leaves
@@ -407,12 +448,7 @@ def main():
     kern = {s: v for s, v in per_stage.items() if s in FLOPS_PER_PAIR}
     dom = max(kern, key=kern.get)
     achieved = FLOPS_PER_PAIR[dom] * pairs[dom] / (kern[dom] * 1e-3) / 1e12
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = tr.get(args.workload, {}).get(dom)
-    except Exception:
-        pass
+    traffic = TRAFFIC.get((args.workload, dom, variants.get(dom), launch.get(dom, {}).get("depth")))
     f_med = float(peaks.get("clocks_under_load", {}).get("sm_mhz_median", f_max))
     f_run = float(clk.get("sm_mhz") or f_max)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -435,7 +471,7 @@ def main():
                        "l2": "inputs (~%.1f GB) larger than L2 (129 MB)" % (h2d / 1e9)},
             "pairs_per_step": pairs, "candidates_per_step": swept, "in_range_fraction": useful,
             "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
-            "variants": variants,
+            "variants": variants, "launch": launch,
             "autotune_ms": tuning["ms"] if tuning else None,
             "kernels_tflops": all_flops / (kern_ms * 1e-3) / 1e12,
             "roofline": roofline, "clocks": clk, "gpu_launches": launches,
@@ -461,14 +497,16 @@ def main():
             line["adjoint_chain"] = {"error": repr(e)}
     if not args.no_batched:
         try:
-            line["batched_vs_plain"] = batched_vs_plain(args, local, dist)
+            line["batched_vs_plain"] = batched_vs_plain(args, local, dist, peak_tflops)
         except Exception as e:  # reported, never silent
             line["batched_vs_plain"] = {"error": repr(e)}
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline(box)
+            ref, sample, line["cpu_baseline"] = cpu_baseline(box)
+            line["errors"] = sample_errors(api, ctx, db, box, ref, sample)
         except Exception as e:  # reported, never silent
-            line["cpu_baseline"] = {"value": None, "error": repr(e)}
+            line.setdefault("cpu_baseline", {"value": None, "error": repr(e)})
+            line["errors"] = {"error": repr(e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -642,12 +680,24 @@ def adjoint_chain(api, ctx, db, stream, peak_tflops, reps=2):
                     "the hydro forward is skipped, geometry adjoint 31); mean of %d calls after a warm-up" % reps}
 
 
-def batched_vs_plain(args, local, dist):
-    """The many-box workload (96 boxes, sides log-uniform in [12, 48]) as per-box plain launches
-    and as one batched form; same kernels, same pairs, same accuracy."""
+def batched_vs_plain(args, local, dist, peak_tflops):
+    """The many-box workload (96 boxes, sides log-uniform in [12, 48]): per-box plain launches
+    against the batched form, the same kernels in the same launch shapes (autotuned on the batch).
+
+    plain:   per box, a leaf build and a crk_step (separate launches);
+    batched: one CUDA graph replayed per step, holding the capture-safe leaf rebuild of all boxes
+             and one crk_step over all boxes (every pair kernel one launch over all boxes, in the
+             tuned launch shape); also with every pair kernel persistent, and eagerly.
+    Per-kernel times of the batched step come from crk_step_profile (CUDA events on the context
+    stream around each stage) on eager steps in the same launch shapes; the leaf rebuild is timed
+    the same way.  The roofline block is the dominant kernel's algorithmic FP32 rate against the
+    FP32 peak, and the whole step's algorithmic rate (all kernels' flops / graph step time)."""
+    import ctypes as _ct
+
+    import numpy as np
     import torch
 
-    from paper_2310_16122_gb300 import api, workloads as W
+    from paper_2310_16122_gb300 import api, native, workloads as W
 
     t_gen = time.perf_counter()
     boxes = W.batched(args.batched_boxes)
@@ -658,27 +708,38 @@ def batched_vs_plain(args, local, dist):
     dbt = api.DeviceBatch(boxes, device=f"cuda:{local}")
     iot = api.StepIO(ctx, dbt)
     stream = ctx.stream
+    tuned = None
+    if not args.no_tune and not args.variants:
+        lv_t = api.build_leaves_batch(ctx, dbt)
+        tuned = api.tune(ctx, lv_t, dbt, api.StepIO(ctx, dbt, extras=True), reps=2)
+        lv_t.free()
+    shapes = {k: {"variant": ctx.get_variant(k), **dict(zip(("persistent", "depth"), ctx.get_launch(k)))}
+              for k in native.KERNELS}
 
     def plain_step(count=False):
         for db, io in zip(dbs, ios):
             lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
             api.step(ctx, lv, db, io, count)
 
-    def batched_step(count=False):
+    def eager_batched_step(count=False):
         lv = api.build_leaves_batch(ctx, dbt)
         api.step(ctx, lv, dbt, iot, count)
 
-    def pairs(c):
-        c = c.cpu().numpy()
-        return int(2 * (c[0] + c[1] + c[2]))
-
     plain_step(count=True)
-    batched_step(count=True)
+    eager_batched_step(count=True)
     torch.cuda.synchronize()
-    p_plain = sum(pairs(io.pair_count) for io in ios)
-    p_batch = pairs(iot.pair_count)
-    res = {}
-    for name, fn in (("plain", plain_step), ("batched", batched_step)):
+    per_kernel_pairs = {"geometry": int(iot.pair_count[0]), "corrections": int(iot.pair_count[1]),
+                        "hydro": int(iot.pair_count[1]), "gravity": int(iot.pair_count[2]),
+                        "gravity_adjoint": int(iot.pair_count[2]), "geometry_adjoint": int(iot.pair_count[0])}
+    c = np.sum([io.pair_count.cpu().numpy() for io in ios], axis=0)
+    p_plain = int(2 * (c[0] + c[1] + c[2]))
+    p_batch = sum(per_kernel_pairs.values())
+    # the same outputs, box by box
+    same = all(torch.equal(io.acc, iot.acc[:, int(dbt.box_start[k]):int(dbt.box_start[k + 1])]) and
+               torch.equal(io.dv, iot.dv[:, int(dbt.box_start[k]):int(dbt.box_start[k + 1])])
+               for k, io in enumerate(ios))
+
+    def timed(fn):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
@@ -688,34 +749,76 @@ def batched_vs_plain(args, local, dist):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        res[name] = e0.elapsed_time(e1) / args.steps
-    # kernel part only (leaves built once): eager crk_step vs CUDA-graph replay on a side stream
-    s2 = torch.cuda.Stream(device=f"cuda:{local}")
-    with torch.cuda.stream(s2):
-        gctx = api.Context(local, stream=s2)
-        lv = api.build_leaves_batch(gctx, dbt)
-        g = api.StepGraph(gctx, lv, dbt, iot)
-        for label, fn in (("eager", lambda: api.step(gctx, lv, dbt, iot)), ("graph", g.launch)):
-            for _ in range(args.warmup):
-                fn()
-            s2.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s2)
-            for _ in range(args.steps):
-                fn()
-            e1.record(s2)
-            s2.synchronize()
-            res["kernels_" + label] = e0.elapsed_time(e1) / args.steps
-        g.close()
+        return e0.elapsed_time(e1) / args.steps
+
+    res = {"plain": timed(plain_step), "batched_eager": timed(eager_batched_step)}
+    # the batched driver: one graph of rebuild + step, tuned launch shapes, then all persistent
+    lv_g = api.build_leaves_batch(ctx, dbt)
+    io_g = api.StepIO(ctx, dbt, outputs=False)
+    g = api.RebuildStepGraph(ctx, lv_g, dbt, io_g)
+    res["batched_graph"] = timed(g.launch)
+    status = lv_g.status()
+    g.close()
+    keep = {k: (ctx.get_variant(k), ctx.get_launch(k)) for k in native.KERNELS}
+    ctx.set_persistent(True)
+    g = api.RebuildStepGraph(ctx, lv_g, dbt, io_g)
+    res["batched_graph_persistent"] = timed(g.launch)
+    status |= lv_g.status()
+    g.close()
+    for k, (v, (pm, d)) in keep.items():
+        ctx.set_launch(k, pm, d)
+    # per-kernel times of the batched step in the tuned shapes (eager, profiled), and the rebuild
+    reps = max(args.steps, 1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ctx.check(native.lib().crk_step_profile(ctx.handle, reps))
+    t_rebuild = 0.0
+    for _ in range(reps):
+        ev[0].record(stream)
+        api.rebuild_leaves(ctx, lv_g, dbt)
+        ev[1].record(stream)
+        api.step(ctx, lv_g, dbt, io_g)
+        torch.cuda.synchronize()
+        t_rebuild += ev[0].elapsed_time(ev[1]) / reps
+    prof = (_ct.c_float * 7)()
+    nprof = _ct.c_int(0)
+    ctx.check(native.lib().crk_step_profile_read(ctx.handle, prof, _ct.byref(nprof)))
+    ctx.check(native.lib().crk_step_profile(ctx.handle, 0))
+    stage_ms = {"leaves_rebuild": round(t_rebuild, 4)}
+    for i, s_ in enumerate(STAGES[1:]):
+        stage_ms[s_] = round(float(prof[i]), 4)
+    stage_ms["outputs"] = round(float(prof[6]), 4)
+    tf = {k: FLOPS_PER_PAIR[k] * per_kernel_pairs[k] / (stage_ms[k] * 1e-3) / 1e12 for k in FLOPS_PER_PAIR}
+    dom = max(FLOPS_PER_PAIR, key=lambda k: stage_ms[k])
+    all_flops = sum(FLOPS_PER_PAIR[k] * per_kernel_pairs[k] for k in FLOPS_PER_PAIR)
+    best_graph = min(res["batched_graph"], res["batched_graph_persistent"])
     n_total = sum(b.n for b in boxes)
     return {"workload": f"{len(boxes)} boxes, sides 12-48 log-uniform, {n_total} particles",
-            "pairs_per_step": p_batch, "pairs_equal": p_plain == p_batch,
+            "pairs_per_step": p_batch, "pairs_equal": p_plain == p_batch, "outputs_equal": bool(same),
             "plain": {"ms_per_step": res["plain"], "value": p_plain / (res["plain"] * 1e-3),
-                      "form": "per box: leaf build + crk_step (separate launches)"},
-            "batched": {"ms_per_step": res["batched"], "value": p_batch / (res["batched"] * 1e-3),
-                        "form": "one multi-box leaf build + one crk_step over all boxes"},
-            "speedup": res["plain"] / res["batched"],
-            "kernels_ms": {"eager": res["kernels_eager"], "graph": res["kernels_graph"]},
+                      "form": "per box: leaf build + crk_step (separate launches), tuned launch shapes"},
+            "batched": {"ms_per_step": res["batched_graph"], "value": p_batch / (res["batched_graph"] * 1e-3),
+                        "form": "one CUDA graph per step: capture-safe leaf rebuild of all boxes + one crk_step "
+                                "over all boxes, tuned launch shapes", "leaves_status": status},
+            "batched_persistent": {"ms_per_step": res["batched_graph_persistent"],
+                                   "value": p_batch / (res["batched_graph_persistent"] * 1e-3),
+                                   "form": "the same graph with every pair kernel persistent (4 blocks per SM, "
+                                           "atomic work queue)"},
+            "batched_eager": {"ms_per_step": res["batched_eager"],
+                              "value": p_batch / (res["batched_eager"] * 1e-3),
+                              "form": "one multi-box leaf build (host reads back sizes) + one crk_step, eager"},
+            "speedup": res["plain"] / best_graph,
+            "launch_shapes": shapes, "tuning_ms": {k: r["ms"] for k, r in tuned.items()} if tuned else None,
+            "stage_ms": stage_ms, "pairs_per_launch": per_kernel_pairs,
+            "tflops": {k: round(v, 3) for k, v in tf.items()},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": tf[dom], "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": tf[dom] / peak_tflops, "traffic": None,
+                         "step_achieved": all_flops / (best_graph * 1e-3) / 1e12,
+                         "step_frac": all_flops / (best_graph * 1e-3) / 1e12 / peak_tflops,
+                         "kernels_frac": all_flops / (sum(stage_ms[k] for k in FLOPS_PER_PAIR) * 1e-3) / 1e12
+                         / peak_tflops,
+                         "note": "frac: dominant kernel of the batched step (eager, tuned shapes, CUDA events); "
+                                 "step_frac: every kernel's algorithmic flops over the whole graph step "
+                                 "(leaf rebuild included); kernels_frac: over the pair kernels' time only"},
             "generation_s": t_gen}
 
 

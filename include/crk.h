@@ -115,25 +115,42 @@ int crk_set_trace(crk_ctx *ctx, int on);
 #define CRK_K_GRAVITY_ADJOINT 4
 #define CRK_K_GEOMETRY_ADJOINT 5
 #define CRK_K_EXTRAS 6
+#define CRK_K_ACCEL 7  /* the Acceleration pass (crk_hydro_accel, and inside crk_advance) */
+#define CRK_K_ENERGY 8 /* the Energy pass (crk_hydro_energy, and inside crk_advance) */
+#define CRK_N_KERNELS 9
 #define CRK_VARIANT_LISTS 0
 #define CRK_VARIANT_TILES 1
 #define CRK_VARIANT_TILES16 2 /* tiles with two 16-particle i-groups per warp */
 #define CRK_VARIANT_TILES8 3  /* tiles with four 8-particle i-groups per warp */
 #define CRK_VARIANT_RING16 4  /* two 16-particle i-groups per warp, balanced ring-buffer sweeps
                                  (every kernel but hydro, which falls back to TILES) */
-/* the paper's half-warp leaf-pair scheme (Sec. 5.3), gravity kernels only: lanes 0-15 hold 16
- * particles of leaf A, lanes 16-31 16 of leaf B, and the pair is evaluated in both directions
- * in one step; partial sums are added atomically.  The partner's particle arrives by register
- * shuffle, through shared memory, or by a second load.  The gas kernels run tiles instead. */
+/* the paper's half-warp leaf-pair scheme (Sec. 5.3), for the gravity kernels and the hydro
+ * passes (crk_hydro, Acceleration, Energy): lanes 0-15 hold 16 particles of leaf A, lanes 16-31
+ * 16 of leaf B, and the pair is evaluated in both directions in one step; partial sums are
+ * added atomically (the hydro passes then take their conservation sums from the finished
+ * outputs).  The partner's particle arrives by register shuffle (Sec. 5.3.1), through shared
+ * memory (Sec. 5.3.2), or by a second load.  The other gas kernels run tiles instead. */
 #define CRK_VARIANT_HALFWARP_SHFL 5
 #define CRK_VARIANT_HALFWARP_SMEM 6
 #define CRK_VARIANT_HALFWARP_LOAD 7
-#define CRK_N_VARIANTS 8
+/* gravity kernels: the candidates of each 32-particle group compacted once, then swept once per
+ * 8-particle sub-cell (only those within the cut of its box) by 4 lanes per particle */
+#define CRK_VARIANT_SPLIT8 8
+#define CRK_N_VARIANTS 9
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
-/* Launch mode of the pair kernels: 0 (default) one block per i-leaf; 1
- * persistent: a grid of 4 blocks per SM whose blocks take i-leaves from an
- * atomic work queue (no block ever waits on another).  Same results. */
+/* Launch mode of every pair kernel: 0 (default) one block per i-leaf (one warp
+ * per group for the list kernels); 1 persistent: a grid of 4 blocks per SM
+ * whose blocks (warps) take i-leaves (groups) from an atomic work queue (no
+ * block ever waits on another).  Same results. */
 int crk_set_persistent(crk_ctx *ctx, int on);
+/* Launch shape of one pair kernel (CRK_K_*), as the autotuner sets it:
+ * persistent as above, and the j-tile depth of the packed tiles sweeps of the
+ * gravity kernels (candidates compacted before each sweep: 32, 64 or 96; the
+ * other kernels and variants sweep at 32 and ignore it).  The results agree
+ * up to the order of FP32 additions.  CRK_EINVAL for an unknown kernel or a
+ * depth other than 32, 64, 96. */
+int crk_set_launch(crk_ctx *ctx, int kernel, int persistent, int depth);
+int crk_get_launch(const crk_ctx *ctx, int kernel, int *persistent, int *depth);
 int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant);
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int crk_launch_count(const crk_ctx *ctx, int64_t *out);
@@ -183,6 +200,44 @@ int crk_leaves_info(const crk_leaves *lv, int64_t info[6]);
 int crk_leaves_export(crk_ctx *ctx, const crk_leaves *lv, int32_t *perm, int32_t *leaf_start, int32_t *grav_ptr,
                       int32_t *grav_list, int32_t *hydro_ptr, int32_t *hydro_list);
 void crk_leaves_free(crk_ctx *ctx, crk_leaves *lv);
+
+/* Capture-safe rebuild (the batched driver's CUDA graph holds the leaf build;
+ * Sec. 5.3 runs every kernel over the leaf pairs of the current positions).
+ * Recomputes leaves lv in place for new positions and h of the same particles
+ * (same count, species, boxes and leaf parameters as the build that made lv),
+ * with no host synchronisation and no allocation, so the call can be captured
+ * in a CUDA graph together with the kernels that use the leaves.  Every
+ * buffer keeps the size the first build gave it (the leaf-pair image lists
+ * their first capacities, the gas neighbour lists 1/8 more groups than the
+ * first build held).  What a build checks on the host becomes a bit of the
+ * leaves' device status word instead: positions outside the box, gas h <= 0,
+ * 2 h_max >= box/2, a changed gas count, a capacity overflow.  After a
+ * nonzero status the leaves and every result computed from them are invalid:
+ * build new leaves with crk_build_leaves.  The particle arrays are device
+ * pointers laid out as for crk_build_leaves (crk_leaves_rebuild) or
+ * crk_build_leaves_batch (crk_leaves_rebuild_batch).  Returns CRK_ESTATE
+ * (before launching anything) if the inputs do not match the leaves, if the
+ * leaves hold gravity neighbour lists (their sizes vary), or if the gas lists
+ * were built by the exact two-pass path; the RCB tree shape of the context
+ * must still be the one of lv (a context caches one shape: a build of other
+ * boxes in between makes the next rebuild recompute it, which synchronises
+ * and fails under stream capture). */
+#define CRK_LEAVES_BAD_POSITION 1   /* a position outside [0, box) */
+#define CRK_LEAVES_BAD_H 2          /* a gas h <= 0 or not finite */
+#define CRK_LEAVES_GAS_COUNT 4      /* the number of gas particles changed */
+#define CRK_LEAVES_LEAF_SIZE 8      /* a leaf above the largest leaf size */
+#define CRK_LEAVES_HMAX 16          /* 2 h_max >= box/2 in some box */
+#define CRK_LEAVES_CANDIDATES 32    /* a leaf with too many candidate leaves within the cut */
+#define CRK_LEAVES_IMAGE_CAP 64     /* a leaf-pair image list above its capacity */
+#define CRK_LEAVES_GROUP_CAP 128    /* more gas groups than the gas lists hold */
+#define CRK_LEAVES_LIST_CAP 256     /* a gas neighbour list or group table above its capacity */
+#define CRK_LEAVES_INTERNAL 512     /* an inconsistent RCB partition */
+int crk_leaves_rebuild(crk_ctx *ctx, crk_leaves *lv, const crk_particles *p, const float *h);
+int crk_leaves_rebuild_batch(crk_ctx *ctx, crk_leaves *lv, const crk_batch *b, const float *h);
+/* Synchronises the context stream, then writes the status word of the last
+ * build or rebuild of lv to *status (host; 0 = valid) and refreshes the pair
+ * and image counts that crk_leaves_info reports. */
+int crk_leaves_status(crk_ctx *ctx, crk_leaves *lv, int32_t *status);
 
 /* Geometry (Sec. 5: volumes of gas particles).
  *   V_i = 1 / sum_{gas j, r_ij < 2 h_ij} W(r_ij, h_ij)  (j = i included),  rho_i = m_i / V_i.
@@ -447,14 +502,37 @@ int crk_step_profile_read(crk_ctx *ctx, float ms[7], int *steps);
 typedef struct crk_graph crk_graph;
 int crk_step_graph_create(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
                           const crk_step_io *io, crk_graph **out);
+/* The batched driver as one CUDA graph: crk_leaves_rebuild_batch of lv (for the
+ * positions and h the arrays of b and h hold when the graph is launched) and
+ * then crk_step, every pair kernel in its context launch shape (persistent
+ * where crk_set_persistent or the autotuner chose it).  The creating call runs
+ * one rebuild and step uncaptured first (sizing the scratch), and fails with
+ * CRK_ESTATE if that rebuild's status is nonzero.  After each launch the
+ * caller reads crk_leaves_status when it needs to know the leaves were valid
+ * (a nonzero status invalidates that step's outputs). */
+int crk_rebuild_step_graph_create(crk_ctx *ctx, crk_leaves *lv, const crk_batch *b, const float *h,
+                                  const crk_grav_params *gp, const crk_hydro_params *hp, const crk_step_io *io,
+                                  crk_graph **out);
 int crk_graph_launch(crk_graph *g);
 void crk_graph_destroy(crk_graph *g);
 
-/* Autotuner: times every variant of every kernel on these leaves (best of
- * reps after a warm-up, CUDA events on the context stream), keeps the fastest
- * in the context, and reports ms_out[6 * CRK_N_VARIANTS] (kernel-major; -1 = not available)
- * and best_out[6] (host arrays, may be NULL).  Runs one crk_step first; every
- * output array of io must be given (they are overwritten while timing). */
+/* Autotuner (Sec. 5.2 tunes register use and sub-group size per kernel and
+ * device; here the dimensions are the sweep variant, the launch mode and the
+ * j-tile depth).  For every kernel CRK_K_* it times each variant on these
+ * leaves (best of reps after a warm-up, CUDA events on the context stream;
+ * a candidate whose warm-up takes more than three times the best time so far
+ * is not timed further and reports its warm-up time) and keeps the fastest,
+ * then times the fastest variant non-persistent and
+ * persistent, then (gravity kernels on tiles) at depths 32, 64 and 96, and
+ * keeps the fastest shape in the context.  ms_out[CRK_N_KERNELS * CRK_TUNE_COLS]
+ * (kernel-major: CRK_N_VARIANTS variant timings, 2 launch-mode timings, 3
+ * depth timings; -1 = not timed) and best_out[3 * CRK_N_KERNELS] (variant,
+ * persistent, depth per kernel) are host arrays and may be NULL.  Runs one
+ * crk_step first; every output array of io must be given (they are
+ * overwritten while timing).  Extras is timed when io->extras is set, the
+ * Acceleration and Energy passes always (with io->dvdx as the limiter's
+ * velocity gradient when io->extras is set). */
+#define CRK_TUNE_COLS (CRK_N_VARIANTS + 5)
 int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io, int reps, float *ms_out, int *best_out);
 
@@ -462,8 +540,13 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
  * for callers that cannot let a library allocate device memory, such as an
  * application whose own memory pool already owns the GPU, or a step loop that
  * must never pay the device synchronisation cudaMalloc/cudaFree can imply.
- * It computes exactly what grav_short computes (same kernels, no pair count)
- * and calls no cudaMalloc, cudaFree or other allocating routine: its only
+ * It computes what grav_short computes, with grav_short's tiles kernel, or
+ * its lists kernel when the context's gravity variant is CRK_VARIANT_LISTS
+ * and the leaves hold gravity lists (no pair count).  The other sweep
+ * variants and the persistent launch mode are not used here: after crk_tune
+ * or crk_set_variant selects one of them, the two calls agree within FP32
+ * rounding instead of bit for bit.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its only
  * scratch, 16 bytes per particle, is a file-scope device array of
  * CRK_NOALLOC_MAX_PARTICLES entries (32 MiB) that every GPU which loads the
  * library holds until the process exits.  The caller passes the inputs (leaves

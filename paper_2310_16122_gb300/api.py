@@ -58,6 +58,14 @@ class Context:
     def set_persistent(self, on: bool) -> None:
         self.check(N.lib().crk_set_persistent(self.handle, int(bool(on))))
 
+    def set_launch(self, kernel: str, persistent: bool, depth: int = 32) -> None:
+        self.check(N.lib().crk_set_launch(self.handle, N.KERNELS[kernel], int(bool(persistent)), int(depth)))
+
+    def get_launch(self, kernel: str) -> tuple:
+        p, d = ctypes.c_int(0), ctypes.c_int(0)
+        self.check(N.lib().crk_get_launch(self.handle, N.KERNELS[kernel], ctypes.byref(p), ctypes.byref(d)))
+        return bool(p.value), int(d.value)
+
     def get_variant(self, kernel: str) -> int:
         v = ctypes.c_int(0)
         self.check(N.lib().crk_get_variant(self.handle, N.KERNELS[kernel], ctypes.byref(v)))
@@ -125,6 +133,16 @@ class Leaves:
         out["grav_list"] = out["grav_list"][:self.n_grav_pairs]
         out["hydro_list"] = out["hydro_list"][:self.n_hydro_pairs]
         return out
+
+    def status(self) -> int:
+        """Status word of the last build or rebuild (synchronises; 0 = valid), and fresh counts."""
+        s = ctypes.c_int(0)
+        self.ctx.check(N.lib().crk_leaves_status(self.ctx.handle, self.handle, ctypes.byref(s)))
+        info = (ctypes.c_int64 * 6)()
+        self.ctx.check(N.lib().crk_leaves_info(self.handle, info))
+        self.n, self.n_leaves, self.n_grav_pairs, self.n_hydro_pairs, self.n_grav_images, self.n_hydro_images = \
+            (int(v) for v in info)
+        return int(s.value)
 
     def free(self) -> None:
         if self.handle:
@@ -418,13 +436,33 @@ class DeviceBatch:
         self.hp = HydroParams()
 
 
-def build_leaves_batch(ctx: Context, dbt: DeviceBatch) -> Leaves:
+def _batch_c(dbt):
+    """crk_batch of a DeviceBatch (or a DeviceBox as a batch of one); the host arrays it points to
+    are returned with it and must stay alive while it is used."""
     n = dbt.n
-    bs = np.ascontiguousarray(dbt.box_start, np.int64)
-    side = np.ascontiguousarray(dbt.box_side, np.float32)
+    if hasattr(dbt, "box_start"):
+        bs = np.ascontiguousarray(dbt.box_start, np.int64)
+        side = np.ascontiguousarray(dbt.box_side, np.float32)
+    else:
+        bs = np.array([0, n], np.int64)
+        side = np.array([dbt.L], np.float32)
     c = N.crk_batch(_f32(dbt.x, "x", n), _f32(dbt.y, "y", n), _f32(dbt.z, "z", n), dbt.species.data_ptr(), n,
                     len(side), bs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                     side.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return c, (bs, side)
+
+
+def rebuild_leaves(ctx: Context, lv: Leaves, dbt) -> None:
+    """crk_leaves_rebuild_batch: lv recomputed in place for the current positions and h of dbt (a
+    DeviceBatch or DeviceBox with the particles lv was built from); no synchronisation (see
+    Leaves.status)."""
+    c, keep = _batch_c(dbt)
+    ctx.check(N.lib().crk_leaves_rebuild_batch(ctx.handle, lv.handle, ctypes.byref(c), _f32(dbt.h, "h", dbt.n)))
+
+
+def build_leaves_batch(ctx: Context, dbt: DeviceBatch) -> Leaves:
+    n = dbt.n
+    c, keep = _batch_c(dbt)
     lp = N.crk_leaf_params(int(dbt.lp.mode), 0, int(dbt.lp.max_leaf), float(dbt.lp.r_cut_grav))
     out = ctypes.c_void_p()
     ctx.check(N.lib().crk_build_leaves_batch(ctx.handle, ctypes.byref(c), _f32(dbt.h, "h", n), ctypes.byref(lp),
@@ -513,16 +551,38 @@ class StepGraph:
             pass
 
 
+class RebuildStepGraph(StepGraph):
+    """The batched driver as one CUDA graph: leaf rebuild (crk_leaves_rebuild_batch) and crk_step."""
+
+    def __init__(self, ctx: Context, lv: Leaves, dbt, io: StepIO):
+        self.ctx, self.keep = ctx, (lv, dbt, io)
+        c, self._host = _batch_c(dbt)
+        self._c = c
+        gp, hp, ci = dbt.gp.c(), dbt.hp.c(), io.c(False)
+        h = ctypes.c_void_p()
+        ctx.check(N.lib().crk_rebuild_step_graph_create(ctx.handle, lv.handle, ctypes.byref(c),
+                                                        _f32(dbt.h, "h", dbt.n), ctypes.byref(gp),
+                                                        ctypes.byref(hp), ctypes.byref(ci), ctypes.byref(h)))
+        self.handle = h
+
+
 def tune(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, reps: int = 3) -> dict:
-    """Autotune the kernel variants on these leaves; returns {kernel: (best, [ms per variant])}."""
+    """Autotune every pair kernel on these leaves (crk_tune): the sweep variant, then the launch
+    mode, then (gravity tiles) the j-tile depth.  Returns {kernel: {"variant", "persistent",
+    "depth", "ms": {"variant": [ms per variant], "launch": [off, on], "depth": [32, 64, 96]}}}
+    (-1 = not timed; extras only when io has the Extras outputs)."""
     gp, hp, c = db.gp.c(), db.hp.c(), io.c(False)
-    ms = (ctypes.c_float * (6 * N.N_VARIANTS))()
-    best = (ctypes.c_int * 6)()
+    ms = (ctypes.c_float * (N.N_KERNELS * N.TUNE_COLS))()
+    best = (ctypes.c_int * (3 * N.N_KERNELS))()
     ctx.check(N.lib().crk_tune(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp), ctypes.byref(c),
                                int(reps), ms, best))
-    names = sorted(N.KERNELS, key=N.KERNELS.get)[:6]  # the six kernels of crk_step
-    return {k: (int(best[i]), [float(ms[N.N_VARIANTS * i + v]) for v in range(N.N_VARIANTS)])
-            for i, k in enumerate(names)}
+    out = {}
+    for k, i in N.KERNELS.items():
+        row = [round(float(ms[N.TUNE_COLS * i + q]), 4) for q in range(N.TUNE_COLS)]
+        out[k] = {"variant": int(best[3 * i]), "persistent": bool(best[3 * i + 1]), "depth": int(best[3 * i + 2]),
+                  "ms": {"variant": row[:N.N_VARIANTS], "launch": row[N.N_VARIANTS:N.N_VARIANTS + 2],
+                         "depth": row[N.N_VARIANTS + 2:]}}
+    return out
 
 
 def autotune(ctx: Context, lv: Leaves, db, io: StepIO, cache_path: str | None = None, reps: int = 3) -> dict:
@@ -542,12 +602,16 @@ def autotune(ctx: Context, lv: Leaves, db, io: StepIO, cache_path: str | None = 
             cache = json.load(open(cache_path))
         except (OSError, ValueError):
             cache = {}
-    if key in cache:
+    if key in cache and "launch" in cache[key]:
         for k, v in cache[key]["variants"].items():
             ctx.set_variant(k, int(v))
+        for k, (pm, d) in cache[key]["launch"].items():
+            ctx.set_launch(k, bool(pm), int(d))
         return dict(cache[key], cached=True)
     res = tune(ctx, lv, db, io, reps)
-    entry = {"variants": {k: b for k, (b, _) in res.items()}, "ms": {k: ms for k, (_, ms) in res.items()}}
+    entry = {"variants": {k: r["variant"] for k, r in res.items()},
+             "launch": {k: [int(r["persistent"]), r["depth"]] for k, r in res.items()},
+             "ms": {k: r["ms"] for k, r in res.items()}}
     if cache_path:
         cache[key] = entry
         tmp = cache_path + ".tmp%d" % os.getpid()

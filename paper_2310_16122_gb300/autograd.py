@@ -9,14 +9,30 @@ and u.  Gradients flow to the positions (as a (3, n)
 tensor) and the masses; h is held fixed and the leaves are treated as
 constant (piecewise constant in the positions, so they carry no gradient).
 
-The positions tensor passed in must be the one the leaves were built from; the
-kernels read the positions captured by the leaves.
+The kernels read the positions captured by the leaves, so every forward
+checks the positions tensor passed in against the ones the leaves were built
+from: the same storage passes at once; another tensor must hold equal values
+(checked on the device), else CRK_ESTATE is raised: leaves built from other
+positions would give values and gradients at the wrong positions.
 """
 from __future__ import annotations
 
 import torch
 
 from . import api
+from . import native as N
+
+
+def _check_positions(pos3, leaves: api.Leaves) -> None:
+    """Refuse positions other than those the leaves were built from (CRK_ESTATE)."""
+    src = leaves._keep[:3]
+    if pos3.dim() != 2 or pos3.shape[0] != 3 or pos3.shape[1] != leaves.n:
+        raise N.CrkError(N.CRK_ESTATE, f"positions must be a (3, {leaves.n}) tensor, got {tuple(pos3.shape)}")
+    p = pos3.detach()
+    if all(p[c].data_ptr() == src[c].data_ptr() and p[c].stride() == src[c].stride() for c in range(3)):
+        return
+    if not all(torch.equal(p[c], src[c]) for c in range(3)):
+        raise N.CrkError(N.CRK_ESTATE, "positions differ from those the leaves were built from: rebuild the leaves")
 
 
 class GravShort(torch.autograd.Function):
@@ -24,6 +40,7 @@ class GravShort(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, pos3, m, ctx: api.Context, leaves: api.Leaves, gp: api.GravParams):
+        _check_positions(pos3, leaves)
         a, _ = api.grav_short(ctx, leaves, gp, m.detach().contiguous())
         fctx.save_for_backward(m)
         fctx.crk = (ctx, leaves, gp)
@@ -42,6 +59,7 @@ class CrkGeometry(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, pos3, m, ctx: api.Context, leaves: api.Leaves):
+        _check_positions(pos3, leaves)
         V, rho, _ = api.geometry(ctx, leaves, m.detach().contiguous())
         fctx.save_for_backward(m, V)
         fctx.crk = (ctx, leaves)
@@ -63,6 +81,7 @@ class CrkCorrections(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, pos3, V, ctx: api.Context, leaves: api.Leaves):
+        _check_positions(pos3, leaves)
         A, B, gA, gB, _ = api.corrections(ctx, leaves, V.detach().contiguous())
         fctx.save_for_backward(V)
         fctx.crk = (ctx, leaves)
@@ -86,6 +105,7 @@ class CrkHydro(torch.autograd.Function):
     @staticmethod
     def forward(fctx, pos3, m, v3, u, V, rho, A, B, gA, gB, ctx: api.Context, leaves: api.Leaves,
                 hp: api.HydroParams):
+        _check_positions(pos3, leaves)
         ins = [t.detach().contiguous() for t in (m, v3, u, V, rho, A, B, gA, gB)]
         dv, du, _, _ = api.hydro(ctx, leaves, hp, *ins)
         fctx.save_for_backward(*ins)

@@ -127,7 +127,7 @@ const char *crk_version(void) { return "libcrk 1 sm_103a"; }
 
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant) {
     if (!ctx) return CRK_EINVAL;
-    if (kernel < 0 || kernel > CRK_K_EXTRAS) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
+    if (kernel < 0 || kernel >= CRK_N_KERNELS) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
     if (variant < CRK_VARIANT_LISTS || variant >= CRK_N_VARIANTS)
         return crk_fail(ctx, CRK_EINVAL, "variant %d not available for kernel %d", variant, kernel);
     ctx->variant[kernel] = variant;
@@ -135,14 +135,30 @@ int crk_set_variant(crk_ctx *ctx, int kernel, int variant) {
 }
 
 int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant) {
-    if (!ctx || !variant || kernel < 0 || kernel > CRK_K_EXTRAS) return CRK_EINVAL;
+    if (!ctx || !variant || kernel < 0 || kernel >= CRK_N_KERNELS) return CRK_EINVAL;
     *variant = ctx->variant[kernel];
     return CRK_OK;
 }
 
 int crk_set_persistent(crk_ctx *ctx, int on) {
     if (!ctx) return CRK_EINVAL;
-    ctx->persistent = on != 0;
+    for (int k = 0; k < CRK_N_KERNELS; ++k) ctx->persist[k] = on != 0;
+    return CRK_OK;
+}
+
+int crk_set_launch(crk_ctx *ctx, int kernel, int persistent, int depth) {
+    if (!ctx) return CRK_EINVAL;
+    if (kernel < 0 || kernel >= CRK_N_KERNELS) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
+    if (depth != 32 && depth != 64 && depth != 96) return crk_fail(ctx, CRK_EINVAL, "depth must be 32, 64 or 96");
+    ctx->persist[kernel] = persistent != 0;
+    ctx->depth[kernel] = depth;
+    return CRK_OK;
+}
+
+int crk_get_launch(const crk_ctx *ctx, int kernel, int *persistent, int *depth) {
+    if (!ctx || kernel < 0 || kernel >= CRK_N_KERNELS) return CRK_EINVAL;
+    if (persistent) *persistent = ctx->persist[kernel];
+    if (depth) *depth = ctx->depth[kernel];
     return CRK_OK;
 }
 

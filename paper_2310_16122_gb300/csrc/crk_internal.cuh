@@ -47,8 +47,9 @@ struct crk_ctx {
     int num_sms = 0;
     std::string err;
     // growable scratch arena: one buffer per slot
-    static const int kSlots = 35;  // leaf build 0-16 and 19-31, radix sort 12-14, scan 15, queue 17, step 18,
-                                   // integrator 32, corrections adjoint 33, adjoint chain 34
+    static const int kSlots = 38;  // leaf build 0-16 and 19-31, radix sort 12-14, scan 15, queue 17, step 18,
+                                   // integrator 32, corrections adjoint 33, adjoint chain 34, half-warp force 35,
+                                   // tuner 36, split-sweep candidates 37
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     int64_t launches = 0;  // kernels this context has launched
@@ -57,12 +58,15 @@ struct crk_ctx {
     std::vector<std::pair<void *, size_t>> block_cache;
     crk_rcb_shape *rcb = nullptr;
     bool trace = false;  // CRK_TRACE=1: synchronise and print phase times of the leaf build
-    bool persistent = false;  // pair kernels: persistent grid + atomic leaf queue
+    // launch shape of each pair kernel (autotuner choices), indexed by CRK_K_*: persistent grid +
+    // atomic work queue, and the j-tile depth of the gravity tiles sweeps
+    int persist[CRK_N_KERNELS] = {};
+    int depth[CRK_N_KERNELS] = {32, 32, 32, 32, 32, 32, 32, 32, 32};
     // crk_step profiling: 8 events per step (start, after each of the 6 stages, end)
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
     // kernel variants (autotuner choices), indexed by CRK_K_*; 0 = default
-    int variant[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int variant[CRK_N_KERNELS] = {};
 };
 
 struct crk_nlist {
@@ -74,7 +78,9 @@ struct crk_nlist {
     int32_t *uoff = nullptr;    // [groups + 1] first j-table entry of each group
     int32_t *unum = nullptr;    // [groups] j-table size of each group
     uint32_t *ucode = nullptr;  // j-table entries: image << 10 | j inside the j-leaf
-    int64_t groups = 0, entries = 0, table = 0;
+    int64_t groups = 0, entries = 0, table = 0;  // groups: the capacity of the group arrays
+    int32_t *dgroups = nullptr;  // device: groups of the last build (at most `groups`)
+    bool onepass = false;        // fixed capacities per group (a rebuild can reuse them)
 };
 
 struct crk_leaves {
@@ -116,6 +122,16 @@ struct crk_leaves {
     // index of j inside its leaf
     crk_nlist gas_lists, grav_lists;
     std::vector<std::pair<void *, size_t>> allocs;
+    // what a capture-safe rebuild (crk_leaves_rebuild) reuses
+    int max_leaf = 0, cells = 0;
+    std::vector<int64_t> box_start;
+    std::vector<float> box_side;
+    float *node_box = nullptr, *node_hmax = nullptr;  // RCB traversal tree: node boxes and h_max
+    int64_t img_cap[4] = {0, 0, 0, 0};               // capacities of gimg, gpair, himg, hpair
+    unsigned char *boxtab = nullptr;                  // device copy of the build's box-table block
+    size_t boxtab_bytes = 0;
+    // device: [0] status bits, [1] gas groups, [2] gravity groups; [16..27] the six list cursors (u64)
+    int32_t *dev = nullptr;
 };
 
 // ---- host helpers (api.cu) ----
@@ -124,7 +140,9 @@ int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 void *crk_scratch(crk_ctx *ctx, int slot, size_t bytes);
 void *crk_leaves_alloc(crk_ctx *ctx, crk_leaves *lv, size_t bytes);
 void crk_rcb_shape_free(crk_ctx *ctx);
-int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas);
+// neighbour lists of the leaves; reuse: a rebuild into the buffers of the first build (no host
+// synchronisation; a capacity overflow sets a bit of the leaves' status word)
+int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas, bool reuse);
 int crk_step_fused(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
                    const crk_step_io *io);
 // One stage of crk_advance in the library's kernel orders.  The work array

@@ -394,10 +394,11 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
     return v;
 }
 
-// Shared state of bisect32 (one per block) for leaves of at most kCap members.
+// Shared state of bisect32 (one per block) for leaves of at most kCap members
+// (parts of 8 for leaves of at most 256, parts of 32 above).
 template <int kCap>
 struct Bisect32 {
-    static constexpr int kMaxSeg = kCap / 32;
+    static constexpr int kMaxSeg = kCap <= 256 ? kCap / 8 : kCap / 32;
     int16_t a[kCap], b[kCap];  // orders (member slots), double-buffered
     float cax[kCap];           // coordinate of the member at each position on its part's axis
     uint32_t cid[kCap];        // its particle index (ties)
@@ -405,29 +406,42 @@ struct Bisect32 {
     int nseg, more;
 };
 
-// Bisects positions [0, m) of the order bs.a (member slots; m <= kCap)
-// into groups of 32: each part above 32 is ranked along the longest extent of
-// its members in (coordinate, index) order and split with 32 ceil(g/2) of its
-// g groups of 32 on the left, until every part holds at most 32; then every
-// run of 32 positions starting at a multiple of 32 is an RCB cell (at most
-// ceil(m/32) <= kCap/32 <= 32 parts, one per lane of warp 0).  All threads call it;
-// returns the array (bs.a or bs.b) holding the result in [0, m).
-template <int kCap>
-__device__ int16_t *bisect32(Bisect32<kCap> &bs, int m, const float4 *pm, const uint64_t *key) {
+// Bisects positions [0, m) of the order src (bs.a or bs.b; member slots; m <= kCap)
+// into groups of U: each part above U is ranked along the longest extent of
+// its members in (coordinate, index) order and split with U ceil(g/2) of its
+// g groups of U on the left, until every part holds at most U; then every run
+// of U positions starting at a multiple of U is an RCB cell.  The parts start
+// as the runs of `start` positions (start = m: the whole range; start = 32
+// with U = 8: the RCB cells of 32, each bisected into cells of 8).  At most
+// ceil(m/U) <= 32 parts, one per lane of warp 0.  All threads call it; returns
+// the array (bs.a or bs.b) holding the result in [0, m).
+template <int kCap, int U = 32>
+__device__ int16_t *bisect32(Bisect32<kCap> &bs, int m, const float4 *pm, const uint64_t *key,
+                             int16_t *src_in = nullptr, int start = 0) {
+    static_assert(kCap / U <= Bisect32<kCap>::kMaxSeg && kCap / U <= 32, "parts per leaf");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int16_t *src = bs.a, *dst = bs.b;
+    int16_t *src = src_in ? src_in : bs.a, *dst = src == bs.a ? bs.b : bs.a;
+    if (start <= 0 || start > m) start = m;
     if (threadIdx.x == 0) {
-        bs.nseg = 1;
-        bs.lo[0] = 0;
-        bs.hi[0] = m;
-        bs.more = m > 32;
+        bs.nseg = 0;
+        bs.more = 0;
+        for (int l = 0; l < m; l += start) {
+            bs.lo[bs.nseg] = l;
+            bs.hi[bs.nseg] = l + start < m ? l + start : m;
+            bs.more |= bs.hi[bs.nseg] - l > U;
+            ++bs.nseg;
+        }
+        if (m == 0) {
+            bs.nseg = 1;
+            bs.lo[0] = bs.hi[0] = 0;
+        }
     }
     __syncthreads();
     while (bs.more) {
         // axis of the longest extent of every part above 32 (one warp per part)
         for (int sg = w; sg < bs.nseg; sg += nw) {
             const int l = bs.lo[sg], hh = bs.hi[sg];
-            if (hh - l <= 32) {
+            if (hh - l <= U) {
                 if (lane == 0) bs.ax[sg] = -1;
                 continue;
             }
@@ -489,8 +503,8 @@ __device__ int16_t *bisect32(Bisect32<kCap> &bs, int m, const float4 *pm, const 
             }
             const int total = __shfl_sync(CRK_FULL_MASK, off, 31);
             off -= nch;
-            const int g = (hh - l + 31) / 32;
-            const int left = split ? 32 * ((g + 1) / 2) : hh - l;
+            const int g = (hh - l + U - 1) / U;
+            const int left = split ? U * ((g + 1) / 2) : hh - l;
             __syncwarp();
             if (have) {
                 bs.lo[off] = l;
@@ -500,7 +514,7 @@ __device__ int16_t *bisect32(Bisect32<kCap> &bs, int m, const float4 *pm, const 
                     bs.hi[off + 1] = hh;
                 }
             }
-            const bool open = have && (left > 32 || (split && hh - l - left > 32));
+            const bool open = have && (left > U || (split && hh - l - left > U));
             const bool any = __any_sync(CRK_FULL_MASK, open);
             if (lane == 0) {
                 bs.nseg = total;
@@ -636,9 +650,11 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
         pos[lo + q] = make_float4(c.x - ox, c.y - oy, c.z - oz, c.w);
     }
     __syncthreads();
-    // gravity order: the whole leaf bisected into groups of 32
+    // gravity order: the whole leaf bisected into groups of 32, and (leaves of at most 256) each
+    // group of 32 into groups of 8 (the sub-cells of the split gravity sweeps)
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) bs.a[t] = (int16_t)t;
-    const int16_t *src = bisect32(bs, cnt, pm, key);
+    int16_t *src = bisect32(bs, cnt, pm, key);
+    if constexpr (kCap <= 256) src = bisect32<kCap, 8>(bs, cnt, pm, key, src, 32);
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int t = src[q];
         const float4 c = pm[t];
@@ -1144,10 +1160,11 @@ static int rcb_shape(crk_ctx *ctx, const std::vector<int64_t> &box_start, int ml
 namespace {
 struct Tracer {
     crk_ctx *ctx;
+    bool on;  // never during a rebuild (it may be captured)
     std::chrono::steady_clock::time_point t;
-    explicit Tracer(crk_ctx *c) : ctx(c), t(std::chrono::steady_clock::now()) {}
+    Tracer(crk_ctx *c, bool allowed) : ctx(c), on(allowed && c->trace), t(std::chrono::steady_clock::now()) {}
     void mark(const char *what) {
-        if (!ctx->trace) return;
+        if (!on) return;
         cudaStreamSynchronize(ctx->stream);
         auto now = std::chrono::steady_clock::now();
         fprintf(stderr, "[crk] %-18s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
@@ -1170,13 +1187,40 @@ __global__ void init_node_of_kernel(int64_t n, const int32_t *__restrict__ box_o
     if (p < n) node_of[p] = seg_of_box[box_of[p]];
 }
 
+// The host checks of a build as bits of the leaves' status word (rebuilds, which do not synchronise).
+__global__ void leaf_status_kernel(const int32_t *__restrict__ flags, const unsigned *__restrict__ hbits,
+                                   const float *__restrict__ box_L, int nbox, int32_t n_gas, int32_t *__restrict__ status) {
+    int32_t s = 0;
+    if (threadIdx.x == 0) {
+        if (flags[0] > 0) s |= CRK_LEAVES_BAD_POSITION;
+        if (flags[1] > 0) s |= CRK_LEAVES_BAD_H;
+        if (flags[2] != n_gas) s |= CRK_LEAVES_GAS_COUNT;
+        if (flags[4] > 0) s |= CRK_LEAVES_LEAF_SIZE;
+        if (flags[5] > 0) s |= CRK_LEAVES_INTERNAL;
+    }
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
+        const float hm = __uint_as_float(hbits[b]);
+        if (!(2.0 * (double)hm < 0.5 * (double)box_L[b])) s |= CRK_LEAVES_HMAX;
+    }
+    if (s) atomicOr(status, s);
+}
+
+__global__ void pairs_status_kernel(const int32_t *__restrict__ err, int32_t *__restrict__ status) {
+    int32_t s = 0;
+    if (err[0] > 0) s |= CRK_LEAVES_CANDIDATES;
+    if (err[1] > 0) s |= CRK_LEAVES_IMAGE_CAP;
+    if (s) atomicOr(status, s);
+}
+
 // Leaves of one box (nbox = 1) or of several independent periodic boxes whose
 // particles are the consecutive ranges box_start[b] .. box_start[b+1].
+// re != NULL: rebuild those leaves in place (crk_leaves_rebuild): no host synchronisation and no
+// allocation; the host checks become bits of the leaves' device status word.
 static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *h, const crk_leaf_params *lp,
                              const std::vector<int64_t> &box_start, const std::vector<float> &box_side,
-                             crk_leaves **out) {
+                             crk_leaves **out, crk_leaves *re = nullptr) {
     if (!p || !lp || !out) return crk_fail(ctx, CRK_EINVAL, "null argument");
-    *out = nullptr;
+    if (!re) *out = nullptr;
     const int64_t n = p->n;
     const int nbox = (int)box_side.size();
     if (n < 0 || n > 2000000000LL) return crk_fail(ctx, CRK_EINVAL, "particle count out of range");
@@ -1197,14 +1241,33 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         box_max = std::max(box_max, box_side[b]);
     }
     if (box_start[0] != 0 || box_start[nbox] != n) return crk_fail(ctx, CRK_EINVAL, "box starts must span [0, n]");
+    if (re) {
+        if (re->n != n || re->box_start != box_start || re->box_side != box_side || re->mode != lp->mode ||
+            re->max_leaf != lp->max_leaf || re->cells != lp->cells_per_side || re->r_cut_grav != lp->r_cut_grav)
+            return crk_fail(ctx, CRK_ESTATE, "rebuild: particles, boxes or leaf parameters differ from the leaves'");
+        if (re->grav_lists.list) return crk_fail(ctx, CRK_ESTATE, "rebuild: leaves with gravity lists");
+        if (re->gas_lists.list && !re->gas_lists.onepass)
+            return crk_fail(ctx, CRK_ESTATE, "rebuild: gas lists of the exact two-pass build");
+        if (!re->dev || !re->boxtab) return crk_fail(ctx, CRK_ESTATE, "rebuild: leaves without rebuild state");
+        if (n > 0 && lp->mode == 1 && !(ctx->rcb && ctx->rcb->box_start == box_start && ctx->rcb->max_leaf == lp->max_leaf)) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(ctx->stream, &cs);
+            if (cs != cudaStreamCaptureStatusNone)
+                return crk_fail(ctx, CRK_ESTATE, "rebuild under capture: the context holds another RCB shape");
+        }
+    }
 
-    Tracer tr(ctx);
-    crk_leaves *lv = new crk_leaves();
+    Tracer tr(ctx, re == nullptr);
+    crk_leaves *lv = re ? re : new crk_leaves();
     lv->n = n;
     lv->box = box_max;
     lv->nbox = nbox;
     lv->mode = lp->mode;
     lv->r_cut_grav = lp->r_cut_grav;
+    lv->max_leaf = lp->max_leaf;
+    lv->cells = lp->cells_per_side;
+    lv->box_start = box_start;
+    lv->box_side = box_side;
     cudaStream_t st = ctx->stream;
     int rc = CRK_OK;
 #define TRY(expr)                          \
@@ -1212,13 +1275,15 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         rc = (expr);                       \
         if (rc != CRK_OK) goto fail;       \
     } while (0)
-#define ALLOC(ptr, type, count)                                                                      \
-    do {                                                                                             \
-        ptr = (type *)crk_leaves_alloc(ctx, lv, sizeof(type) * (size_t)((count) > 0 ? (count) : 1)); \
-        if (!ptr) {                                                                                  \
-            rc = crk_fail(ctx, CRK_ENOMEM, "leaf allocation");                                       \
-            goto fail;                                                                               \
-        }                                                                                            \
+#define ALLOC(ptr, type, count)                                                                          \
+    do {                                                                                                 \
+        if (!re) { /* a rebuild keeps the buffers of the first build */                                \
+            ptr = (type *)crk_leaves_alloc(ctx, lv, sizeof(type) * (size_t)((count) > 0 ? (count) : 1)); \
+            if (!ptr) {                                                                                  \
+                rc = crk_fail(ctx, CRK_ENOMEM, "leaf allocation");                                       \
+                goto fail;                                                                               \
+            }                                                                                            \
+        }                                                                                                \
     } while (0)
 #define KCHECK(what)                                       \
     do {                                                   \
@@ -1242,12 +1307,30 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             h_seg[b] = q;
             if (box_start[b + 1] > box_start[b]) ++q;
         }
-        if (cudaMemsetAsync(flags, 0, 64 + 4 * (size_t)nbox, st) != cudaSuccess ||
-            cudaMemcpyAsync(box_L, box_side.data(), 4 * (size_t)nbox, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(d_box_start, box_start.data(), 8 * (size_t)(nbox + 1), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(seg_of_box, h_seg.data(), 4 * (size_t)nbox, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        if (!re) {
+            if (cudaMemcpyAsync(box_L, box_side.data(), 4 * (size_t)nbox, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(d_box_start, box_start.data(), 8 * (size_t)(nbox + 1), cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(seg_of_box, h_seg.data(), 4 * (size_t)nbox, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                rc = crk_fail(ctx, CRK_ECUDA, "leaf build set-up copies");
+                goto fail;
+            }
+            // the rebuild state: a device copy of the box tables, the status word, group counts and cursors
+            lv->boxtab_bytes = fbytes + 64;
+            lv->boxtab = (unsigned char *)crk_leaves_alloc(ctx, lv, lv->boxtab_bytes);
+            lv->dev = (int32_t *)crk_leaves_alloc(ctx, lv, 256);
+            if (!lv->boxtab || !lv->dev) { rc = crk_fail(ctx, CRK_ENOMEM, "leaf allocation"); goto fail; }
+            if (cudaMemcpyAsync(lv->boxtab, flags, lv->boxtab_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                rc = crk_fail(ctx, CRK_ECUDA, "leaf build set-up copies");
+                goto fail;
+            }
+        } else if (cudaMemcpyAsync(flags, lv->boxtab, lv->boxtab_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
             rc = crk_fail(ctx, CRK_ECUDA, "leaf build set-up copies");
+            goto fail;
+        }
+        if (cudaMemsetAsync(flags, 0, 64 + 4 * (size_t)nbox, st) != cudaSuccess ||
+            cudaMemsetAsync(lv->dev, 0, 256, st) != cudaSuccess) {
+            rc = crk_fail(ctx, CRK_ECUDA, "memset");
             goto fail;
         }
         int32_t *box_of = nullptr;
@@ -1298,8 +1381,10 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                 rc = crk_fail(ctx, CRK_ECUDA, "leaf starts");
                 goto fail;
             }
-            ALLOC(node_box, float, 6 * shape->n_nodes);
-            ALLOC(node_hmax, float, shape->n_nodes);
+            ALLOC(lv->node_box, float, 6 * shape->n_nodes);
+            ALLOC(lv->node_hmax, float, shape->n_nodes);
+            node_box = lv->node_box;
+            node_hmax = lv->node_hmax;
             tr.mark("shape");
             int32_t *Lc[3];
             size_t nb = sizeof(int32_t) * (size_t)(n > 0 ? n : 1);
@@ -1412,16 +1497,22 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             ++ctx->launches;
         }
         KCHECK("leaf data");
+        if (re) {  // the checks below, on the device
+            leaf_status_kernel<<<1, 256, 0, st>>>(flags, hbits, box_L, nbox, (int32_t)lv->n_gas, lv->dev);
+            ++ctx->launches;
+        }
         // ---- host checks (one synchronisation)
         int32_t hflags[16];
         std::vector<unsigned> hb(nbox);
-        if (cudaMemcpyAsync(hflags, flags, 64, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (re) {
+        } else if (cudaMemcpyAsync(hflags, flags, 64, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(hb.data(), hbits, 4 * (size_t)nbox, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             rc = crk_fail(ctx, CRK_ECUDA, "leaf build: %s", cudaGetErrorString(cudaGetLastError()));
             goto fail;
         }
         tr.mark("leaf data");
+        if (!re) {
         if (hflags[0] > 0) { rc = crk_fail(ctx, CRK_EBOX, "%d particle positions outside [0, box)", hflags[0]); goto fail; }
         if (hflags[1] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "%d gas particles with h <= 0 or not finite", hflags[1]); goto fail; }
         if (hflags[4] > 0) { rc = crk_fail(ctx, CRK_EINVAL, "a leaf holds more than %d particles", kMaxLeafCap); goto fail; }
@@ -1451,6 +1542,7 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         } else {
             lv->max_leaf_size = shape->max_leaf_size;
         }
+        }
         // ---- tree for traversal (RCB): leaf boxes and h_max into the nodes, then bottom-up h_max
         TreeDev tree{};
         const int brute = lp->mode == 0 ? 1 : 0;
@@ -1476,14 +1568,18 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
         // ---- leaf-pair image lists, one warp per leaf; retried once with exact
         // capacities if the first estimate is too small
         {
-            int32_t *se[8];
+            int32_t *se[8] = {lv->gimg_start, lv->gimg_cnt, lv->gpair_start, lv->gpair_cnt,
+                              lv->himg_start, lv->himg_cnt, lv->hpair_start, lv->hpair_cnt};
             for (int q = 0; q < 8; ++q) ALLOC(se[q], int32_t, nl);
-            unsigned long long *cur = (unsigned long long *)crk_scratch(ctx, 3, 64);
-            if (!cur) { rc = crk_fail(ctx, CRK_ENOMEM, "scratch"); goto fail; }
+            // the list cursors live with the leaves (a rebuild refreshes the counts from them later)
+            unsigned long long *cur = (unsigned long long *)(lv->dev + 16);
             int64_t cap[4] = {48 * nl + 64, 32 * nl + 64, 48 * nl + 64, 32 * nl + 64};
-            crk_image *gimg = nullptr, *himg = nullptr;
-            int32_t *gpair = nullptr, *hpair = nullptr;
-            unsigned long long hcur[6];
+            if (re)
+                for (int k = 0; k < 4; ++k) cap[k] = lv->img_cap[k];
+            crk_image *gimg = lv->gimg, *himg = lv->himg;
+            int32_t *gpair = lv->gpair_list, *hpair = lv->hpair_list;
+            unsigned long long hcur[6] = {(unsigned long long)lv->n_gimg, (unsigned long long)lv->n_gpairs,
+                                          (unsigned long long)lv->n_himg, (unsigned long long)lv->n_hpairs, 0, 0};
             for (int attempt = 0; attempt < 2; ++attempt) {
                 // capacity blocks come from the leaves' own allocations; a retry leaves the
                 // first (too small) blocks unused until the leaves are freed
@@ -1514,6 +1610,11 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                     ++ctx->launches;
                 }
                 KCHECK("pair lists");
+                if (re) {  // one attempt at the first build's capacities; overflows go to the status word
+                    pairs_status_kernel<<<1, 1, 0, st>>>(po.err, lv->dev);
+                    ++ctx->launches;
+                    break;
+                }
                 if (cudaMemcpyAsync(hcur, cur, 48, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                     cudaStreamSynchronize(st) != cudaSuccess) {
                     rc = crk_fail(ctx, CRK_ECUDA, "pair lists: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1527,21 +1628,26 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                     goto fail;
                 }
                 if (herr[1] == 0) break;
-                for (int k = 0; k < 4; ++k) cap[k] = (int64_t)hcur[k] + 64;
+                // exact counts plus an eighth (room for the rebuilds of moved particles)
+                for (int k = 0; k < 4; ++k) cap[k] = (int64_t)hcur[k] + (int64_t)(hcur[k] / 8) + 64;
                 if (attempt == 1) { rc = crk_fail(ctx, CRK_ESTATE, "pair list capacity"); goto fail; }
             }
             lv->gimg_start = se[0]; lv->gimg_cnt = se[1]; lv->gimg = gimg; lv->n_gimg = (int64_t)hcur[0];
             lv->gpair_start = se[2]; lv->gpair_cnt = se[3]; lv->gpair_list = gpair; lv->n_gpairs = (int64_t)hcur[1];
             lv->himg_start = se[4]; lv->himg_cnt = se[5]; lv->himg = himg; lv->n_himg = (int64_t)hcur[2];
             lv->hpair_start = se[6]; lv->hpair_cnt = se[7]; lv->hpair_list = hpair; lv->n_hpairs = (int64_t)hcur[3];
+            for (int k = 0; k < 4; ++k) lv->img_cap[k] = cap[k];
         }
         tr.mark("pair lists");
-        if (ctx->variant[CRK_K_GEOMETRY] == CRK_VARIANT_LISTS || ctx->variant[CRK_K_CORRECTIONS] == CRK_VARIANT_LISTS ||
-            ctx->variant[CRK_K_HYDRO] == CRK_VARIANT_LISTS || ctx->variant[CRK_K_GEOMETRY_ADJOINT] == CRK_VARIANT_LISTS)
-            TRY(crk_build_lists(ctx, lv, true));
+        bool gas_lists = false;  // every gas-pair kernel may walk the gas lists
+        for (int k : {CRK_K_GEOMETRY, CRK_K_CORRECTIONS, CRK_K_HYDRO, CRK_K_GEOMETRY_ADJOINT, CRK_K_EXTRAS, CRK_K_ACCEL,
+                      CRK_K_ENERGY})
+            gas_lists = gas_lists || ctx->variant[k] == CRK_VARIANT_LISTS;
+        if (re ? lv->gas_lists.list != nullptr : gas_lists) TRY(crk_build_lists(ctx, lv, true, re != nullptr));
         tr.mark("gas lists");
-        if (ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS || ctx->variant[CRK_K_GRAVITY_ADJOINT] == CRK_VARIANT_LISTS)
-            TRY(crk_build_lists(ctx, lv, false));
+        if (!re && (ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS ||
+                    ctx->variant[CRK_K_GRAVITY_ADJOINT] == CRK_VARIANT_LISTS))
+            TRY(crk_build_lists(ctx, lv, false, false));
         tr.mark("gravity lists");
     }
 #undef TRY
@@ -1550,7 +1656,7 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
     *out = lv;
     return CRK_OK;
 fail:
-    crk_leaves_free(ctx, lv);
+    if (!re) crk_leaves_free(ctx, lv);
     return rc;
 }
 
@@ -1573,6 +1679,47 @@ int crk_build_leaves_batch(crk_ctx *ctx, const crk_batch *bt, const float *h, co
     crk_particles p{bt->x, bt->y, bt->z, bt->species, bt->n, 0.0f};
     for (float s : side) p.box = std::max(p.box, s);
     return build_leaves_impl(ctx, &p, h, lp, bs, side, out);
+}
+
+int crk_leaves_rebuild(crk_ctx *ctx, crk_leaves *lv, const crk_particles *p, const float *h) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !p) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    if (lv->nbox != 1) return crk_fail(ctx, CRK_ESTATE, "rebuild: the leaves hold several boxes");
+    std::vector<int64_t> bs = {0, p->n};
+    std::vector<float> side = {p->box};
+    crk_leaf_params lp{lv->mode, lv->cells, lv->max_leaf, lv->r_cut_grav};
+    crk_leaves *out = lv;
+    return build_leaves_impl(ctx, p, h, &lp, bs, side, &out, lv);
+}
+
+int crk_leaves_rebuild_batch(crk_ctx *ctx, crk_leaves *lv, const crk_batch *bt, const float *h) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !bt || !bt->box_start || !bt->box_side || bt->nbox < 1) return crk_fail(ctx, CRK_EINVAL, "bad batch");
+    std::vector<int64_t> bs(bt->box_start, bt->box_start + bt->nbox + 1);
+    std::vector<float> side(bt->box_side, bt->box_side + bt->nbox);
+    crk_particles p{bt->x, bt->y, bt->z, bt->species, bt->n, 0.0f};
+    for (float s : side) p.box = std::max(p.box, s);
+    crk_leaf_params lp{lv->mode, lv->cells, lv->max_leaf, lv->r_cut_grav};
+    crk_leaves *out = lv;
+    return build_leaves_impl(ctx, &p, h, &lp, bs, side, &out, lv);
+}
+
+int crk_leaves_status(crk_ctx *ctx, crk_leaves *lv, int32_t *status) {
+    if (!ctx) return CRK_EINVAL;
+    if (!lv || !status) return crk_fail(ctx, CRK_EINVAL, "null argument");
+    *status = 0;
+    if (!lv->dev) return CRK_OK;  // an empty box
+    int32_t head[4];
+    unsigned long long cur[6];
+    CRK_CUDA(ctx, cudaMemcpyAsync(head, lv->dev, sizeof(head), cudaMemcpyDeviceToHost, ctx->stream));
+    CRK_CUDA(ctx, cudaMemcpyAsync(cur, lv->dev + 16, sizeof(cur), cudaMemcpyDeviceToHost, ctx->stream));
+    CRK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *status = head[0];
+    lv->n_gimg = (int64_t)cur[0];
+    lv->n_gpairs = (int64_t)cur[1];
+    lv->n_himg = (int64_t)cur[2];
+    lv->n_hpairs = (int64_t)cur[3];
+    return CRK_OK;
 }
 
 int crk_leaves_info(const crk_leaves *lv, int64_t info[6]) {

@@ -24,6 +24,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCap = 64;                     // per-warp candidate buffer
+constexpr int kCapPair = 128;                // per-warp candidate buffer of the packed sweeps (depth <= 96)
 constexpr int kGroupImgCap = 128;            // image table of one i-leaf staged per warp in shared memory
 // capacities of the one-pass gas lists (adaptive h keeps a gas particle near 58 neighbours;
 // the largest lane list and group table seen in the clustered workloads are ~95 and ~360)
@@ -44,6 +45,7 @@ struct LeafView {
     int64_t n_leaves;
     int32_t *queue;  // persistent mode: next leaf to take (zeroed before launch); NULL = one block per leaf
     int korder;      // 1: the stage's per-particle arrays are in kernel order (no permutation)
+    int depth;       // packed tiles sweeps: candidates compacted before each sweep (32, 64 or 96)
 };
 
 // Next i-leaf of this block: the grid-stride successor, or (persistent mode)
@@ -129,6 +131,7 @@ struct GravP {
 };
 
 struct GravStage {
+    static constexpr bool kHalfWarp = true;
     static constexpr bool kGasOnly = false;
     static constexpr bool kTag = false;
     static constexpr bool kAllVariants = true;
@@ -214,12 +217,22 @@ struct GravStage {
         if (kCount) s.cnt += (int)in0 + (int)in1;
     }
     // partial sums of one i from one leaf-pair tile (half-warp arms): added atomically
-    __device__ static void flush(const P &p, const I &s, int32_t o) {
+    __device__ static void flush(const P &p, const I &s, const Rec &, int32_t o) {
         atomicAdd(&p.a3[o], s.ax);
         atomicAdd(&p.a3[p.n + o], s.ay);
         atomicAdd(&p.a3[2 * p.n + o], s.az);
     }
     static void zero_outputs(const P &p, cudaStream_t st) { cudaMemsetAsync(p.a3, 0, sizeof(float) * 3 * p.n, st); }
+    // adds the accumulators of lane ^ x (split sweeps: the lanes sharing one i)
+    __device__ static void combine2(I2 &s, int x) {
+        s.ax.x += __shfl_xor_sync(CRK_FULL_MASK, s.ax.x, x);
+        s.ax.y += __shfl_xor_sync(CRK_FULL_MASK, s.ax.y, x);
+        s.ay.x += __shfl_xor_sync(CRK_FULL_MASK, s.ay.x, x);
+        s.ay.y += __shfl_xor_sync(CRK_FULL_MASK, s.ay.y, x);
+        s.az.x += __shfl_xor_sync(CRK_FULL_MASK, s.az.x, x);
+        s.az.y += __shfl_xor_sync(CRK_FULL_MASK, s.az.y, x);
+        s.cnt += __shfl_xor_sync(CRK_FULL_MASK, s.cnt, x);
+    }
     __device__ static void finish2(const P &p, I2 &s, int32_t orig) {
         p.a3[orig] = s.ax.x + s.ax.y;
         p.a3[p.n + orig] = s.ay.x + s.ay.y;
@@ -238,6 +251,7 @@ struct GravAdjP {
 };
 
 struct GravAdjStage {
+    static constexpr bool kHalfWarp = true;
     static constexpr bool kGasOnly = false;
     static constexpr bool kTag = false;
     static constexpr bool kAllVariants = true;
@@ -362,7 +376,7 @@ struct GravAdjStage {
         if (kCount) s.cnt += (int)in0 + (int)in1;
     }
     // partial sums of one i from one leaf-pair tile (half-warp arms): added atomically
-    __device__ static void flush(const P &p, const I &s, int32_t o) {
+    __device__ static void flush(const P &p, const I &s, const Rec &, int32_t o) {
         atomicAdd(&p.gx3[o], s.gx);
         atomicAdd(&p.gx3[p.n + o], s.gy);
         atomicAdd(&p.gx3[2 * p.n + o], s.gz);
@@ -371,6 +385,16 @@ struct GravAdjStage {
     static void zero_outputs(const P &p, cudaStream_t st) {
         cudaMemsetAsync(p.gx3, 0, sizeof(float) * 3 * p.n, st);
         cudaMemsetAsync(p.gm, 0, sizeof(float) * p.n, st);
+    }
+    // adds the accumulators of lane ^ x (split sweeps: the lanes sharing one i)
+    __device__ static void combine2(I2 &s, int x) {
+        float2 *acc[8] = {&s.kx, &s.ky, &s.kz, &s.s1x, &s.s1y, &s.s1z, &s.s2, &s.sg};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q]->x += __shfl_xor_sync(CRK_FULL_MASK, acc[q]->x, x);
+            acc[q]->y += __shfl_xor_sync(CRK_FULL_MASK, acc[q]->y, x);
+        }
+        s.cnt += __shfl_xor_sync(CRK_FULL_MASK, s.cnt, x);
     }
     __device__ static void finish2(const P &p, I2 &s, int32_t o) {
         const float mi = s.mi.x, nbx = s.nbx.x, nby = s.nby.x, nbz = s.nbz.x;
@@ -1100,6 +1124,46 @@ struct HydroStageT {
         }
         if constexpr (kPass != kHydroAccel) p.du[o] = 0.f;
     }
+
+    // Half-warp arms (Sec. 5.3): partial sums of one i from one leaf-pair tile are added
+    // to the zeroed outputs with atomics (the Energy pass also adds its recomputed force
+    // to p.dv3 when given, for the conservation sums); the signal-velocity maximum goes
+    // straight to the one atomic max of vsig_i / h_i (a max of partial maxima).
+    static constexpr bool kHalfWarp = true;
+    __device__ static void flush(const P &p, const I &s, const Rec &ri, int32_t o) {
+        const float mi = p.m[o];
+        if (p.dv3) {
+            atomicAdd(&p.dv3[o], s.fx / mi);
+            atomicAdd(&p.dv3[p.n + o], s.fy / mi);
+            atomicAdd(&p.dv3[2 * p.n + o], s.fz / mi);
+        }
+        if constexpr (kPass != kHydroAccel) atomicAdd(&p.du[o], s.e / mi);
+        if constexpr (kPass == kHydroAccel) {
+            if (p.vsig_h) atomicMax(p.vsig_h, __float_as_uint(__fdividef(s.e, ri.h)));
+        }
+    }
+    // outside every cut (r^2 ~ 1e30 against (h_i + h_j)^2) with zero fields: exact zeros
+    __device__ static Rec far_dummy(float fx, float fy, float fz) {
+        Rec r{};
+        r.x = fx; r.y = fy; r.z = fz; r.h = 1.0f;
+        return r;
+    }
+    static void zero_outputs(const P &p, cudaStream_t st) {
+        if (p.dv3) cudaMemsetAsync(p.dv3, 0, sizeof(float) * 3 * p.n, st);
+        if (kPass != kHydroAccel && p.du) cudaMemsetAsync(p.du, 0, sizeof(float) * p.n, st);
+    }
+    // the conservation terms of cons_terms from the finished outputs of gas particle o
+    __device__ static void cons_of(const P &p, int32_t o, double c[4]) {
+        const int64_t n = p.n;
+        const double mi = (double)p.m[o];
+        const double dvx = p.dv3[o], dvy = p.dv3[n + o], dvz = p.dv3[2 * n + o];
+        const double du = kPass == kHydroAccel ? 0.0 : (double)p.du[o];
+        const float *w = kPass == kHydroEnergy ? p.vstar : p.v3;
+        c[0] = mi * dvx;
+        c[1] = mi * dvy;
+        c[2] = mi * dvz;
+        c[3] = mi * ((double)w[o] * dvx + (double)w[n + o] * dvy + (double)w[2 * n + o] * dvz + du);
+    }
 };
 
 
@@ -1433,6 +1497,7 @@ struct ListStage {
         int u;    // table size (warp-uniform)
         int cnt;
     };
+
     __device__ static Rec gather(const P &, int32_t, float4 ps) { return {ps.x, ps.y, ps.z, ps.w, 0u, 0u, 0u, 0u}; }
     __device__ static float box_cut(const P &p, float hmax_i, const Rec &rj) {
         return kGas ? hmax_i + rj.h : sqrtf(p.rc2);
@@ -1630,6 +1695,8 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
     }
     const float far = 2.0f * S::leaf_cut(p, hm, hm) + 1.0f;
     const Rec dummy = S::far_dummy(bh0 + far, bh1 + far, bh2 + far);
+    // sweep once at least `depth` candidates are compacted (the buffer holds depth + 31 + 1 dummy)
+    const int depth = lv.depth >= 64 ? (lv.depth >= 96 ? 96 : 64) : 32;
     auto sweep = [&](int cnt) {
         if (cnt & 1) {
             if (lane == 0) S::put2(buf, cnt, dummy);
@@ -1670,7 +1737,7 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
             const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
             if (keep) S::put2(buf, cnt + __popc(m & below), rj);
             cnt += __popc(m);
-            if (cnt >= 32) {
+            if (cnt >= depth) {
                 sweep(cnt);
                 if (kCount) swept += cnt;
                 cnt = 0;
@@ -1687,6 +1754,159 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
         if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
         const unsigned long long na = __popc(__ballot_sync(CRK_FULL_MASK, act));
         if (lane == 0 && p.swept) atomicAdd(p.swept, swept * na);
+    }
+}
+
+// Split tiles for the packed gravity sweeps (CRK_VARIANT_SPLIT8).  The warp
+// compacts the candidates within the cut of its 32-particle group (an RCB cell
+// of the leaf) once, into a per-warp buffer in global memory (its working set
+// stays in L2), then sweeps that buffer once for each of the group's four
+// 8-particle RCB sub-cells: only the candidates within the cut of the
+// sub-cell's box are kept (compacted into shared memory), and the 4 lanes of
+// each of the sub-cell's 8 i-particles take every 4th packed candidate pair,
+// so the lanes stay balanced; their partial sums are added by shuffles at the
+// end.  A sub-cell box is about a quarter of the group's volume, so a larger
+// share of the evaluated pairs lies within r_c.  A group whose candidates
+// overflow the buffer (gcap) is swept as plain tiles.
+template <class S, bool kCount>
+__global__ void __launch_bounds__(kThreads) pair_kernel_split(LeafView lv, typename S::P p,
+                                                              const typename S::Rec *__restrict__ rec,
+                                                              typename S::Rec *__restrict__ gbuf, int gcap) {
+    using Rec = typename S::Rec;
+    using Rec2 = typename S::Rec2;
+    static_assert(S::kPair && !S::kCons && !S::kGasOnly, "split sweeps: packed gravity-type stages only");
+    __shared__ __align__(16) Rec sbuf[kWarps][kCapPair];
+    __shared__ int64_t leaf_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Rec2 *buf = reinterpret_cast<Rec2 *>(sbuf[warp]);
+    Rec *gb = gbuf + ((size_t)blockIdx.x * kWarps + warp) * (size_t)gcap;
+    const unsigned below = lanemask_lt();
+    const int depth = lv.depth >= 64 ? (lv.depth >= 96 ? 96 : 64) : 64;  // at least 64: 8 pairs per split lane
+    for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
+        const int lo = lv.leaf_start[a], hi = lv.leaf_start[a + 1];
+        const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32) {
+            // ---- the group's candidates into the per-warp buffer
+            const int i = g0 + lane;
+            const Rec ri = rec[i < hi ? i : g0];
+            float bl0 = ri.x, bl1 = ri.y, bl2 = ri.z, bh0 = ri.x, bh1 = ri.y, bh2 = ri.z;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bl0 = fminf(bl0, __shfl_xor_sync(CRK_FULL_MASK, bl0, o));
+                bl1 = fminf(bl1, __shfl_xor_sync(CRK_FULL_MASK, bl1, o));
+                bl2 = fminf(bl2, __shfl_xor_sync(CRK_FULL_MASK, bl2, o));
+                bh0 = fmaxf(bh0, __shfl_xor_sync(CRK_FULL_MASK, bh0, o));
+                bh1 = fmaxf(bh1, __shfl_xor_sync(CRK_FULL_MASK, bh1, o));
+                bh2 = fmaxf(bh2, __shfl_xor_sync(CRK_FULL_MASK, bh2, o));
+            }
+            const float cut = S::leaf_cut(p, 0.f, 0.f);
+            const float cut2 = cut * cut * 1.0001f + 1e-6f;
+            int cnt = 0;
+            bool ovf = false;
+            for (int e = ib; e < ie && !ovf; ++e) {
+                const crk_image im = lv.img[e];
+                const int jlo = lv.leaf_start[im.b], jhi = lv.leaf_start[im.b + 1];
+                {
+                    const float *bb = lv.bbox + 6 * (int64_t)im.b;
+                    float gx = fmaxf(fmaxf(im.sx - bh0, bl0 - (im.sx + (bb[3] - bb[0]))), 0.f);
+                    float gy = fmaxf(fmaxf(im.sy - bh1, bl1 - (im.sy + (bb[4] - bb[1]))), 0.f);
+                    float gz = fmaxf(fmaxf(im.sz - bh2, bl2 - (im.sz + (bb[5] - bb[2]))), 0.f);
+                    if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut2)) continue;
+                }
+                for (int j0 = jlo; j0 < jhi; j0 += 32) {
+                    const int j = j0 + lane;
+                    Rec rj;
+                    bool keep = false;
+                    if (j < jhi) {
+                        rj = rec[j];
+                        S::shift(rj, im.sx, im.sy, im.sz);
+                        float dx = fmaxf(fmaxf(bl0 - rj.x, rj.x - bh0), 0.f);
+                        float dy = fmaxf(fmaxf(bl1 - rj.y, rj.y - bh1), 0.f);
+                        float dz = fmaxf(fmaxf(bl2 - rj.z, rj.z - bh2), 0.f);
+                        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut2;
+                    }
+                    const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+                    if (cnt + __popc(m) > gcap) {
+                        ovf = true;
+                        break;
+                    }
+                    if (keep) gb[cnt + __popc(m & below)] = rj;
+                    cnt += __popc(m);
+                }
+            }
+            if (ovf) {  // a dense group: plain tiles
+                tile_group_pair<S, kCount>(lv, p, rec, buf, a, lo, g0, hi, lane);
+                __syncwarp();
+                continue;
+            }
+            __syncwarp();  // the buffer's stores are visible to the whole warp
+            // ---- the four sub-cells of 8: 4 lanes per i, each taking every 4th packed pair
+            const int il = lane >> 2, sp = lane & 3;
+            for (int c0 = g0; c0 < g0 + 32 && c0 < hi; c0 += 8) {
+                const int ii = c0 + il;
+                const bool iact = ii < hi;
+                const Rec rs = rec[iact ? ii : c0];
+                float sl0 = rs.x, sl1 = rs.y, sl2 = rs.z, sh0 = rs.x, sh1 = rs.y, sh2 = rs.z;
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {  // over the 8 i of the sub-cell
+                    sl0 = fminf(sl0, __shfl_xor_sync(CRK_FULL_MASK, sl0, o));
+                    sl1 = fminf(sl1, __shfl_xor_sync(CRK_FULL_MASK, sl1, o));
+                    sl2 = fminf(sl2, __shfl_xor_sync(CRK_FULL_MASK, sl2, o));
+                    sh0 = fmaxf(sh0, __shfl_xor_sync(CRK_FULL_MASK, sh0, o));
+                    sh1 = fmaxf(sh1, __shfl_xor_sync(CRK_FULL_MASK, sh1, o));
+                    sh2 = fmaxf(sh2, __shfl_xor_sync(CRK_FULL_MASK, sh2, o));
+                }
+                const float far = 2.0f * cut + 1.0f;
+                const Rec dummy = S::far_dummy(sh0 + far, sh1 + far, sh2 + far);
+                typename S::I2 st;
+                S::init2(p, st, rs);
+                unsigned long long swept = 0;
+                int bc = 0;
+                auto sweep = [&](int n) {
+                    if (n & 1) {
+                        if (lane == 0) S::put2(buf, n, dummy);
+                        ++n;
+                    }
+                    __syncwarp();
+                    for (int k = sp; k < (n >> 1); k += 4) S::template interact2<kCount>(p, st, buf[k]);
+                    __syncwarp();
+                };
+                for (int q0 = 0; q0 < cnt; q0 += 32) {
+                    const int q = q0 + lane;
+                    Rec rj;
+                    bool keep = false;
+                    if (q < cnt) {
+                        rj = gb[q];
+                        float dx = fmaxf(fmaxf(sl0 - rj.x, rj.x - sh0), 0.f);
+                        float dy = fmaxf(fmaxf(sl1 - rj.y, rj.y - sh1), 0.f);
+                        float dz = fmaxf(fmaxf(sl2 - rj.z, rj.z - sh2), 0.f);
+                        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= cut2;
+                    }
+                    const unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
+                    if (keep) S::put2(buf, bc + __popc(m & below), rj);
+                    bc += __popc(m);
+                    if (bc >= depth) {
+                        sweep(bc);
+                        if (kCount) swept += bc;
+                        bc = 0;
+                    }
+                }
+                sweep(bc);
+                if (kCount) swept += bc;
+                S::combine2(st, 1);
+                S::combine2(st, 2);
+                if (sp == 0 && iact) S::finish2(p, st, lv.korder ? ii : lv.kperm[ii]);
+                if (kCount) {
+                    int c = (sp == 0 && iact) ? st.cnt - 1 : 0;  // the self pair (r = 0) is always in range
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(CRK_FULL_MASK, c, o);
+                    if (lane == 0 && c) atomicAdd(p.count, (unsigned long long)c);
+                    const unsigned long long na = __popc(__ballot_sync(CRK_FULL_MASK, sp == 0 && iact));
+                    if (lane == 0 && p.swept) atomicAdd(p.swept, swept * na);
+                }
+            }
+            __syncwarp();  // the buffer is reused by the next group
+        }
     }
 }
 
@@ -1715,18 +1935,22 @@ __device__ __forceinline__ bool positive_shift(float sx, float sy, float sz) {
     return sx > 0.f || (sx == 0.f && (sy > 0.f || (sy == 0.f && sz > 0.f)));
 }
 
+// Gas stages (the Acceleration and Energy passes) use the gas prefix of each
+// leaf and the tile cut h_max(A slice) + h_max(B slice); their conservation
+// sums are taken afterwards from the finished outputs (halfwarp_cons_kernel).
 template <class S, bool kCount, int kEx>
 __global__ void __launch_bounds__(kThreads) pair_kernel_halfwarp(LeafView lv, typename S::P p,
                                                                  const typename S::Rec *__restrict__ rec,
                                                                  double *__restrict__) {
     using Rec = typename S::Rec;
-    static_assert(!S::kCons && !S::kGasOnly, "half-warp arms: gravity-type stages");
+    static_assert(S::kHalfWarp, "half-warp arms: stages with atomic partial sums");
     __shared__ __align__(16) Rec xbuf[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const float rc = S::leaf_cut(p, 0.f, 0.f);
     __shared__ int64_t leaf_slot;
     for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
-        const int alo = lv.leaf_start[a], ahi = lv.leaf_start[a + 1];
+        const int alo = lv.leaf_start[a];
+        const int ahi = S::kGasOnly ? alo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
         const int nsa = (ahi - alo + 15) >> 4;
         const int ib = lv.img_start[a], ie = ib + lv.img_cnt[a];
         int t0 = warp;  // tiles are dealt to the block's warps in turn across the leaf's entries
@@ -1735,7 +1959,8 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_halfwarp(LeafView lv, ty
             const int b = im.b;
             const bool self = b == a && im.sx == 0.f && im.sy == 0.f && im.sz == 0.f;
             if (b < a || (b == a && !self && !positive_shift(im.sx, im.sy, im.sz))) continue;
-            const int blo = lv.leaf_start[b], bhi = lv.leaf_start[b + 1];
+            const int blo = lv.leaf_start[b];
+            const int bhi = S::kGasOnly ? blo + lv.leaf_ngas[b] : lv.leaf_start[b + 1];
             const int nsb = (bhi - blo + 15) >> 4;
             const int ntile = nsa * nsb;
             int t = t0;
@@ -1759,14 +1984,21 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_halfwarp(LeafView lv, ty
                     h1 = fmaxf(h1, __shfl_xor_sync(CRK_FULL_MASK, h1, o));
                     h2 = fmaxf(h2, __shfl_xor_sync(CRK_FULL_MASK, h2, o));
                 }
+                float cut = rc;
+                if constexpr (S::kGasOnly) {  // h_max of each slice: the cut is their sum
+                    float hs = valid ? lv.pos[idx].w : 0.0f;
+#pragma unroll
+                    for (int o = 1; o < 16; o <<= 1) hs = fmaxf(hs, __shfl_xor_sync(CRK_FULL_MASK, hs, o));
+                    cut = S::leaf_cut(p, hs, __shfl_xor_sync(CRK_FULL_MASK, hs, 16));
+                }
                 const float ol0 = __shfl_xor_sync(CRK_FULL_MASK, l0, 16), ol1 = __shfl_xor_sync(CRK_FULL_MASK, l1, 16),
                             ol2 = __shfl_xor_sync(CRK_FULL_MASK, l2, 16), oh0 = __shfl_xor_sync(CRK_FULL_MASK, h0, 16),
                             oh1 = __shfl_xor_sync(CRK_FULL_MASK, h1, 16), oh2 = __shfl_xor_sync(CRK_FULL_MASK, h2, 16);
                 const float gx = fmaxf(fmaxf(ol0 - h0, l0 - oh0), 0.f), gy = fmaxf(fmaxf(ol1 - h1, l1 - oh1), 0.f),
                             gz = fmaxf(fmaxf(ol2 - h2, l2 - oh2), 0.f);
                 // empty halves give NaN/inf gaps: those tiles are skipped too
-                if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= rc * rc * 1.0001f + 1e-6f)) continue;
-                if (!valid) {  // a massless particle outside every cut: contributes exact zeros
+                if (!(fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= cut * cut * 1.0001f + 1e-6f)) continue;
+                if (!valid) {  // a particle outside every cut that contributes exact zeros
                     r = S::far_dummy(1e15f, 1e15f, 1e15f);
                 }
                 if constexpr (kEx == 1) {
@@ -1797,7 +2029,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_halfwarp(LeafView lv, ty
                     }
                     if (acc) S::template interact<kCount>(p, st, r, q);
                 }
-                if (acc) S::flush(p, st, stage_index(lv, idx));
+                if (acc) S::flush(p, st, r, stage_index(lv, idx));
                 if (kCount) {
                     int c = acc ? st.cnt - (diag ? 1 : 0) : 0;  // the self pair of a diagonal tile
 #pragma unroll
@@ -1846,7 +2078,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
                                                         const typename S::Rec *__restrict__ rec,
                                                         double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
-    __shared__ __align__(16) Rec buf[kWarps][kCap];
+    __shared__ __align__(16) Rec buf[kWarps][S::kPair ? kCapPair : kCap];
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1865,10 +2097,18 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
 // Group table of one set of leaves: groups of 32 consecutive kernel-order
 // particles (gas only for gas stages), numbered leaf by leaf.
 struct GroupTable {
-    const int32_t *gstart;  // [n_leaves + 1] first group of each leaf
-    const int32_t *gleaf;   // [groups] leaf of each group
-    int64_t groups;
+    const int32_t *gstart;   // [n_leaves + 1] first group of each leaf
+    const int32_t *gleaf;    // [groups] leaf of each group
+    int64_t groups;          // capacity of the group arrays
+    const int32_t *dgroups;  // device: the groups of this build (<= groups), or NULL for all
 };
+
+// groups of a build: the device count when the arrays have room for more
+__device__ __forceinline__ int64_t group_count(int64_t cap, const int32_t *dgroups) {
+    if (!dgroups) return cap;
+    const int64_t g = *dgroups;
+    return g < cap ? g : cap;
+}
 
 // Tiles, one warp per i-group: every warp works even where a leaf holds fewer
 // groups than a block has warps (gas stages: a leaf of 128 holds about 64 gas).
@@ -1881,7 +2121,8 @@ __global__ void __launch_bounds__(kThreads) pair_group_kernel(LeafView lv, typen
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t grp = next_group(lv, -1, lane); grp < gt.groups; grp = next_group(lv, grp, lane)) {
+    const int64_t ngroups = group_count(gt.groups, gt.dgroups);
+    for (int64_t grp = next_group(lv, -1, lane); grp < ngroups; grp = next_group(lv, grp, lane)) {
         const int64_t a = gt.gleaf[grp];
         const int lo = lv.leaf_start[a];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
@@ -2291,6 +2532,41 @@ __global__ void __launch_bounds__(kThreads) pair_kernel_ring(LeafView lv, typena
     }
 }
 
+// stages with half-warp arms (kHalfWarp): partial sums flushed with atomics
+template <class S, class = void>
+struct has_halfwarp : std::false_type {};
+template <class S>
+struct has_halfwarp<S, std::void_t<decltype(S::kHalfWarp)>> : std::bool_constant<S::kHalfWarp> {};
+
+// Conservation sums of a half-warp arm, from the finished outputs: per-block
+// FP64 partials over the gas particles in kernel order (fixed assignment of
+// particles to blocks and a fixed reduction order: deterministic).
+template <class S>
+__global__ void __launch_bounds__(256) halfwarp_cons_kernel(int64_t n, const float4 *__restrict__ pos,
+                                                            const int32_t *__restrict__ kperm, int korder,
+                                                            typename S::P p, double *__restrict__ part) {
+    __shared__ double sh[8][4];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        if (!(pos[q].w > 0.0f)) continue;  // dark matter
+        double c[4];
+        S::cons_of(p, korder ? (int32_t)q : kperm[q], c);
+        for (int k = 0; k < 4; ++k) acc[k] += c[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(CRK_FULL_MASK, acc[k], o);
+        if (lane == 0) sh[w][k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int v = 0; v < (int)(blockDim.x >> 5); ++v) t += sh[v][threadIdx.x];
+        part[4 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
 __global__ void cons_reduce_kernel(const double *__restrict__ part, int64_t nb, double *__restrict__ out) {
     __shared__ double sh[256];
     for (int k = 0; k < 4; ++k) {
@@ -2317,7 +2593,8 @@ struct GasLists {
     const int32_t *uoff, *unum;
     const uint32_t *ucode;
     const int32_t *gleaf;
-    int64_t groups;
+    int64_t groups;          // capacity of the group arrays
+    const int32_t *dgroups;  // device: the groups of this build, or NULL for all
 };
 
 // j-table entries staged per warp in shared memory (records of at most 48
@@ -2352,7 +2629,8 @@ __global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S:
     float4 *itab = itab_all[warp];
     Rec *table = reinterpret_cast<Rec *>(list_dyn) + (size_t)warp * kTab;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t grp = next_group(lv, -1, lane); grp < gl.groups; grp = next_group(lv, grp, lane)) {
+    const int64_t ngroups = group_count(gl.groups, gl.dgroups);
+    for (int64_t grp = next_group(lv, -1, lane); grp < ngroups; grp = next_group(lv, grp, lane)) {
         const int64_t a = gl.gleaf[grp];
         const int q = (int)(grp - gl.gstart[a]);
         const int lo = lv.leaf_start[a];
@@ -2490,12 +2768,21 @@ __global__ void strided_offsets_kernel(int64_t m, int capr, int capt, int32_t *_
     }
 }
 
-// groups of each leaf, and the leaf of each group
+// groups of each leaf, and the leaf of each group (groups beyond the capacity cap are dropped)
 __global__ void list_group_leaf_kernel(int64_t n_leaves, const int32_t *__restrict__ gstart,
-                                       int32_t *__restrict__ gleaf) {
+                                       int32_t *__restrict__ gleaf, int64_t cap) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n_leaves) return;
-    for (int32_t g = gstart[a]; g < gstart[a + 1]; ++g) gleaf[g] = (int32_t)a;
+    for (int32_t g = gstart[a]; g < gstart[a + 1] && g < cap; ++g) gleaf[g] = (int32_t)a;
+}
+
+// a rebuild's group count and list overflow as bits of the leaves' status word
+__global__ void lists_status_kernel(const int32_t *__restrict__ groups, int64_t cap, const int32_t *__restrict__ ovf,
+                                    int32_t *__restrict__ status) {
+    int32_t s = 0;
+    if (*groups > cap) s |= CRK_LEAVES_GROUP_CAP;
+    if (ovf && *ovf) s |= CRK_LEAVES_LIST_CAP;
+    if (s) atomicOr(status, s);
 }
 
 __global__ void list_group_count_kernel(int64_t n_leaves, const int32_t *__restrict__ leaf_start,
@@ -2536,58 +2823,107 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     int64_t grid = lists ? (nls.groups + kWarps - 1) / kWarps : lv->n_leaves;
     if (grid < 1) grid = 1;
     if (grid > 2147483647LL) grid = 2147483647LL;
-    if (ctx->persistent) {
+    const bool persistent = ctx->persist[kernel_id] != 0;
+    if (persistent) {
         // persistent grid: resident blocks on every SM (4 blocks of 128 threads per SM is the design point)
         int64_t g = (int64_t)ctx->num_sms * 4;
         if (g < grid) grid = g;
     }
+    const bool halfwarp = !lists && ctx->variant[kernel_id] >= CRK_VARIANT_HALFWARP_SHFL &&
+                          ctx->variant[kernel_id] <= CRK_VARIANT_HALFWARP_LOAD && has_halfwarp<S>::value;
+    // half-warp arms take their conservation sums from the finished outputs, in cblocks partials
+    const int64_t cblocks = std::min<int64_t>(crk_grid(n, 256), (int64_t)ctx->num_sms * 8);
+    int64_t nparts = halfwarp ? cblocks : grid;
     double *part = nullptr;
     if (cons) {
-        part = (double *)crk_scratch(ctx, 5, sizeof(double) * 4 * (size_t)grid);
+        part = (double *)crk_scratch(ctx, 5, sizeof(double) * 4 * (size_t)nparts);
         if (!part) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
     }
     const float4 *kpos = gas_pairs ? lv->pos : lv->pos_g;          // gravity: species-mixed kernel order
     const int32_t *kperm = gas_pairs ? lv->kperm : lv->kperm_g;
     gather_kernel<S><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, kpos, kperm, p, rec, korder ? 1 : 0);
     int32_t *queue = nullptr;
-    if (ctx->persistent) {
+    if (persistent) {
         queue = (int32_t *)crk_scratch(ctx, 17, 64);
         if (!queue) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
         CRK_CUDA(ctx, cudaMemsetAsync(queue, 0, sizeof(int32_t), ctx->stream));
     }
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kpos, kperm,
                gas_pairs ? lv->himg_start : lv->gimg_start, gas_pairs ? lv->himg_cnt : lv->gimg_cnt,
-               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue, korder ? 1 : 0};
+               gas_pairs ? lv->himg : lv->gimg, lv->n_leaves, queue, korder ? 1 : 0, ctx->depth[kernel_id]};
     if (p.count) CRK_CUDA(ctx, cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), ctx->stream));
     if (p.swept) CRK_CUDA(ctx, cudaMemsetAsync(p.swept, 0, sizeof(unsigned long long), ctx->stream));
     if (lists) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.unum, nls.ucode, nls.gleaf, nls.groups};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.unum, nls.ucode, nls.gleaf, nls.groups,
+                    nls.dgroups};
         if (p.count)
             list_kernel<S, true><<<(unsigned)grid, kThreads, list_kernel_smem<S, true>(), ctx->stream>>>(v, p, rec, gl,
                                                                                                        part);
         else
             list_kernel<S, false><<<(unsigned)grid, kThreads, list_kernel_smem<S, false>(), ctx->stream>>>(v, p, rec, gl,
                                                                                                          part);
+    } else if (halfwarp) {
+        if constexpr (has_halfwarp<S>::value) {
+            typename S::P q = p;
+            if constexpr (S::kCons) {
+                if (cons && !q.dv3) {  // the Energy pass: its recomputed force, for the conservation sums
+                    q.dv3 = (float *)crk_scratch(ctx, 35, sizeof(float) * 3 * (size_t)n);
+                    if (!q.dv3) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
+                }
+            }
+            S::zero_outputs(q, ctx->stream);
+            const int ex = ctx->variant[kernel_id] - CRK_VARIANT_HALFWARP_SHFL;
+            const unsigned gg = (unsigned)grid;
+            if (p.count) {
+                if (ex == 0) pair_kernel_halfwarp<S, true, 0><<<gg, kThreads, 0, ctx->stream>>>(v, q, rec, part);
+                else if (ex == 1) pair_kernel_halfwarp<S, true, 1><<<gg, kThreads, 0, ctx->stream>>>(v, q, rec, part);
+                else pair_kernel_halfwarp<S, true, 2><<<gg, kThreads, 0, ctx->stream>>>(v, q, rec, part);
+            } else {
+                if (ex == 0) pair_kernel_halfwarp<S, false, 0><<<gg, kThreads, 0, ctx->stream>>>(v, q, rec, part);
+                else if (ex == 1) pair_kernel_halfwarp<S, false, 1><<<gg, kThreads, 0, ctx->stream>>>(v, q, rec, part);
+                else pair_kernel_halfwarp<S, false, 2><<<gg, kThreads, 0, ctx->stream>>>(v, q, rec, part);
+            }
+            if constexpr (S::kCons) {
+                if (cons) {
+                    halfwarp_cons_kernel<S><<<(unsigned)cblocks, 256, 0, ctx->stream>>>(n, kpos, kperm, korder ? 1 : 0,
+                                                                                         q, part);
+                    ++ctx->launches;
+                }
+            }
+        }
     } else if constexpr (!S::kAllVariants) {  // built for lists and tiles only
         if (p.count)
             pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
         else
             pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
     } else {
-        if (ctx->variant[kernel_id] >= CRK_VARIANT_HALFWARP_SHFL && S::kPair) {
+        if (ctx->variant[kernel_id] == CRK_VARIANT_SPLIT8 && S::kPair) {
             if constexpr (S::kPair) {
-                S::zero_outputs(p, ctx->stream);
-                const int ex = ctx->variant[kernel_id] - CRK_VARIANT_HALFWARP_SHFL;
-                const unsigned gg = (unsigned)grid;
-                if (p.count) {
-                    if (ex == 0) pair_kernel_halfwarp<S, true, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                    else if (ex == 1) pair_kernel_halfwarp<S, true, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                    else pair_kernel_halfwarp<S, true, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                } else {
-                    if (ex == 0) pair_kernel_halfwarp<S, false, 0><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                    else if (ex == 1) pair_kernel_halfwarp<S, false, 1><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
-                    else pair_kernel_halfwarp<S, false, 2><<<gg, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+                // a bounded grid: every block's warps own a slot of the candidate buffer
+                constexpr int kGcap = 4096;
+                static int occ[2] = {0, 0};  // resident blocks per SM, from the kernel's registers and shared memory
+                int &oc = occ[p.count ? 1 : 0];
+                if (!oc) {
+                    cudaFuncAttributes fa{};
+                    const cudaError_t e = p.count ? cudaFuncGetAttributes(&fa, pair_kernel_split<S, true>)
+                                                  : cudaFuncGetAttributes(&fa, pair_kernel_split<S, false>);
+                    int by_regs = 16, by_smem = 16;
+                    if (e == cudaSuccess && fa.numRegs > 0) {
+                        const int regs = (fa.numRegs + 7) / 8 * 8;  // allocated per thread in units of 8
+                        by_regs = 65536 / (regs * kThreads);
+                        by_smem = (int)((228u * 1024u) / ((unsigned)fa.sharedSizeBytes + 1024u));
+                    } else {
+                        cudaGetLastError();
+                    }
+                    oc = std::max(1, std::min(16, std::min(by_regs, by_smem)));
                 }
+                const int64_t g = std::min<int64_t>(grid, (int64_t)ctx->num_sms * oc);
+                Rec *gbuf = (Rec *)crk_scratch(ctx, 37, sizeof(Rec) * (size_t)g * kWarps * kGcap);
+                if (!gbuf) return crk_fail(ctx, CRK_ENOMEM, "stage scratch");
+                if (p.count)
+                    pair_kernel_split<S, true><<<(unsigned)g, kThreads, 0, ctx->stream>>>(v, p, rec, gbuf, kGcap);
+                else
+                    pair_kernel_split<S, false><<<(unsigned)g, kThreads, 0, ctx->stream>>>(v, p, rec, gbuf, kGcap);
             }
         } else if (ctx->variant[kernel_id] == CRK_VARIANT_TILES16) {
             if constexpr (S::kPair) {  // gravity stages: packed two-candidate sweeps
@@ -2619,7 +2955,7 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
             pair_kernel<S, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
         }
     }
-    if (cons) cons_reduce_kernel<<<1, 256, 0, ctx->stream>>>(part, grid, cons);
+    if (cons) cons_reduce_kernel<<<1, 256, 0, ctx->stream>>>(part, nparts, cons);
     ctx->launches += 2 + (cons ? 1 : 0);
     CRK_LAUNCH_CHECK(ctx, "pair kernel");
     return CRK_OK;
@@ -2739,8 +3075,8 @@ int crk_hydro_accel(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *
              hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count, dvdx};
     p.vsig_h = vsig_h_max;
     p.sig_beta = sig_beta;
-    if (dvdx) return run_stage<HydroAccelStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
-    return run_stage<HydroAccelStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+    if (dvdx) return run_stage<HydroAccelStage<true>>(ctx, lv, p, true, CRK_K_ACCEL, conservation);
+    return run_stage<HydroAccelStage<false>>(ctx, lv, p, true, CRK_K_ACCEL, conservation);
 }
 
 int crk_hydro_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params *hp, const float *m, const float *v3,
@@ -2754,8 +3090,8 @@ int crk_hydro_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params 
     HydroP p{m, v3, u, V, rho, A, B, gradA, gradB, nullptr, dudt, conservation,
              hp->gamma, hp->alpha, hp->beta, hp->eta2, lv->n, (unsigned long long *)pair_count, dvdx};
     p.vstar = vstar3;
-    if (dvdx) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
-    return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation);
+    if (dvdx) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_ENERGY, conservation);
+    return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_ENERGY, conservation);
 }
 
 int crk_corrections_adjoint(crk_ctx *ctx, const crk_leaves *lv, const float *V, const float *Abar,
@@ -2801,14 +3137,17 @@ int crk_hydro_adjoint(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params
     return run_stage<HydroAdjStage>(ctx, lv, p, true, CRK_K_HYDRO);
 }
 
+// reuse: a rebuild of one-pass gas lists into the buffers of the first build (group arrays with
+// room for 1/8 more groups); no host synchronisation, overflows go to the leaves' status word.
 template <bool kGas>
-static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
+static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out, bool reuse) {
     const int64_t nl = lv->n_leaves, n = lv->n;
     if (nl == 0 || n == 0 || (kGas && lv->n_gas == 0)) return CRK_OK;
+    if (reuse && (!kGas || !out.onepass)) return crk_fail(ctx, CRK_ESTATE, "rebuild: lists without fixed capacities");
     cudaStream_t st = ctx->stream;
     using LS = ListStage<kGas>;
-    int32_t *gstart = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(nl + 1));
-    int32_t *cnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)n);
+    int32_t *gstart = reuse ? out.gstart : (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(nl + 1));
+    int32_t *cnt = reuse ? out.cnt : (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)n);
     int32_t *ng = (int32_t *)crk_scratch(ctx, 6, sizeof(int32_t) * (size_t)(nl + 1));
     int32_t *tot = (int32_t *)crk_scratch(ctx, 7, 64);  // [0] groups, [1] rows, [2] table entries, [4] largest table
     if (!gstart || !cnt || !ng || !tot) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
@@ -2817,21 +3156,41 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     ++ctx->launches;
     int rc = crk_exclusive_scan_i32(ctx, ng, gstart, nl + 1, tot);
     if (rc) return rc;
+    int32_t *dgroups = lv->dev + (kGas ? 1 : 2);  // this build's group count, for the kernels
+    CRK_CUDA(ctx, cudaMemcpyAsync(dgroups, tot, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, kGas ? lv->pos : lv->pos_g,
                kGas ? lv->kperm : lv->kperm_g, kGas ? lv->himg_start : lv->gimg_start,
-               kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg, nl, nullptr, 0};
+               kGas ? lv->himg_cnt : lv->gimg_cnt, kGas ? lv->himg : lv->gimg, nl, nullptr, 0, 32};
     typename LS::Rec *rec = (typename LS::Rec *)crk_scratch(ctx, 4, sizeof(typename LS::Rec) * (size_t)n);
     if (!rec) return crk_fail(ctx, CRK_ENOMEM, "neighbour list scratch");
+    const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
+    const int capr = kGasListCapRows, capt = kGasTableCap;
+    if (reuse) {
+        const int64_t capg = out.groups;
+        list_group_leaf_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, gstart, out.gleaf, capg);
+        gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
+        CRK_CUDA(ctx, cudaMemsetAsync(tot + 5, 0, sizeof(int32_t), st));
+        ListP pf{out.list, out.ucode, gstart, out.goff, out.uoff, cnt, out.unum, nullptr, tot + 5, capr, capt, rc2, n,
+                 nullptr};
+        const GroupTable gt{gstart, out.gleaf, capg, dgroups};
+        const unsigned gg = (unsigned)((capg + kWarps - 1) / kWarps > 0 ? (capg + kWarps - 1) / kWarps : 1);
+        pair_group_kernel<LS, false><<<gg, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
+        lists_status_kernel<<<1, 1, 0, st>>>(tot, capg, tot + 5, lv->dev);
+        ctx->launches += 4;
+        CRK_LAUNCH_CHECK(ctx, "neighbour lists");
+        return CRK_OK;
+    }
     int32_t ngroups = 0;
     CRK_CUDA(ctx, cudaMemcpyAsync(&ngroups, tot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CRK_CUDA(ctx, cudaStreamSynchronize(st));
-    int32_t *gleaf = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups > 0 ? ngroups : 1));
+    // one-pass lists: room for 1/8 more groups than this build holds (a rebuild of moved particles reuses them)
+    const int64_t capg = (int64_t)ngroups + ngroups / 8 + 64;
+    int32_t *gleaf = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)capg);
     if (!gleaf) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
-    list_group_leaf_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, gstart, gleaf);
-    const GroupTable gt{gstart, gleaf, ngroups};
+    list_group_leaf_kernel<<<crk_grid(nl, 256), 256, 0, st>>>(nl, gstart, gleaf, capg);
+    const GroupTable gt{gstart, gleaf, ngroups, nullptr};
     const unsigned ggrid = (unsigned)((ngroups + kWarps - 1) / kWarps > 0 ? (ngroups + kWarps - 1) / kWarps : 1);
-    const float rc2 = lv->r_cut_grav * lv->r_cut_grav;
-    int32_t *ucnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
+    int32_t *ucnt = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(capg + 1));
     if (!ucnt) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
     gather_kernel<LS><<<crk_grid(n, 256), 256, 0, st>>>(n, v.pos, v.kperm, ListP{}, rec, 0);
     ctx->launches += 2;
@@ -2842,15 +3201,14 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     // Gas lists: one pass into fixed capacities (a lane's list and a group's table), which the
     // adaptive smoothing lengths keep well above the largest counts; the exact two-pass build
     // (count, scan, fill) runs only if something overflowed.
-    const int capr = kGasListCapRows, capt = kGasTableCap;
     bool done = false;
-    if (kGas && (int64_t)ngroups * capt < 2147483647LL) {
-        goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
-        uoff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(ngroups + 1));
-        list = (uint16_t *)crk_leaves_alloc(ctx, lv, sizeof(uint16_t) * (size_t)ngroups * capr * 32);
-        ucode = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)ngroups * capt);
+    if (kGas && capg * capt < 2147483647LL) {
+        goff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(capg + 1));
+        uoff = (int32_t *)crk_leaves_alloc(ctx, lv, sizeof(int32_t) * (size_t)(capg + 1));
+        list = (uint16_t *)crk_leaves_alloc(ctx, lv, sizeof(uint16_t) * (size_t)capg * capr * 32);
+        ucode = (uint32_t *)crk_leaves_alloc(ctx, lv, sizeof(uint32_t) * (size_t)capg * capt);
         if (!goff || !uoff || !list || !ucode) return crk_fail(ctx, CRK_ENOMEM, "neighbour list allocation");
-        strided_offsets_kernel<<<crk_grid(ngroups + 1, 256), 256, 0, st>>>(ngroups + 1, capr, capt, goff, uoff);
+        strided_offsets_kernel<<<crk_grid(capg + 1, 256), 256, 0, st>>>(capg + 1, capr, capt, goff, uoff);
         CRK_CUDA(ctx, cudaMemsetAsync(tot + 5, 0, sizeof(int32_t), st));
         ListP pf{list, ucode, gstart, goff, uoff, cnt, ucnt, nullptr, tot + 5, capr, capt, rc2, n, nullptr};
         pair_group_kernel<LS, false><<<ggrid, kThreads, 0, st>>>(v, pf, rec, gt, nullptr);
@@ -2861,8 +3219,8 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
         CRK_CUDA(ctx, cudaStreamSynchronize(st));
         if (ovf == 0) {
             done = true;
-            entries = (int64_t)ngroups * capr * 32;
-            tsize = (int64_t)ngroups * capt;
+            entries = (int64_t)capg * capr * 32;
+            tsize = (int64_t)capg * capt;
         } else if (ctx->trace) {
             fprintf(stderr, "[crk] gas lists: a list or table exceeded its capacity, exact build\n");
         }
@@ -2918,13 +3276,15 @@ static int build_lists(crk_ctx *ctx, crk_leaves *lv, crk_nlist &out) {
     out.goff = goff;
     out.cnt = cnt;
     out.list = list;
-    out.groups = ngroups;
+    out.groups = done ? capg : ngroups;
+    out.dgroups = dgroups;
+    out.onepass = done;
     out.entries = entries;
     return CRK_OK;
 }
 
-int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas) {
-    return gas ? build_lists<true>(ctx, lv, lv->gas_lists) : build_lists<false>(ctx, lv, lv->grav_lists);
+int crk_build_lists(crk_ctx *ctx, crk_leaves *lv, bool gas, bool reuse) {
+    return gas ? build_lists<true>(ctx, lv, lv->gas_lists, reuse) : build_lists<false>(ctx, lv, lv->grav_lists, reuse);
 }
 
 // ---------------------------------------------------------------------------
@@ -2984,11 +3344,12 @@ int grav_short_noalloc(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params
     // every record is rewritten before it is read, so nothing needs clearing
     gather_kernel<GravStage><<<crk_grid(n, 256), 256, 0, ctx->stream>>>(n, lv->pos_g, lv->kperm_g, p, rec, 0);
     LeafView v{lv->leaf_start, lv->leaf_ngas, lv->bbox, lv->hmax, lv->pos_g, lv->kperm_g, lv->gimg_start,
-               lv->gimg_cnt, lv->gimg, lv->n_leaves, nullptr, 0};
+               lv->gimg_cnt, lv->gimg, lv->n_leaves, nullptr, 0, 32};
     const int64_t grid = lv->n_leaves < 1 ? 1 : lv->n_leaves;
     const crk_nlist &nls = lv->grav_lists;
     if (nls.list && ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_LISTS) {
-        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.unum, nls.ucode, nls.gleaf, nls.groups};
+        GasLists gl{nls.gstart, nls.goff, nls.cnt, nls.list, nls.uoff, nls.unum, nls.ucode, nls.gleaf, nls.groups,
+                    nls.dgroups};
         const int64_t lgrid = (nls.groups + kWarps - 1) / kWarps;
         list_kernel<GravStage, false><<<(unsigned)(lgrid > 0 ? lgrid : 1), kThreads,
                                         list_kernel_smem<GravStage, false>(), ctx->stream>>>(v, p, rec, gl, nullptr);
@@ -3077,8 +3438,8 @@ int crk_stage_forces(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *
                  limited ? C(K::dvdx) : nullptr};
         p.vsig_h = vsig_h;
         p.sig_beta = sig_beta;
-        if (limited) rc = run_stage<HydroAccelStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, nullptr, true);
-        else rc = run_stage<HydroAccelStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, nullptr, true);
+        if (limited) rc = run_stage<HydroAccelStage<true>>(ctx, lv, p, true, CRK_K_ACCEL, nullptr, true);
+        else rc = run_stage<HydroAccelStage<false>>(ctx, lv, p, true, CRK_K_ACCEL, nullptr, true);
         if (rc) return rc;
     }
     if (gravity) {
@@ -3116,8 +3477,8 @@ int crk_stage_energy(crk_ctx *ctx, const crk_leaves *lv, const crk_hydro_params 
              C(K::gB), nullptr, C(K::du), conservation, hp->gamma, hp->alpha, hp->beta, hp->eta2, n, nullptr,
              limited ? C(K::dvdx) : nullptr};
     p.vstar = vs;
-    if (limited) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_HYDRO, conservation, true);
-    return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_HYDRO, conservation, true);
+    if (limited) return run_stage<HydroEnergyStage<true>>(ctx, lv, p, true, CRK_K_ENERGY, conservation, true);
+    return run_stage<HydroEnergyStage<false>>(ctx, lv, p, true, CRK_K_ENERGY, conservation, true);
 }
 
 namespace {

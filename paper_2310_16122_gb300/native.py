@@ -21,8 +21,12 @@ CRK_ESTATE = -5
 CRK_ETIMEOUT = -6
 CRK_ETOOLARGE = -7
 NOALLOC_MAX_PARTICLES = 1 << 21
+# bits of the leaves' status word (crk_leaves_status)
+LEAVES_STATUS = {1: "bad position", 2: "bad h", 4: "gas count", 8: "leaf size", 16: "h_max", 32: "candidates",
+                 64: "image capacity", 128: "group capacity", 256: "list capacity", 512: "internal"}
 KERNELS = {"geometry": 0, "corrections": 1, "hydro": 2, "gravity": 3, "gravity_adjoint": 4, "geometry_adjoint": 5,
-           "extras": 6}
+           "extras": 6, "accel": 7, "energy": 8}
+N_KERNELS = 9
 VARIANT_LISTS = 0
 VARIANT_TILES = 1
 VARIANT_TILES16 = 2
@@ -31,7 +35,9 @@ VARIANT_RING16 = 4
 VARIANT_HALFWARP_SHFL = 5
 VARIANT_HALFWARP_SMEM = 6
 VARIANT_HALFWARP_LOAD = 7
-N_VARIANTS = 8
+VARIANT_SPLIT8 = 8
+N_VARIANTS = 9
+TUNE_COLS = N_VARIANTS + 5  # per kernel: variant timings, launch mode off/on, depth 32/64/96
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
                 -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT", -7: "CRK_ETOOLARGE"}
 
@@ -100,6 +106,8 @@ SIGNATURES = {
     "crk_set_trace": [_P, _I],
     "crk_set_variant": [_P, _I, _I],
     "crk_set_persistent": [_P, _I],
+    "crk_set_launch": [_P, _I, _I, _I],
+    "crk_get_launch": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "crk_get_variant": [_P, _I, ctypes.POINTER(_I)],
     "crk_build_leaves": [_P, ctypes.POINTER(crk_particles), _P, ctypes.POINTER(crk_leaf_params), ctypes.POINTER(_P)],
     "crk_build_leaves_batch": [_P, ctypes.POINTER(crk_batch), _P, ctypes.POINTER(crk_leaf_params),
@@ -131,6 +139,11 @@ SIGNATURES = {
     "crk_step_graph_create": [_P, _P, ctypes.POINTER(crk_grav_params), ctypes.POINTER(crk_hydro_params),
                               ctypes.POINTER(crk_step_io), ctypes.POINTER(_P)],
     "crk_graph_launch": [_P],
+    "crk_rebuild_step_graph_create": [_P, _P, ctypes.POINTER(crk_batch), _P, ctypes.POINTER(crk_grav_params),
+                                      ctypes.POINTER(crk_hydro_params), ctypes.POINTER(crk_step_io), ctypes.POINTER(_P)],
+    "crk_leaves_rebuild": [_P, _P, ctypes.POINTER(crk_particles), _P],
+    "crk_leaves_rebuild_batch": [_P, _P, ctypes.POINTER(crk_batch), _P],
+    "crk_leaves_status": [_P, _P, ctypes.POINTER(_I)],
     "crk_step_profile": [_P, _I],
     "crk_step_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)],
     "crk_graph_destroy": [_P],

@@ -19,3 +19,14 @@ def orc():
 
     O.build()
     return O
+
+
+def pytest_sessionfinish(session, exitstatus):
+    out = os.environ.get("CRK_ERRORS_OUT")
+    if out:
+        import json
+
+        from tests import _errors
+
+        with open(out, "w") as fh:
+            json.dump(_errors.RECORDS, fh, indent=0)

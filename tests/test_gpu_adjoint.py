@@ -16,6 +16,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2310_16122_gb300 import workloads as W
+from tests._errors import check, cut_boundary_particles
 
 pytestmark = pytest.mark.gpu
 
@@ -35,8 +36,10 @@ def run():
     b = W.adjoint_box()
     ctx = api.Context(0)
     db = api.DeviceBox(b)
-    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
-    pos3 = torch.stack([db.x, db.y, db.z]).contiguous().requires_grad_(True)
+    # the leaves are built from the rows of the positions tensor the loss differentiates
+    pos3 = torch.stack([db.x, db.y, db.z]).contiguous()
+    lv = api.build_leaves(ctx, pos3[0], pos3[1], pos3[2], db.species, db.h, db.L, db.lp)
+    pos3.requires_grad_(True)
     m = db.m.clone().requires_grad_(True)
     a = AG.gravity(pos3, m, ctx, lv, db.gp)
     V, rho = AG.geometry(pos3, m, ctx, lv)
@@ -69,10 +72,8 @@ def test_gradient_matches_oracle_analytic(run):
     _, rho, _ = O.geometry(I)
     ref_loss = float(np.sum(acc * acc) + rho[b.species == 0].sum())
     assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss)
-    e_x = rel_l2(gx, ogx1 + ogx2)
-    e_m = rel_l2(gm, ogm1 + ogm2)
-    print(f"adjoint vs oracle: positions {e_x:.2e} masses {e_m:.2e}")
-    assert e_x < 1e-4 and e_m < 1e-4
+    check("adjoint/config3", "gx", gx, ogx1 + ogx2, exclude=cut_boundary_particles(I.pos, b.L, b.r_cut))
+    check("adjoint/config3", "gm", gm, ogm1 + ogm2)
 
 
 def test_gradient_matches_fp64_central_differences(run):
@@ -103,3 +104,27 @@ def test_gradient_matches_fp64_central_differences(run):
         errs.append(abs(gm[k] - fd) / (abs(fd) + 1e-3 * sm))
     print(f"adjoint vs FD: max {max(errs):.2e} median {np.median(errs):.2e}")
     assert max(errs) < 1e-3
+
+
+def test_stale_leaves_are_refused():
+    """Positions other than those the leaves were built from raise CRK_ESTATE; equal copies pass."""
+    from paper_2310_16122_gb300 import api, autograd as AG, native as N
+
+    b = W.clustered_box(12, 1, 52)
+    ctx = api.Context(0)
+    db = api.DeviceBox(b)
+    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+    m = db.m.clone().requires_grad_(True)
+    same = torch.stack([db.x, db.y, db.z]).requires_grad_(True)  # another tensor, equal values
+    a = AG.gravity(same, m, ctx, lv, db.gp)
+    (a * a).sum().backward()
+    assert same.grad is not None and bool(torch.isfinite(same.grad).all())
+    moved = torch.stack([db.x, db.y, db.z]).clone()
+    moved[0, 7] += 0.01
+    for f in (lambda p: AG.gravity(p, m, ctx, lv, db.gp), lambda p: AG.geometry(p, m, ctx, lv)):
+        with pytest.raises(N.CrkError) as e:
+            f(moved.requires_grad_(True))
+        assert e.value.status == N.CRK_ESTATE
+    with pytest.raises(N.CrkError) as e:
+        AG.gravity(moved[:, :-1], m, ctx, lv, db.gp)
+    assert e.value.status == N.CRK_ESTATE

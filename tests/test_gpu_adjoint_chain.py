@@ -14,6 +14,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2310_16122_gb300 import workloads as W
+from tests._errors import check
 
 pytestmark = pytest.mark.gpu
 
@@ -76,9 +77,8 @@ def test_corrections_adjoint_matches_oracle(api, name, variant):
     gx, gV, gns = api.corrections_adjoint(ctx, lv, _t(V), _t(cb[0]), _t(cb[1].T), _t(cb[2].T), _t(cb[3].T))
     torch.cuda.synchronize()
     assert int(gns.cpu()) == 0
-    ex, eV = rel_l2(gx.cpu().numpy().T[gas], ox[gas]), rel_l2(gV.cpu().numpy()[gas], oV[gas])
-    print(name, variant, f"xbar {ex:.2e} Vbar {eV:.2e}")
-    assert ex <= 1e-4 and eV <= 1e-4
+    check(f"corrections_adjoint/{name}/v{variant}", "xbar", gx.cpu().numpy().T[gas], ox[gas], "adj")
+    check(f"corrections_adjoint/{name}/v{variant}", "Vbar", gV.cpu().numpy()[gas], oV[gas], "adj")
     assert np.all(gx.cpu().numpy()[:, ~gas] == 0) and np.all(gV.cpu().numpy()[~gas] == 0)
 
 
@@ -103,14 +103,11 @@ def test_hydro_adjoint_matches_oracle(api, name, variant):
     t = [_t(ins[0]), _t(ins[1]), _t(ins[2]), _t(ins[3].T), _t(ins[4].T), _t(ins[5].T)]
     gg = api.hydro_adjoint(ctx, lv, db.hp, db.m, db.v3, db.u, *t, _t(dvbar.T), _t(dubar))
     torch.cuda.synchronize()
-    errs = {}
     for k, v in gg.items():
         g = v.cpu().numpy()
         g = g.T if g.ndim == 2 else g
-        errs[k] = rel_l2(g[gas], og[k][gas])
+        check(f"hydro_adjoint/{name}/v{variant}", k + "bar", g[gas], og[k][gas], "adj")
         assert np.all(g[~gas] == 0), k
-    print(name, variant, {k: f"{e:.1e}" for k, e in errs.items()})
-    assert max(errs.values()) <= 1e-4, errs
 
 
 @pytest.mark.parametrize("name", ["clustered12", "clustered24"])
@@ -146,9 +143,8 @@ def test_chain_gradient_through_autograd(api, name):
     torch.cuda.synchronize()
     got = dict(x=pos.grad.cpu().numpy().T, m=m.grad.cpu().numpy(), v=v.grad.cpu().numpy().T,
                u=u.grad.cpu().numpy())
-    errs = {k: rel_l2(got[k][gas], want[k][gas]) for k in want}
-    print(name, {k: f"{e:.1e}" for k, e in errs.items()})
-    assert max(errs.values()) <= 1e-4, errs
+    for k in want:
+        check(f"chain_autograd/{name}", k + "bar", got[k][gas], want[k][gas], "adj")
 
 
 def test_fused_chain_equals_autograd_chain(api):

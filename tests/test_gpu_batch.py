@@ -14,6 +14,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2310_16122_gb300 import workloads as W
+from tests._errors import check
 
 pytestmark = pytest.mark.gpu
 
@@ -90,8 +91,8 @@ def test_batched_step_matches_per_box(setup):
         I = O.from_box(b)
         ref = O.forward(I, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
         gas = b.species == 0
-        assert rel_l2(acc[sl], ref["acc"]) <= 2e-5
-        assert rel_l2(dv[sl][gas], ref["dv"][gas]) <= 2e-5
+        check(f"batch/box{k}", "acc", acc[sl], ref["acc"])
+        check(f"batch/box{k}", "dv", dv[sl][gas], ref["dv"][gas])
     assert counts[1] == tot_h and counts[2] == tot_g
     # candidate evaluations bound the in-range pairs from above (tiles sweep more, lists add the self pair)
     swept = io.swept_count.cpu().numpy()
@@ -132,17 +133,34 @@ def test_autotuner(setup):
     ctx.set_variant("gravity", 0)  # build the gravity lists too, so every variant can be timed
     ctx.set_variant("gravity_adjoint", 0)
     lv = api.build_leaves_batch(ctx, dbt)
-    io = api.StepIO(ctx, dbt)
+    io = api.StepIO(ctx, dbt, extras=True)
     res = api.tune(ctx, lv, dbt, io, reps=2)
-    for k, (best, ms) in res.items():
-        assert ms[best] > 0 and ms[best] == min(t for t in ms if t > 0)
-        assert ctx.get_variant(k) == best
+    assert set(res) == set(api.N.KERNELS)  # all nine pair kernels, Extras and both hydro passes included
+    for k, r in res.items():
+        mv, ml, md = r["ms"]["variant"], r["ms"]["launch"], r["ms"]["depth"]
+        best = r["variant"]
+        # the variant is the fastest one timed, then the launch mode of that variant, then the depth
+        assert mv[best] > 0 and mv[best] == min(t for t in mv if t > 0), k
+        assert min(ml) > 0 and ml[int(r["persistent"])] == min(ml), k
+        assert ctx.get_variant(k) == best and ctx.get_launch(k) == (r["persistent"], r["depth"]), k
+        if k.startswith("gravity") and best == 1:
+            assert min(md) > 0 and md[r["depth"] // 32 - 1] == min(md), k
+        else:
+            assert r["depth"] == 32 and max(md) < 0, k
+    # half-warp arms are timed for the gravity kernels and the hydro passes, not for the others
+    for k in ("gravity", "gravity_adjoint", "hydro", "accel", "energy"):
+        assert min(res[k]["ms"]["variant"][5:8]) > 0, k
+    for k in ("geometry", "corrections", "geometry_adjoint", "extras"):
+        assert max(res[k]["ms"]["variant"][5:8]) < 0, k
+    # the split sweep: gravity kernels only
+    for k, r in res.items():
+        assert (r["ms"]["variant"][8] > 0) == k.startswith("gravity"), k
     api.step(ctx, lv, dbt, io)
     torch.cuda.synchronize()
     for k, b in enumerate(boxes[:2]):
         sl = slice(int(dbt.box_start[k]), int(dbt.box_start[k + 1]))
         ref, _ = O.gravity(O.from_box(b))
-        assert rel_l2(io.acc.cpu().numpy().T[sl], ref) <= 2e-5
+        check(f"batch_tuned/box{k}", "acc", io.acc.cpu().numpy().T[sl], ref)
 
 
 def test_persistent_launch_matches(setup):

@@ -17,6 +17,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2310_16122_gb300 import workloads as W
+from tests._errors import check, cut_boundary_particles
 
 pytestmark = pytest.mark.gpu
 
@@ -61,18 +62,16 @@ def test_clustered_2x64_full(tmp_path):
         assert np.array_equal(g["export"][key + "_list"], lst)
     ref = O.forward(I, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
     gas = b.species == 0
-    e = {"acc": rel_l2(g["acc"], ref["acc"]), "dv": rel_l2(g["dv"][gas], ref["dv"][gas]),
-         "du": rel_l2(g["du"][gas], ref["du"][gas]), "V": rel_l2(g["V"][gas], ref["V"][gas]),
-         "A": rel_l2(g["A"][gas], ref["A"][gas]), "B": rel_l2(g["B"][gas], ref["B"][gas]),
-         "gA": rel_l2(g["gA"][gas], ref["gA"][gas]), "gB": rel_l2(g["gB"][gas], ref["gB"][gas])}
+    where = "clustered_2x64^3"
+    check(where, "acc", g["acc"], ref["acc"])
+    for k in ("dv", "du", "V", "rho", "A", "B", "gA", "gB"):
+        check(where, k, g[k][gas], ref[k][gas])
     ogx, ogm = O.gravity_adjoint(I, 2.0 * ref["acc"])
     ogx2, ogm2 = O.geometry_adjoint(I, gas.astype(np.float64))
-    e.update(grav_gx=rel_l2(g["gx"], ogx), grav_gm=rel_l2(g["gm"], ogm), geom_gx=rel_l2(g["gx2"], ogx2),
-             geom_gm=rel_l2(g["gm2"], ogm2))
-    print("clustered 2x64^3:", {k: f"{v:.2e}" for k, v in e.items()})
-    assert e["acc"] <= 2e-5 and e["dv"] <= 2e-5 and e["du"] <= 5e-5
-    assert e["V"] < 1e-5 and e["A"] < 1e-5 and max(e["B"], e["gA"], e["gB"]) < 1e-3
-    assert max(e["grav_gx"], e["grav_gm"], e["geom_gx"], e["geom_gm"]) < 1e-4
+    check(where, "grav_gx", g["gx"], ogx, "gx", exclude=cut_boundary_particles(I.pos, b.L, b.r_cut))
+    check(where, "grav_gm", g["gm"], ogm, "gm")
+    check(where, "geom_gx", g["gx2"], ogx2, "gx")
+    check(where, "geom_gm", g["gm2"], ogm2, "gm")
 
 
 def test_large_2x256_sampled():
@@ -94,14 +93,13 @@ def test_large_2x256_sampled():
     sample = rng.choice(b.n, 384, replace=False)
     r = O.sampled_chain(I, sample, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
     gas_s = sample[b.species[sample] == 0]
-    e = {"acc": rel_l2(g["acc"][sample], r["acc"][sample]),
-         "gx": rel_l2(g["gx"][sample], r["gx"][sample]), "gm": rel_l2(g["gm"][sample], r["gm"][sample]),
-         "dv": rel_l2(g["dv"][gas_s], r["dv"][gas_s]), "du": rel_l2(g["du"][gas_s], r["du"][gas_s]),
-         "V": rel_l2(g["V"][gas_s], r["V"][gas_s]), "A": rel_l2(g["A"][gas_s], r["A"][gas_s]),
-         "B": rel_l2(g["B"][gas_s], r["B"][gas_s])}
-    print("large 2x256^3 sample:", {k: f"{v:.2e}" for k, v in e.items()})
-    assert e["acc"] <= 2e-5 and e["dv"] <= 2e-5 and e["du"] <= 5e-5
-    assert e["V"] < 1e-5 and e["A"] < 1e-5 and e["B"] < 1e-3 and max(e["gx"], e["gm"]) < 1e-4
+    where = "large_2x256^3/sample384"
+    for k in ("acc", "gm"):
+        check(where, k, g[k][sample], r[k][sample])
+    check(where, "gx", g["gx"][sample], r["gx"][sample],
+          exclude=cut_boundary_particles(I.pos, b.L, b.r_cut, subset=sample))
+    for k in ("dv", "du", "V", "A", "B"):
+        check(where, k, g[k][gas_s], r[k][gas_s])
     # FP64 conservation sums of the whole box: momentum and energy rates vanish up to FP32 rounding
     cons = g["cons"]
     gas = b.species == 0

@@ -1,10 +1,11 @@
 """GPU parity: libcrk (through its C ABI) against the FP64 oracle on the same seeded inputs.
 
 Integer results (leaf permutation, leaf starts, leaf-pair lists) must be
-bit-exact.  Floating point uses the global relative L2 error
-E = sqrt(sum |dx|^2 / sum |x_ref|^2): gravity and hydro accelerations
-E <= 2e-5, du/dt E <= 5e-5; volumes, densities, corrections and adjoints are
-reported with looser sanity bounds (no gate is specified for them).
+bit-exact.  Floating point is gated on the global relative L2 error
+E = sqrt(sum |dx|^2 / sum |x_ref|^2) (gravity and hydro accelerations
+E <= 2e-5, du/dt E <= 5e-5) and on the largest per-particle relative error
+e_i = |dx_i| / (|x_ref,i| + 0.01 rms|x_ref|); the gates of the other outputs
+are in tests/_errors.py.
 Pair counts come from FP32 range tests on the GPU and FP64 tests in the
 oracle; they may differ only for pairs within rounding of the cut.
 """
@@ -15,14 +16,9 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2310_16122_gb300 import workloads as W
+from tests._errors import check, cut_boundary_particles
 
 pytestmark = pytest.mark.gpu
-
-
-def rel_l2(a, b):
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
-    return float(np.sqrt(np.sum((a - b) ** 2) / max(np.sum(b * b), 1e-300)))
 
 
 @pytest.fixture(scope="module")
@@ -148,8 +144,9 @@ def test_error_statuses(api, ctx):
 VARIANTS = [0, 1, 2, 3, 4]
 VARIANT_IDS = ["lists", "tiles", "tiles16", "tiles8", "ring16"]
 # the gravity kernels also have the half-warp leaf-pair arms (shuffle, shared memory, second load)
-GRAV_VARIANTS = VARIANTS + [5, 6, 7]
-GRAV_VARIANT_IDS = VARIANT_IDS + ["halfwarp_shfl", "halfwarp_smem", "halfwarp_load"]
+# and the split sweep over 8-particle sub-cells
+GRAV_VARIANTS = VARIANTS + [5, 6, 7, 8]
+GRAV_VARIANT_IDS = VARIANT_IDS + ["halfwarp_shfl", "halfwarp_smem", "halfwarp_load", "split8"]
 
 
 @pytest.mark.parametrize("variant", GRAV_VARIANTS, ids=GRAV_VARIANT_IDS)
@@ -165,8 +162,7 @@ def test_gravity_parity(api, ctx, name, variant):
         ctx.set_variant("gravity", 1)
     I = O.from_box(b)
     ref, npairs = O.gravity(I)
-    e = rel_l2(a.cpu().numpy().T, ref)
-    assert e <= 2e-5, e
+    check(f"gravity/{name}/v{variant}", "acc", a.cpu().numpy().T, ref)
     assert abs(int(cnt.item()) - npairs) <= boundary_pairs(b, False)
 
 
@@ -179,7 +175,8 @@ def set_gas_variant(ctx, variant):
         ctx.set_variant(k, (1 if k.startswith("gravity") else 0) if variant is None else variant)
 
 
-@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
+# the hydro pass also has the half-warp arms (the other gas kernels then run tiles)
+@pytest.mark.parametrize("variant", GRAV_VARIANTS, ids=GRAV_VARIANT_IDS)
 @pytest.mark.parametrize("name", ["tiny_mesh", "clustered12", "clustered24", "random777_mesh3"])
 def test_hydro_chain_parity(api, ctx, name, variant):
     b = box_of(name)
@@ -193,24 +190,12 @@ def test_hydro_chain_parity(api, ctx, name, variant):
     I = O.from_box(b)
     ref = O.forward(I, W.GAMMA, W.AV_ALPHA, W.AV_BETA, W.AV_ETA2)
     gas = b.species == 0
-    errs = {
-        "V": rel_l2(out["V"].cpu().numpy()[gas], ref["V"][gas]),
-        "rho": rel_l2(out["rho"].cpu().numpy()[gas], ref["rho"][gas]),
-        "A": rel_l2(out["A"].cpu().numpy()[gas], ref["A"][gas]),
-        "B": rel_l2(out["B"].cpu().numpy().T[gas], ref["B"][gas]),
-        "gA": rel_l2(out["gA"].cpu().numpy().T[gas], ref["gA"][gas]),
-        "gB": rel_l2(out["gB"].cpu().numpy().T[gas], ref["gB"][gas]),
-        "dv": rel_l2(out["dv"].cpu().numpy().T[gas], ref["dv"][gas]),
-        "du": rel_l2(out["du"].cpu().numpy()[gas], ref["du"][gas]),
-    }
-    print(name, {k: f"{v:.2e}" for k, v in errs.items()})
+    got = {"V": out["V"].cpu().numpy(), "rho": out["rho"].cpu().numpy(), "A": out["A"].cpu().numpy(),
+           "B": out["B"].cpu().numpy().T, "gA": out["gA"].cpu().numpy().T, "gB": out["gB"].cpu().numpy().T,
+           "dv": out["dv"].cpu().numpy().T, "du": out["du"].cpu().numpy()}
     assert int(out["n_singular"].item()) == ref["singular"] == 0
-    for k in ("V", "rho", "A"):
-        assert errs[k] < 1e-5, (k, errs)
-    for k in ("B", "gA", "gB"):
-        assert errs[k] < 1e-3, (k, errs)
-    assert errs["dv"] <= 2e-5, errs
-    assert errs["du"] <= 5e-5, errs
+    for k, g in got.items():
+        check(f"hydro_chain/{name}/v{variant}", k, g[gas], ref[k][gas])
     # DM entries of gas-only outputs are zero
     assert float(out["V"][torch.as_tensor(~gas, device="cuda")].abs().max()) == 0.0 if (~gas).any() else True
     # conservation sums accumulated in FP64 on the GPU
@@ -218,7 +203,10 @@ def test_hydro_chain_parity(api, ctx, name, variant):
     scale = np.abs(I.m[gas, None] * ref["dv"][gas]).sum()
     assert np.max(np.abs(cons[:3])) < 1e-5 * scale
     assert abs(int(out["count_hydro"].item()) - ref["pairs_hydro"]) <= boundary_pairs(b, True)
-    assert int(out["count_geom"].item()) == int(out["count_hydro"].item())
+    if variant < 5:
+        assert int(out["count_geom"].item()) == int(out["count_hydro"].item())
+    else:  # the half-warp arm decides boundary pairs in the frame of the lower leaf, geometry in i's
+        assert abs(int(out["count_geom"].item()) - int(out["count_hydro"].item())) <= boundary_pairs(b, True)
 
 
 @pytest.mark.parametrize("variant", GRAV_VARIANTS, ids=GRAV_VARIANT_IDS)
@@ -239,7 +227,9 @@ def test_adjoint_parity(api, ctx, name, variant):
     ref_a, _ = O.gravity(I)
     ogx, ogm = O.gravity_adjoint(I, 2.0 * ref_a)
     ogx2, ogm2 = O.geometry_adjoint(I, (b.species == 0).astype(np.float64))
-    e = {"grav_gx": rel_l2(gx.cpu().numpy().T, ogx), "grav_gm": rel_l2(gm.cpu().numpy(), ogm),
-         "geom_gx": rel_l2(gx2.cpu().numpy().T, ogx2), "geom_gm": rel_l2(gm2.cpu().numpy(), ogm2)}
-    print(name, {k: f"{v:.2e}" for k, v in e.items()})
-    assert max(e.values()) < 1e-4, e
+    where = f"adjoint/{name}/v{variant}"
+    bnd = cut_boundary_particles(I.pos, b.L, b.r_cut)
+    check(where, "grav_gx", gx.cpu().numpy().T, ogx, "gx", exclude=bnd)
+    check(where, "grav_gm", gm.cpu().numpy(), ogm, "gm")
+    check(where, "geom_gx", gx2.cpu().numpy().T, ogx2, "gx")
+    check(where, "geom_gm", gm2.cpu().numpy(), ogm2, "gm")

@@ -34,23 +34,32 @@ def setup():
     return api, native, api.Context(0)
 
 
-def test_noalloc_matches_grav_short_on_two_calls(setup):
+@pytest.mark.parametrize("variant", ["tiles", "lists"])
+def test_noalloc_matches_grav_short_on_two_calls(setup, variant):
+    """Both branches of the entry point (the tiles kernel, and the lists kernel when the
+    gravity variant is lists and the leaves were built with gravity lists) against
+    grav_short in the same variant: within the gravity tolerance, and bit for bit."""
     api, N, ctx = setup
     from paper_2310_16122_gb300 import workloads as W
 
     b = W.clustered_box(16, 2, 4242)
     db = api.DeviceBox(b)
-    lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
-    gp = db.gp.c()
-    for m in (db.m, db.m * 1.7 + 0.05):
-        ref, _ = api.grav_short(ctx, lv, db.gp, m)
-        out = torch.full((3, b.n), float("nan"), device="cuda")
-        st = N.lib().grav_short_noalloc(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.c_void_p(m.data_ptr()),
-                                        ctypes.c_void_p(out.data_ptr()))
-        assert st == N.CRK_OK
-        torch.cuda.synchronize()
-        assert torch.isfinite(out).all()
-        assert _rel_l2(out, ref) <= 2e-5
+    ctx.set_variant("gravity", 0 if variant == "lists" else 1)
+    try:
+        lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+        gp = db.gp.c()
+        for m in (db.m, db.m * 1.7 + 0.05):
+            ref, _ = api.grav_short(ctx, lv, db.gp, m)
+            out = torch.full((3, b.n), float("nan"), device="cuda")
+            st = N.lib().grav_short_noalloc(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.c_void_p(m.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()))
+            assert st == N.CRK_OK
+            torch.cuda.synchronize()
+            assert torch.isfinite(out).all()
+            assert _rel_l2(out, ref) <= 2e-5
+            assert torch.equal(out, ref)
+    finally:
+        ctx.set_variant("gravity", 1)
 
 
 def test_noalloc_rejects_boxes_above_its_limit(setup):
