@@ -39,7 +39,7 @@ MUFU_PER_PAIR = {"geometry": 2, "corrections": 2, "hydro": 3, "gravity": 1, "gra
                  "geometry_adjoint": 2}
 STAGES = ["leaves", "geometry", "corrections", "hydro", "gravity", "gravity_adjoint", "geometry_adjoint"]
 # DRAM bytes (read + write) per launch of a kernel in one launch shape (workload, kernel, variant,
-# depth), from one ncu capture of the current build (dram__bytes_read.sum + dram__bytes_write.sum;
+# depth, warps), from one ncu capture of the current build (dram__bytes_read.sum + dram__bytes_write.sum;
 # the summaries under profiles/ give the commands).  A shape not captured since its kernel last
 # changed has no entry, and the bench line then reports traffic null.
 TRAFFIC = {}
@@ -337,7 +337,7 @@ def main():
         tuning = api.autotune(ctx, lv_t, db, io_t, reps=2)
         del lv_t, io_t
         variants = {k: ctx.get_variant(k) for k in native.KERNELS}
-    launch = {k: dict(zip(("persistent", "depth"), ctx.get_launch(k))) for k in native.KERNELS}
+    launch = {k: dict(zip(("persistent", "depth", "warps"), ctx.get_launch(k))) for k in native.KERNELS}
     # counting step (untimed): pair counts of every kernel
     lv_c = step(count=True)
     n_leaves = lv_c.n_leaves
@@ -448,7 +448,8 @@ def main():
     kern = {s: v for s, v in per_stage.items() if s in FLOPS_PER_PAIR}
     dom = max(kern, key=kern.get)
     achieved = FLOPS_PER_PAIR[dom] * pairs[dom] / (kern[dom] * 1e-3) / 1e12
-    traffic = TRAFFIC.get((args.workload, dom, variants.get(dom), launch.get(dom, {}).get("depth")))
+    traffic = TRAFFIC.get((args.workload, dom, variants.get(dom), launch.get(dom, {}).get("depth"),
+                           launch.get(dom, {}).get("warps")))
     f_med = float(peaks.get("clocks_under_load", {}).get("sm_mhz_median", f_max))
     f_run = float(clk.get("sm_mhz") or f_max)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -702,7 +703,21 @@ def batched_vs_plain(args, local, dist, peak_tflops):
     t_gen = time.perf_counter()
     boxes = W.batched(args.batched_boxes)
     t_gen = time.perf_counter() - t_gen
-    ctx = api.Context(local)
+    # a stream of its own: graph capture needs one other than the legacy default stream
+    side = torch.cuda.Stream(device=f"cuda:{local}")
+    with torch.cuda.stream(side):
+        return _batched_vs_plain(args, local, peak_tflops, boxes, t_gen, side)
+
+
+def _batched_vs_plain(args, local, peak_tflops, boxes, t_gen, side):
+    import ctypes as _ct
+
+    import numpy as np
+    import torch
+
+    from paper_2310_16122_gb300 import api, native
+
+    ctx = api.Context(local, stream=side)
     dbs = [api.DeviceBox(b, device=f"cuda:{local}") for b in boxes]
     ios = [api.StepIO(ctx, db) for db in dbs]
     dbt = api.DeviceBatch(boxes, device=f"cuda:{local}")
@@ -713,7 +728,7 @@ def batched_vs_plain(args, local, dist, peak_tflops):
         lv_t = api.build_leaves_batch(ctx, dbt)
         tuned = api.tune(ctx, lv_t, dbt, api.StepIO(ctx, dbt, extras=True), reps=2)
         lv_t.free()
-    shapes = {k: {"variant": ctx.get_variant(k), **dict(zip(("persistent", "depth"), ctx.get_launch(k)))}
+    shapes = {k: {"variant": ctx.get_variant(k), **dict(zip(("persistent", "depth", "warps"), ctx.get_launch(k)))}
               for k in native.KERNELS}
 
     def plain_step(count=False):
@@ -759,14 +774,14 @@ def batched_vs_plain(args, local, dist, peak_tflops):
     res["batched_graph"] = timed(g.launch)
     status = lv_g.status()
     g.close()
-    keep = {k: (ctx.get_variant(k), ctx.get_launch(k)) for k in native.KERNELS}
+    keep = {k: ctx.get_launch(k) for k in native.KERNELS}
     ctx.set_persistent(True)
     g = api.RebuildStepGraph(ctx, lv_g, dbt, io_g)
     res["batched_graph_persistent"] = timed(g.launch)
     status |= lv_g.status()
     g.close()
-    for k, (v, (pm, d)) in keep.items():
-        ctx.set_launch(k, pm, d)
+    for k, (pm, d, w) in keep.items():
+        ctx.set_launch(k, pm, d, w)
     # per-kernel times of the batched step in the tuned shapes (eager, profiled), and the rebuild
     reps = max(args.steps, 1)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]

@@ -134,7 +134,8 @@ int crk_set_trace(crk_ctx *ctx, int on);
 #define CRK_VARIANT_HALFWARP_SMEM 6
 #define CRK_VARIANT_HALFWARP_LOAD 7
 /* gravity kernels: the candidates of each 32-particle group compacted once, then swept once per
- * 8-particle sub-cell (only those within the cut of its box) by 4 lanes per particle */
+ * 8-particle sub-cell (only those within the cut of its box) by 4 lanes per particle; the leaf
+ * build makes the sub-cells RCB cells of 8 when a gravity kernel is set to it at build time */
 #define CRK_VARIANT_SPLIT8 8
 #define CRK_N_VARIANTS 9
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
@@ -144,13 +145,15 @@ int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
  * block ever waits on another).  Same results. */
 int crk_set_persistent(crk_ctx *ctx, int on);
 /* Launch shape of one pair kernel (CRK_K_*), as the autotuner sets it:
- * persistent as above, and the j-tile depth of the packed tiles sweeps of the
- * gravity kernels (candidates compacted before each sweep: 32, 64 or 96; the
- * other kernels and variants sweep at 32 and ignore it).  The results agree
- * up to the order of FP32 additions.  CRK_EINVAL for an unknown kernel or a
- * depth other than 32, 64, 96. */
-int crk_set_launch(crk_ctx *ctx, int kernel, int persistent, int depth);
-int crk_get_launch(const crk_ctx *ctx, int kernel, int *persistent, int *depth);
+ * persistent as above; the j-tile depth of the packed tiles sweeps of the
+ * gravity kernels (candidates compacted before each sweep: 32, 64 or 96); and
+ * their warps per i-leaf block (4: one warp per 32-particle group of a
+ * 128-leaf; 2: blocks of two warps, each taking two groups).  The other
+ * kernels and variants sweep at depth 32 with 4 warps and ignore both.  The
+ * results agree up to the order of FP32 additions.  CRK_EINVAL for an unknown
+ * kernel, a depth other than 32, 64, 96 or warps other than 2, 4. */
+int crk_set_launch(crk_ctx *ctx, int kernel, int persistent, int depth, int warps);
+int crk_get_launch(const crk_ctx *ctx, int kernel, int *persistent, int *depth, int *warps);
 int crk_get_variant(const crk_ctx *ctx, int kernel, int *variant);
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int crk_launch_count(const crk_ctx *ctx, int64_t *out);
@@ -517,22 +520,23 @@ int crk_graph_launch(crk_graph *g);
 void crk_graph_destroy(crk_graph *g);
 
 /* Autotuner (Sec. 5.2 tunes register use and sub-group size per kernel and
- * device; here the dimensions are the sweep variant, the launch mode and the
- * j-tile depth).  For every kernel CRK_K_* it times each variant on these
+ * device; here the dimensions are the sweep variant, the launch mode, the
+ * j-tile depth and the warps per leaf).  For every kernel CRK_K_* it times each variant on these
  * leaves (best of reps after a warm-up, CUDA events on the context stream;
  * a candidate whose warm-up takes more than three times the best time so far
  * is not timed further and reports its warm-up time) and keeps the fastest,
  * then times the fastest variant non-persistent and
- * persistent, then (gravity kernels on tiles) at depths 32, 64 and 96, and
- * keeps the fastest shape in the context.  ms_out[CRK_N_KERNELS * CRK_TUNE_COLS]
- * (kernel-major: CRK_N_VARIANTS variant timings, 2 launch-mode timings, 3
- * depth timings; -1 = not timed) and best_out[3 * CRK_N_KERNELS] (variant,
- * persistent, depth per kernel) are host arrays and may be NULL.  Runs one
+ * persistent, then (gravity kernels on tiles) at depths 32, 64 and 96 and with
+ * 2 and 4 warps per leaf, and keeps the fastest shape in the context.
+ * ms_out[CRK_N_KERNELS * CRK_TUNE_COLS] (kernel-major: CRK_N_VARIANTS variant
+ * timings, 2 launch-mode timings, 3 depth timings, 2 warps timings; -1 = not
+ * timed) and best_out[4 * CRK_N_KERNELS] (variant, persistent, depth, warps
+ * per kernel) are host arrays and may be NULL.  Runs one
  * crk_step first; every output array of io must be given (they are
  * overwritten while timing).  Extras is timed when io->extras is set, the
  * Acceleration and Energy passes always (with io->dvdx as the limiter's
  * velocity gradient when io->extras is set). */
-#define CRK_TUNE_COLS (CRK_N_VARIANTS + 5)
+#define CRK_TUNE_COLS (CRK_N_VARIANTS + 7)
 int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, const crk_hydro_params *hp,
              const crk_step_io *io, int reps, float *ms_out, int *best_out);
 

@@ -58,13 +58,16 @@ class Context:
     def set_persistent(self, on: bool) -> None:
         self.check(N.lib().crk_set_persistent(self.handle, int(bool(on))))
 
-    def set_launch(self, kernel: str, persistent: bool, depth: int = 32) -> None:
-        self.check(N.lib().crk_set_launch(self.handle, N.KERNELS[kernel], int(bool(persistent)), int(depth)))
+    def set_launch(self, kernel: str, persistent: bool, depth: int = 32, warps: int = 4) -> None:
+        self.check(N.lib().crk_set_launch(self.handle, N.KERNELS[kernel], int(bool(persistent)), int(depth),
+                                          int(warps)))
 
     def get_launch(self, kernel: str) -> tuple:
-        p, d = ctypes.c_int(0), ctypes.c_int(0)
-        self.check(N.lib().crk_get_launch(self.handle, N.KERNELS[kernel], ctypes.byref(p), ctypes.byref(d)))
-        return bool(p.value), int(d.value)
+        """(persistent, depth, warps per leaf) of one pair kernel."""
+        p, d, w = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self.check(N.lib().crk_get_launch(self.handle, N.KERNELS[kernel], ctypes.byref(p), ctypes.byref(d),
+                                          ctypes.byref(w)))
+        return bool(p.value), int(d.value), int(w.value)
 
     def get_variant(self, kernel: str) -> int:
         v = ctypes.c_int(0)
@@ -568,20 +571,22 @@ class RebuildStepGraph(StepGraph):
 
 def tune(ctx: Context, lv: Leaves, db: "DeviceBox", io: StepIO, reps: int = 3) -> dict:
     """Autotune every pair kernel on these leaves (crk_tune): the sweep variant, then the launch
-    mode, then (gravity tiles) the j-tile depth.  Returns {kernel: {"variant", "persistent",
-    "depth", "ms": {"variant": [ms per variant], "launch": [off, on], "depth": [32, 64, 96]}}}
-    (-1 = not timed; extras only when io has the Extras outputs)."""
+    mode, then (gravity tiles) the j-tile depth and the warps per leaf.  Returns {kernel:
+    {"variant", "persistent", "depth", "warps", "ms": {"variant": [ms per variant], "launch":
+    [off, on], "depth": [32, 64, 96], "warps": [4, 2]}}} (-1 = not timed; extras only when io
+    has the Extras outputs)."""
     gp, hp, c = db.gp.c(), db.hp.c(), io.c(False)
     ms = (ctypes.c_float * (N.N_KERNELS * N.TUNE_COLS))()
-    best = (ctypes.c_int * (3 * N.N_KERNELS))()
+    best = (ctypes.c_int * (4 * N.N_KERNELS))()
     ctx.check(N.lib().crk_tune(ctx.handle, lv.handle, ctypes.byref(gp), ctypes.byref(hp), ctypes.byref(c),
                                int(reps), ms, best))
     out = {}
     for k, i in N.KERNELS.items():
         row = [round(float(ms[N.TUNE_COLS * i + q]), 4) for q in range(N.TUNE_COLS)]
-        out[k] = {"variant": int(best[3 * i]), "persistent": bool(best[3 * i + 1]), "depth": int(best[3 * i + 2]),
+        out[k] = {"variant": int(best[4 * i]), "persistent": bool(best[4 * i + 1]), "depth": int(best[4 * i + 2]),
+                  "warps": int(best[4 * i + 3]),
                   "ms": {"variant": row[:N.N_VARIANTS], "launch": row[N.N_VARIANTS:N.N_VARIANTS + 2],
-                         "depth": row[N.N_VARIANTS + 2:]}}
+                         "depth": row[N.N_VARIANTS + 2:N.N_VARIANTS + 5], "warps": row[N.N_VARIANTS + 5:]}}
     return out
 
 
@@ -602,15 +607,15 @@ def autotune(ctx: Context, lv: Leaves, db, io: StepIO, cache_path: str | None = 
             cache = json.load(open(cache_path))
         except (OSError, ValueError):
             cache = {}
-    if key in cache and "launch" in cache[key]:
+    if key in cache and "launch" in cache[key] and all(len(v) == 3 for v in cache[key]["launch"].values()):
         for k, v in cache[key]["variants"].items():
             ctx.set_variant(k, int(v))
-        for k, (pm, d) in cache[key]["launch"].items():
-            ctx.set_launch(k, bool(pm), int(d))
+        for k, (pm, d, w) in cache[key]["launch"].items():
+            ctx.set_launch(k, bool(pm), int(d), int(w))
         return dict(cache[key], cached=True)
     res = tune(ctx, lv, db, io, reps)
     entry = {"variants": {k: r["variant"] for k, r in res.items()},
-             "launch": {k: [int(r["persistent"]), r["depth"]] for k, r in res.items()},
+             "launch": {k: [int(r["persistent"]), r["depth"], r["warps"]] for k, r in res.items()},
              "ms": {k: r["ms"] for k, r in res.items()}}
     if cache_path:
         cache[key] = entry

@@ -146,19 +146,22 @@ int crk_set_persistent(crk_ctx *ctx, int on) {
     return CRK_OK;
 }
 
-int crk_set_launch(crk_ctx *ctx, int kernel, int persistent, int depth) {
+int crk_set_launch(crk_ctx *ctx, int kernel, int persistent, int depth, int warps) {
     if (!ctx) return CRK_EINVAL;
     if (kernel < 0 || kernel >= CRK_N_KERNELS) return crk_fail(ctx, CRK_EINVAL, "unknown kernel %d", kernel);
     if (depth != 32 && depth != 64 && depth != 96) return crk_fail(ctx, CRK_EINVAL, "depth must be 32, 64 or 96");
+    if (warps != 2 && warps != 4) return crk_fail(ctx, CRK_EINVAL, "warps per leaf must be 2 or 4");
     ctx->persist[kernel] = persistent != 0;
     ctx->depth[kernel] = depth;
+    ctx->warps[kernel] = warps;
     return CRK_OK;
 }
 
-int crk_get_launch(const crk_ctx *ctx, int kernel, int *persistent, int *depth) {
+int crk_get_launch(const crk_ctx *ctx, int kernel, int *persistent, int *depth, int *warps) {
     if (!ctx || kernel < 0 || kernel >= CRK_N_KERNELS) return CRK_EINVAL;
     if (persistent) *persistent = ctx->persist[kernel];
     if (depth) *depth = ctx->depth[kernel];
+    if (warps) *warps = ctx->warps[kernel];
     return CRK_OK;
 }
 

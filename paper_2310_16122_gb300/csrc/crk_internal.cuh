@@ -62,6 +62,7 @@ struct crk_ctx {
     // atomic work queue, and the j-tile depth of the gravity tiles sweeps
     int persist[CRK_N_KERNELS] = {};
     int depth[CRK_N_KERNELS] = {32, 32, 32, 32, 32, 32, 32, 32, 32};
+    int warps[CRK_N_KERNELS] = {4, 4, 4, 4, 4, 4, 4, 4, 4};  // warps per i-leaf of the packed gravity tiles
     // crk_step profiling: 8 events per step (start, after each of the 6 stages, end)
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
@@ -124,6 +125,7 @@ struct crk_leaves {
     std::vector<std::pair<void *, size_t>> allocs;
     // what a capture-safe rebuild (crk_leaves_rebuild) reuses
     int max_leaf = 0, cells = 0;
+    bool cells8 = false;  // gravity order bisected down to RCB cells of 8 (split gravity sweeps)
     std::vector<int64_t> box_start;
     std::vector<float> box_side;
     float *node_box = nullptr, *node_hmax = nullptr;  // RCB traversal tree: node boxes and h_max

@@ -550,7 +550,7 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
                                  int32_t *__restrict__ perm, int32_t *__restrict__ kperm,
                                  int32_t *__restrict__ leaf_ngas, float *__restrict__ bbox,
                                  float *__restrict__ hmax, float4 *__restrict__ pos, int32_t *__restrict__ kperm_g,
-                                 float4 *__restrict__ pos_g, int32_t *__restrict__ err) {
+                                 float4 *__restrict__ pos_g, int32_t *__restrict__ err, int cells8) {
     __shared__ uint64_t key[kCap], zkey[kCap];
     __shared__ Bisect32<kCap> bs;
     __shared__ float4 pm[kCap];  // member position and h (0 for dark matter), gathered once
@@ -650,11 +650,13 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
         pos[lo + q] = make_float4(c.x - ox, c.y - oy, c.z - oz, c.w);
     }
     __syncthreads();
-    // gravity order: the whole leaf bisected into groups of 32, and (leaves of at most 256) each
-    // group of 32 into groups of 8 (the sub-cells of the split gravity sweeps)
+    // gravity order: the whole leaf bisected into groups of 32, and (cells8, leaves of at most 256)
+    // each group of 32 into groups of 8 (the sub-cells of the split gravity sweeps)
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) bs.a[t] = (int16_t)t;
     int16_t *src = bisect32(bs, cnt, pm, key);
-    if constexpr (kCap <= 256) src = bisect32<kCap, 8>(bs, cnt, pm, key, src, 32);
+    if constexpr (kCap <= 256) {
+        if (cells8) src = bisect32<kCap, 8>(bs, cnt, pm, key, src, 32);
+    }
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int t = src[q];
         const float4 c = pm[t];
@@ -1268,6 +1270,9 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
     lv->cells = lp->cells_per_side;
     lv->box_start = box_start;
     lv->box_side = box_side;
+    if (!re)  // the split gravity sweeps want RCB cells of 8 in the gravity order (kept by rebuilds)
+        lv->cells8 = ctx->variant[CRK_K_GRAVITY] == CRK_VARIANT_SPLIT8 ||
+                     ctx->variant[CRK_K_GRAVITY_ADJOINT] == CRK_VARIANT_SPLIT8;
     cudaStream_t st = ctx->stream;
     int rc = CRK_OK;
 #define TRY(expr)                          \
@@ -1485,11 +1490,11 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                 leaf_data_kernel<128><<<(unsigned)nl, 32, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
                                                                    p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
                                                                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g,
-                                                                   lv->pos_g, flags + 4);
+                                                                   lv->pos_g, flags + 4, lv->cells8 ? 1 : 0);
             else
                 leaf_data_kernel<kMaxLeafCap><<<(unsigned)nl, 128, 0, st>>>(
                     nl, lv->leaf_start, members, p->x, p->y, p->z, p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
-                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g, flags + 4);
+                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g, flags + 4, 0);
             ++ctx->launches;
         }
         if (n > 0) {

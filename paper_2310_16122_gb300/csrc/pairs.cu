@@ -2072,13 +2072,15 @@ __device__ __forceinline__ void cons_block_partial(double (*cons_sh)[4], const d
 }
 
 // Tiles, one block per i-leaf (or leaves from the persistent queue); the
-// block's warps take the leaf's groups in turn.
-template <class S, bool kCount>
-__global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S::P p,
-                                                        const typename S::Rec *__restrict__ rec,
-                                                        double *__restrict__ cons_part) {
+// block's kW warps take the leaf's groups in turn (kW = 2: the packed gravity
+// sweeps' narrow launch shape, two groups of a 128-leaf per warp).
+template <class S, bool kCount, int kW = kWarps>
+__global__ void __launch_bounds__(32 * kW) pair_kernel(LeafView lv, typename S::P p,
+                                                       const typename S::Rec *__restrict__ rec,
+                                                       double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
-    __shared__ __align__(16) Rec buf[kWarps][S::kPair ? kCapPair : kCap];
+    static_assert(kW == kWarps || !S::kCons, "conservation partials assume kWarps warps per block");
+    __shared__ __align__(16) Rec buf[kW][S::kPair ? kCapPair : kCap];
     __shared__ double cons_sh[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cons_acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -2086,7 +2088,7 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(LeafView lv, typename S:
     for (int64_t a = next_leaf(lv, -1, &leaf_slot); a < lv.n_leaves; a = next_leaf(lv, a, &leaf_slot)) {
         const int lo = lv.leaf_start[a];
         const int hi = S::kGasOnly ? lo + lv.leaf_ngas[a] : lv.leaf_start[a + 1];
-        for (int g0 = lo + warp * 32; g0 < hi; g0 += kWarps * 32)
+        for (int g0 = lo + warp * 32; g0 < hi; g0 += kW * 32)
             tile_group_any<S, kCount>(lv, p, rec, buf[warp], a, lo, g0, hi, lane, cons_acc);
     }
     if constexpr (S::kCons) {
@@ -2949,6 +2951,14 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
                 pair_kernel_sub<S, 8, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
             else
                 pair_kernel_sub<S, 8, false><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
+        } else if (S::kPair && ctx->warps[kernel_id] == 2) {
+            if constexpr (S::kPair) {  // two warps per i-leaf (persistent: twice the blocks per SM)
+                const unsigned g2 = (unsigned)(persistent ? std::min<int64_t>(lv->n_leaves, 2 * grid) : grid);
+                if (p.count)
+                    pair_kernel<S, true, 2><<<g2, 64, 0, ctx->stream>>>(v, p, rec, part);
+                else
+                    pair_kernel<S, false, 2><<<g2, 64, 0, ctx->stream>>>(v, p, rec, part);
+            }
         } else if (p.count) {
             pair_kernel<S, true><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(v, p, rec, part);
         } else {

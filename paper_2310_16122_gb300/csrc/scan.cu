@@ -87,99 +87,109 @@ __global__ void scan_tile_kernel(const int32_t *__restrict__ in, int32_t *__rest
 }
 
 // ---------------------------------------------------------------- radix sort
+// LSD radix sort with 8-bit digits: a histogram pass per tile, one exclusive
+// scan of the digit-major counts, and a scatter pass that ranks each tile
+// stably by digit and writes every digit's run to consecutive positions.
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadix = 16;  // 4-bit digits
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRadix = 256;  // 8-bit digits
+static_assert(kRadix == kSortThreads, "one digit per thread in the scatter's digit scan");
 
-__global__ void radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift, int32_t *__restrict__ counts,
-                                  int64_t nb) {
-    __shared__ int32_t h[kRadix];
-    if (threadIdx.x < kRadix) h[threadIdx.x] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
-    for (int k = 0; k < kSortItems; ++k) {
-        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x < kRadix) counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+__device__ __forceinline__ unsigned lanemask_below() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
 }
 
-// One LSD pass over a tile: stable tile-local ranks by digit (per-thread
-// counts in digit-major, thread-minor order, scanned), the tile sorted by
-// digit in shared memory, then written out in order so that each digit's run
-// goes to consecutive global positions (coalesced stores).
-__global__ void radix_scatter_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
-                                     uint32_t *__restrict__ kout, int32_t *__restrict__ vout, int64_t n, int shift,
-                                     const int32_t *__restrict__ offsets, int64_t nb) {
-    static_assert(kRadix * kSortThreads <= 2 * kSortTile, "counters fit the staging buffer");
-    __shared__ int32_t sm[2 * kSortTile];  // first the counters, then the digit-sorted tile (keys, values)
-    int32_t *cnt = sm;                     // digit-major, thread-minor
-    __shared__ int32_t wt[32];
-    __shared__ int32_t goff[kRadix];
+// per tile: the count of each digit (lanes with equal digits add once per warp step)
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n,
+                                                                  int shift, int32_t *__restrict__ counts, int64_t nb) {
+    __shared__ int32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
+        const int d = i < n ? (int)((keys[i] >> shift) & (kRadix - 1)) : kRadix;
+        const unsigned peers = __match_any_sync(CRK_FULL_MASK, d);
+        if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// One LSD pass over a tile.  Warp w takes the tile's items w*512 .. w*512 + 511
+// in 16 coalesced steps of 32; the lanes of a step with equal digits are found
+// by __match_any_sync, so each item's rank among the earlier items of its warp
+// with the same digit is a running per-warp count plus its rank among its
+// peers.  The per-warp counts then give each warp's offset inside the digit,
+// a scan over the 256 digits gives each digit's start in the tile, the tile is
+// sorted in shared memory, and every digit's run is written to consecutive
+// global positions (coalesced stores).  Stable: the tile order is item order.
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint32_t *__restrict__ kin,
+                                                                     const int32_t *__restrict__ vin,
+                                                                     uint32_t *__restrict__ kout,
+                                                                     int32_t *__restrict__ vout, int64_t n, int shift,
+                                                                     const int32_t *__restrict__ offsets, int64_t nb) {
+    __shared__ int32_t whist[kSortWarps][kRadix];  // per-warp digit counts, then the warp's offset in the digit
     __shared__ int32_t dstart[kRadix];
-    const int t = threadIdx.x;
-    if (t < kRadix) goff[t] = offsets[(int64_t)t * nb + blockIdx.x];
+    __shared__ int32_t goff[kRadix];
+    __shared__ uint32_t skey[kSortTile];
+    __shared__ int32_t sval[kSortTile];
+    __shared__ int32_t wt[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    goff[t] = offsets[(int64_t)t * nb + blockIdx.x];
+#pragma unroll
+    for (int v = 0; v < kSortWarps; ++v) whist[v][t] = 0;
+    __syncthreads();
     const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
-    const int64_t base = tile0 + (int64_t)t * kSortItems;  // blocked: thread-contiguous
+    const unsigned below = lanemask_below();
     uint32_t key[kSortItems];
     int32_t val[kSortItems];
-    int dig[kSortItems];
+    int dig[kSortItems], rank[kSortItems];
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        int64_t i = base + k;
-        bool ok = i < n;
-        key[k] = ok ? kin[i] : 0u;
-        val[k] = ok ? vin[i] : 0;
-        dig[k] = ok ? (int)((key[k] >> shift) & (kRadix - 1)) : -1;
-    }
-#pragma unroll
-    for (int d = 0; d < kRadix; ++d) {
-        int c = 0;
-#pragma unroll
-        for (int k = 0; k < kSortItems; ++k) c += dig[k] == d;
-        cnt[d * kSortThreads + t] = c;
-    }
-    __syncthreads();
-    // exclusive scan of the kRadix*kSortThreads counters (each thread owns 16 consecutive ones)
-    int32_t loc[kSortItems];
-    int32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        loc[k] = cnt[t * kSortItems + k];
-        s += loc[k];
-    }
-    int32_t tot;
-    int32_t e = block_exclusive_scan(s, wt, tot);
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        cnt[t * kSortItems + k] = e;
-        e += loc[k];
-    }
-    __syncthreads();
-    // cnt now holds prefixes in digit-major order (they include the counts of all smaller
-    // digits in this tile); dstart[d] is the tile-local start of digit d
-    if (t < kRadix) dstart[t] = cnt[t * kSortThreads];
-    __syncthreads();     // dstart read before thread 0 advances its counters
-    int rr[kSortItems];  // tile-local sorted position of each item
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const int d = dig[k];
-        rr[k] = -1;
-        if (d < 0) continue;
-        rr[k] = cnt[d * kSortThreads + t];
-        cnt[d * kSortThreads + t] = rr[k] + 1;  // only this thread touches its own counter
-    }
-    __syncthreads();  // counters read: the buffer now takes the sorted tile
-    uint32_t *skey = reinterpret_cast<uint32_t *>(sm);
-    int32_t *sval = sm + kSortTile;
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k)
-        if (rr[k] >= 0) {
-            skey[rr[k]] = key[k];
-            sval[rr[k]] = val[k];
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = tile0 + (int64_t)w * (32 * kSortItems) + 32 * r + lane;
+        const bool ok = i < n;
+        key[r] = ok ? kin[i] : 0u;
+        val[r] = ok ? vin[i] : 0;
+        const int d = ok ? (int)((key[r] >> shift) & (kRadix - 1)) : kRadix;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(CRK_FULL_MASK, d);
+        const int leader = __ffs(peers) - 1;
+        int before = 0;
+        if (lane == leader && d < kRadix) {
+            before = whist[w][d];
+            whist[w][d] = before + __popc(peers);
         }
+        before = __shfl_sync(CRK_FULL_MASK, before, leader);
+        rank[r] = before + __popc(peers & below);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread t = digit t: the warps' offsets inside the digit, then the digits' starts in the tile
+    int32_t tot = 0;
+#pragma unroll
+    for (int v = 0; v < kSortWarps; ++v) {
+        const int32_t c = whist[v][t];
+        whist[v][t] = tot;
+        tot += c;
+    }
+    int32_t all;
+    dstart[t] = block_exclusive_scan(tot, wt, all);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int d = dig[r];
+        if (d < kRadix) {
+            const int pos = dstart[d] + whist[w][d] + rank[r];
+            skey[pos] = key[r];
+            sval[pos] = val[r];
+        }
+    }
     __syncthreads();
     const int m = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
     for (int i = t; i < m; i += kSortThreads) {
@@ -213,7 +223,7 @@ int crk_radix_sort_u32(crk_ctx *ctx, uint32_t *keys, int32_t *vals, int64_t n, i
     if (n <= 1) return CRK_OK;
     if (n > 2147483647LL) return crk_fail(ctx, CRK_EINVAL, "radix sort: n too large");
     int64_t nb = (n + kSortTile - 1) / kSortTile;
-    int passes = (key_bits + 3) / 4;
+    int passes = (key_bits + 7) / 8;
     uint32_t *k2 = (uint32_t *)crk_scratch(ctx, 13, sizeof(uint32_t) * (size_t)n);
     int32_t *v2 = (int32_t *)crk_scratch(ctx, 14, sizeof(int32_t) * (size_t)n);
     int32_t *counts = (int32_t *)crk_scratch(ctx, 12, sizeof(int32_t) * (size_t)(nb * kRadix));
@@ -221,7 +231,7 @@ int crk_radix_sort_u32(crk_ctx *ctx, uint32_t *keys, int32_t *vals, int64_t n, i
     uint32_t *ka = keys, *kb = k2;
     int32_t *va = vals, *vb = v2;
     for (int p = 0; p < passes; ++p) {
-        int shift = 4 * p;
+        int shift = 8 * p;
         radix_hist_kernel<<<(unsigned)nb, kSortThreads, 0, ctx->stream>>>(ka, n, shift, counts, nb);
         CRK_LAUNCH_CHECK(ctx, "radix hist");
         int rc = crk_exclusive_scan_i32(ctx, counts, counts, nb * kRadix, nullptr);

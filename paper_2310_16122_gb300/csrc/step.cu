@@ -187,11 +187,12 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
         return crk_fail(ctx, CRK_EINVAL, "crk_tune needs every output array of the step");
     if (io->extras && (!io->rho_r || !io->dvdx)) return crk_fail(ctx, CRK_EINVAL, "extras needs rho_r and dvdx");
     const int nvar = CRK_N_VARIANTS, cols = CRK_TUNE_COLS;
-    int keep_v[CRK_N_KERNELS], keep_p[CRK_N_KERNELS], keep_d[CRK_N_KERNELS];
+    int keep_v[CRK_N_KERNELS], keep_p[CRK_N_KERNELS], keep_d[CRK_N_KERNELS], keep_w[CRK_N_KERNELS];
     for (int k = 0; k < CRK_N_KERNELS; ++k) {
         keep_v[k] = ctx->variant[k];
         keep_p[k] = ctx->persist[k];
         keep_d[k] = ctx->depth[k];
+        keep_w[k] = ctx->warps[k];
     }
     if (ms_out)
         for (int q = 0; q < CRK_N_KERNELS * cols; ++q) ms_out[q] = -1.0f;
@@ -246,9 +247,11 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
         return tmin;
     };
     for (int k = 0; k < CRK_N_KERNELS && rc == CRK_OK; ++k) {
-        int bv = keep_v[k], bp = keep_p[k], bd = keep_d[k];
+        int bv = keep_v[k], bp = keep_p[k], bd = keep_d[k], bw = keep_w[k];
         if (k == CRK_K_EXTRAS && !io->extras) {
-            if (best_out) { best_out[3 * k] = bv; best_out[3 * k + 1] = bp; best_out[3 * k + 2] = bd; }
+            if (best_out) {
+                best_out[4 * k] = bv; best_out[4 * k + 1] = bp; best_out[4 * k + 2] = bd; best_out[4 * k + 3] = bw;
+            }
             continue;
         }
         const bool gas = k != CRK_K_GRAVITY && k != CRK_K_GRAVITY_ADJOINT;
@@ -258,6 +261,7 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
         float best = 1e30f;
         ctx->persist[k] = 0;
         ctx->depth[k] = 32;
+        ctx->warps[k] = 4;
         for (int v = 0; v < nvar && rc == CRK_OK; ++v) {
             if (!tune_variant_available(k, v, have_lists)) continue;
             ctx->variant[k] = v;
@@ -293,7 +297,23 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
             if (rc) break;
         }
         ctx->depth[k] = bd;
-        if (best_out) { best_out[3 * k] = bv; best_out[3 * k + 1] = bp; best_out[3 * k + 2] = bd; }
+        // 4. the warps per leaf of the packed gravity tiles
+        bw = 4;
+        if ((k == CRK_K_GRAVITY || k == CRK_K_GRAVITY_ADJOINT) && bv == CRK_VARIANT_TILES) {
+            best = 1e30f;
+            for (int q = 0; q < 2 && rc == CRK_OK; ++q) {
+                ctx->warps[k] = q ? 2 : 4;
+                const float t = timed(k, best);
+                if (rc) break;
+                if (row) row[nvar + 5 + q] = t;
+                if (t < best) { best = t; bw = q ? 2 : 4; }
+            }
+            if (rc) break;
+        }
+        ctx->warps[k] = bw;
+        if (best_out) {
+            best_out[4 * k] = bv; best_out[4 * k + 1] = bp; best_out[4 * k + 2] = bd; best_out[4 * k + 3] = bw;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -302,6 +322,7 @@ int crk_tune(crk_ctx *ctx, const crk_leaves *lv, const crk_grav_params *gp, cons
             ctx->variant[k] = keep_v[k];
             ctx->persist[k] = keep_p[k];
             ctx->depth[k] = keep_d[k];
+            ctx->warps[k] = keep_w[k];
         }
         return rc;
     }

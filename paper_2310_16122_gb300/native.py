@@ -37,7 +37,7 @@ VARIANT_HALFWARP_SMEM = 6
 VARIANT_HALFWARP_LOAD = 7
 VARIANT_SPLIT8 = 8
 N_VARIANTS = 9
-TUNE_COLS = N_VARIANTS + 5  # per kernel: variant timings, launch mode off/on, depth 32/64/96
+TUNE_COLS = N_VARIANTS + 7  # per kernel: variant timings, launch mode off/on, depth 32/64/96, warps 4/2
 STATUS_NAMES = {0: "CRK_OK", -1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_EBOX",
                 -5: "CRK_ESTATE", -6: "CRK_ETIMEOUT", -7: "CRK_ETOOLARGE"}
 
@@ -106,8 +106,8 @@ SIGNATURES = {
     "crk_set_trace": [_P, _I],
     "crk_set_variant": [_P, _I, _I],
     "crk_set_persistent": [_P, _I],
-    "crk_set_launch": [_P, _I, _I, _I],
-    "crk_get_launch": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "crk_set_launch": [_P, _I, _I, _I, _I],
+    "crk_get_launch": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "crk_get_variant": [_P, _I, ctypes.POINTER(_I)],
     "crk_build_leaves": [_P, ctypes.POINTER(crk_particles), _P, ctypes.POINTER(crk_leaf_params), ctypes.POINTER(_P)],
     "crk_build_leaves_batch": [_P, ctypes.POINTER(crk_batch), _P, ctypes.POINTER(crk_leaf_params),

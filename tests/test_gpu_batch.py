@@ -137,16 +137,17 @@ def test_autotuner(setup):
     res = api.tune(ctx, lv, dbt, io, reps=2)
     assert set(res) == set(api.N.KERNELS)  # all nine pair kernels, Extras and both hydro passes included
     for k, r in res.items():
-        mv, ml, md = r["ms"]["variant"], r["ms"]["launch"], r["ms"]["depth"]
+        mv, ml, md, mw = r["ms"]["variant"], r["ms"]["launch"], r["ms"]["depth"], r["ms"]["warps"]
         best = r["variant"]
         # the variant is the fastest one timed, then the launch mode of that variant, then the depth
         assert mv[best] > 0 and mv[best] == min(t for t in mv if t > 0), k
         assert min(ml) > 0 and ml[int(r["persistent"])] == min(ml), k
-        assert ctx.get_variant(k) == best and ctx.get_launch(k) == (r["persistent"], r["depth"]), k
+        assert ctx.get_variant(k) == best and ctx.get_launch(k) == (r["persistent"], r["depth"], r["warps"]), k
         if k.startswith("gravity") and best == 1:
             assert min(md) > 0 and md[r["depth"] // 32 - 1] == min(md), k
+            assert min(mw) > 0 and mw[0 if r["warps"] == 4 else 1] == min(mw), k
         else:
-            assert r["depth"] == 32 and max(md) < 0, k
+            assert r["depth"] == 32 and max(md) < 0 and r["warps"] == 4 and max(mw) < 0, k
     # half-warp arms are timed for the gravity kernels and the hydro passes, not for the others
     for k in ("gravity", "gravity_adjoint", "hydro", "accel", "energy"):
         assert min(res[k]["ms"]["variant"][5:8]) > 0, k

@@ -166,6 +166,33 @@ def test_gravity_parity(api, ctx, name, variant):
     assert abs(int(cnt.item()) - npairs) <= boundary_pairs(b, False)
 
 
+@pytest.mark.parametrize("shape", [(False, 64, 2), (True, 96, 2), (True, 32, 4)], ids=["d64w2", "pers_d96w2", "pers_d32w4"])
+@pytest.mark.parametrize("name", ["clustered24", "random1000_leaf7"])
+def test_gravity_launch_shapes(api, ctx, name, shape):
+    """The packed gravity tiles and their adjoint in other launch shapes (persistent, j-tile depth,
+    warps per leaf) against the oracle."""
+    b = box_of(name)
+    db = api.DeviceBox(b)
+    for k in ("gravity", "gravity_adjoint"):
+        ctx.set_launch(k, *shape)
+    try:
+        lv = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
+        a, cnt = api.grav_short(ctx, lv, db.gp, db.m, count=True)
+        gx, gm = api.grav_short_adjoint(ctx, lv, db.gp, db.m, 2.0 * a)
+        torch.cuda.synchronize()
+    finally:
+        for k in ("gravity", "gravity_adjoint"):
+            ctx.set_launch(k, False, 32, 4)
+    I = O.from_box(b)
+    ref, npairs = O.gravity(I)
+    where = f"gravity_shape/{name}/{shape}"
+    check(where, "acc", a.cpu().numpy().T, ref)
+    assert abs(int(cnt.item()) - npairs) <= boundary_pairs(b, False)
+    ogx, ogm = O.gravity_adjoint(I, 2.0 * ref)
+    check(where, "grav_gx", gx.cpu().numpy().T, ogx, "gx", exclude=cut_boundary_particles(I.pos, b.L, b.r_cut))
+    check(where, "grav_gm", gm.cpu().numpy(), ogm, "gm")
+
+
 GAS_KERNELS = ("geometry", "corrections", "hydro", "geometry_adjoint", "gravity", "gravity_adjoint")
 
 
