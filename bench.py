@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 # algorithmic FP32 operations per in-range pair (FMA = 2, add/mul = 1; MUFU counted apart),
 # counted from the operations of each kernel's pair term (e.g. gravity: d 3, r^2 5, +eps^2 1,
 # r^-3 2, Horner P5 10, g 1, m g 1, three FMAs 6)
-FLOPS_PER_PAIR = {"geometry": 24, "corrections": 135, "hydro": 160, "gravity": 29, "gravity_adjoint": 68,
+FLOPS_PER_PAIR = {"geometry": 24, "corrections": 88, "hydro": 160, "gravity": 29, "gravity_adjoint": 68,
                   "geometry_adjoint": 31}
 MUFU_PER_PAIR = {"geometry": 2, "corrections": 2, "hydro": 3, "gravity": 1, "gravity_adjoint": 1,
                  "geometry_adjoint": 2}

@@ -32,6 +32,7 @@ struct crk_rcb_shape {
     int64_t n_leaves = 0, n_nodes = 0;
     int max_leaf_size = 0;
     std::vector<size_t> level_off, level_size;  // segment tables, 7 int32 columns per level
+    std::vector<int32_t> level_max;             // largest segment of each level
     int32_t *dtab = nullptr;                    // device: lo, hi, k, child, node, axis, leftbase per segment
     int32_t *leaf_start = nullptr;              // device [n_leaves + 1]
     int32_t *left = nullptr, *right = nullptr;  // device [n_nodes], -1 for leaves

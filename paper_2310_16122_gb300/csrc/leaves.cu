@@ -28,44 +28,67 @@ __device__ __forceinline__ uint32_t coord_key(float x) {
 }
 
 // Positions in [0, L_box), gas h > 0 and finite; largest gas h per box.
-// Counts and maxima are combined per warp first, so the global atomics are
-// one per warp and box (millions of same-address atomics would serialise).
-__global__ void validate_kernel(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
-                                const uint8_t *__restrict__ sp, const float *__restrict__ h, int64_t n,
-                                const int32_t *__restrict__ box_of, const float *__restrict__ box_L,
-                                int32_t *__restrict__ flags /* [0] bad pos, [1] bad h, [2] n_gas */,
-                                unsigned *__restrict__ hmax_bits /* per box */) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in = i < n;
-    const int b = in && box_of ? box_of[i] : 0;
-    bool bad = false, gas = false, badh = false;
-    unsigned hb = 0u;
-    if (in) {
+// Each block takes kValItems rows of 256 consecutive particles and combines
+// its counts (and, when its range lies in one box, its h maximum) in shared
+// memory, so the global atomics are a few per block: same-address atomics
+// from every warp of a 33M-particle launch serialise at L2 (about 1.7 ms).
+constexpr int kValItems = 16;
+constexpr int kValTile = 256 * kValItems;
+
+__global__ void __launch_bounds__(256) validate_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                                       const float *__restrict__ z, const uint8_t *__restrict__ sp,
+                                                       const float *__restrict__ h, int64_t n,
+                                                       const int32_t *__restrict__ box_of,
+                                                       const float *__restrict__ box_L,
+                                                       int32_t *__restrict__ flags /* [0] bad pos, [1] bad h, [2] n_gas */,
+                                                       unsigned *__restrict__ hmax_bits /* per box */) {
+    __shared__ unsigned part[4][8];
+    const int64_t base = (int64_t)blockIdx.x * kValTile;
+    const int64_t last = (base + kValTile < n ? base + kValTile : n) - 1;
+    const int bfirst = box_of ? box_of[base] : 0;
+    const bool one_box = !box_of || box_of[last] == bfirst;  // boxes are contiguous ranges
+    unsigned nbad = 0, nbadh = 0, ngas = 0, hb_blk = 0;
+    for (int k = 0; k < kValItems; ++k) {
+        const int64_t i = base + (int64_t)k * 256 + threadIdx.x;
+        if (i >= n) break;
+        const int b = box_of ? box_of[i] : 0;
         const float L = box_L[b];
-        float c[3] = {x[i], y[i], z[i]};
+        const float c[3] = {x[i], y[i], z[i]};
+        bool bad = false;
         for (int a = 0; a < 3; ++a) bad |= !(c[a] >= 0.0f && c[a] < L);
-        gas = sp[i] == 0;
-        if (gas) {
+        nbad += bad;
+        if (sp[i] == 0) {
+            ++ngas;
             const float hi = h[i];
-            badh = !(hi > 0.0f) || !isfinite(hi);
-            if (!badh) hb = __float_as_uint(hi);  // positive floats order like their bits
+            if (!(hi > 0.0f) || !isfinite(hi)) {
+                ++nbadh;
+            } else {
+                const unsigned hb = __float_as_uint(hi);  // positive floats order like their bits
+                if (one_box) hb_blk = hb > hb_blk ? hb : hb_blk;
+                else atomicMax(&hmax_bits[b], hb);
+            }
         }
     }
-    const int lane = threadIdx.x & 31;
-    const unsigned nbad = __reduce_add_sync(CRK_FULL_MASK, (unsigned)bad);
-    const unsigned nbadh = __reduce_add_sync(CRK_FULL_MASK, (unsigned)badh);
-    const unsigned ngas = __reduce_add_sync(CRK_FULL_MASK, (unsigned)gas);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    nbad = __reduce_add_sync(CRK_FULL_MASK, nbad);
+    nbadh = __reduce_add_sync(CRK_FULL_MASK, nbadh);
+    ngas = __reduce_add_sync(CRK_FULL_MASK, ngas);
+    hb_blk = __reduce_max_sync(CRK_FULL_MASK, hb_blk);
     if (lane == 0) {
-        if (nbad) atomicAdd(&flags[0], (int)nbad);
-        if (nbadh) atomicAdd(&flags[1], (int)nbadh);
-        if (ngas) atomicAdd(&flags[2], (int)ngas);
+        part[0][w] = nbad;
+        part[1][w] = nbadh;
+        part[2][w] = ngas;
+        part[3][w] = hb_blk;
     }
-    const int b0 = __shfl_sync(CRK_FULL_MASK, b, 0);
-    if (__all_sync(CRK_FULL_MASK, b == b0)) {
-        const unsigned m = __reduce_max_sync(CRK_FULL_MASK, hb);
-        if (lane == 0 && m) atomicMax(&hmax_bits[b0], m);
-    } else if (hb) {
-        atomicMax(&hmax_bits[b], hb);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int v = 1; v < 8; ++v) {
+            for (int q = 0; q < 3; ++q) part[q][0] += part[q][v];
+            part[3][0] = part[3][v] > part[3][0] ? part[3][v] : part[3][0];
+        }
+        for (int q = 0; q < 3; ++q)
+            if (part[q][0]) atomicAdd(&flags[q], (int)part[q][0]);
+        if (part[3][0]) atomicMax(&hmax_bits[bfirst], part[3][0]);
     }
 }
 
@@ -382,6 +405,206 @@ __global__ void __launch_bounds__(kPartThreads, 4) rcb_scatter3_kernel(int64_t n
             O.A[b][1][np] = r1;
         }
     }
+}
+
+// --- RCB bottom levels in shared memory --------------------------------------
+// Once every segment of a level holds at most kLocalCap entries, one block
+// takes one segment and runs all the remaining levels on it in shared memory:
+// the same boxes, axes, rank thresholds and stable partitions as the level
+// kernels above (so the same tree, bit for bit), but a level costs a few
+// shared-memory passes instead of three DRAM passes over the six rank
+// columns.  The block ends by writing the final member order of its range.
+constexpr int kLocalCap = 2048;
+constexpr int kLocalThreads = 512;
+constexpr int kLocalBlocks = 2;                         // resident blocks per SM (shared memory: ~113 KB each)
+constexpr int kLocalItems = kLocalCap / kLocalThreads;  // consecutive positions per thread
+constexpr int kLocalLevels = 7;                         // levels one block may run
+constexpr int kLocalSegs = 1 << kLocalLevels;           // segments per block at its deepest level
+constexpr size_t kLocalSmem = sizeof(int32_t) * 2 * 6 * kLocalCap + sizeof(int16_t) * 2 * kLocalCap;
+static_assert(kLocalItems == 4, "positions are moved as int4");
+
+// the level tables a block walks: tab[l] = 7 columns of m[l] segments (lo, hi, k, child, node, axis, leftbase)
+struct LocalShape {
+    int32_t *tab[kLocalLevels];
+    int32_t m[kLocalLevels];
+    int nlev;
+};
+
+struct __align__(16) LocalSeg {
+    int32_t lo, hi, k, child;  // lo, hi relative to the block's range; child relative to the next level's first
+    int32_t axis, thr, lb, pad;  // lb: left entries of the block's earlier segments (every list alike)
+};
+
+// three 21-bit counters in one word (at most kLocalCap per counter)
+__device__ __forceinline__ uint64_t pack3(unsigned f) {
+    return (uint64_t)(f & 1u) | ((uint64_t)((f >> 1) & 1u) << 21) | ((uint64_t)((f >> 2) & 1u) << 42);
+}
+__device__ __forceinline__ int field3(uint64_t v, int b) { return (int)((v >> (21 * b)) & 0x1fffffu); }
+
+__global__ void __launch_bounds__(kLocalThreads, kLocalBlocks) rcb_local_kernel(int64_t n, LocalShape sh, RankLists L, AxisOrder o,
+                                                                       const float *__restrict__ x,
+                                                                       const float *__restrict__ y,
+                                                                       const float *__restrict__ z,
+                                                                       float *__restrict__ node_box,
+                                                                       int32_t *__restrict__ members,
+                                                                       int32_t *__restrict__ err) {
+    extern __shared__ int4 local_smem[];
+    int32_t *cur = reinterpret_cast<int32_t *>(local_smem);  // [6][kLocalCap]: column 2b + c of list b
+    int32_t *nxt = cur + 6 * kLocalCap;
+    int16_t *sc = reinterpret_cast<int16_t *>(nxt + 6 * kLocalCap);  // segment of each position
+    int16_t *sn = sc + kLocalCap;
+    __shared__ LocalSeg seg[kLocalSegs];
+    __shared__ uint64_t wsum[kLocalThreads / 32];
+    __shared__ int bad;
+    const int s0 = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int m0 = sh.m[0];
+    const int lo = sh.tab[0][s0], cnt = sh.tab[0][m0 + s0] - lo;
+    if (t == 0) bad = 0;
+    if (cnt > kLocalCap) {
+        if (t == 0) atomicAdd(err, 1);
+        return;
+    }
+    for (int q = t; q < cnt; q += kLocalThreads) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            cur[(2 * b) * kLocalCap + q] = L.A[b][0][lo + q];
+            cur[(2 * b + 1) * kLocalCap + q] = L.A[b][1][lo + q];
+        }
+        sc[q] = 0;
+    }
+    const float *cs[3] = {x, y, z};
+    // a rank used as an index; a partition found inconsistent (reported through err) may leave
+    // positions unwritten, whose values then never index out of the arrays
+    auto rk = [n](int32_t r) -> int64_t { return (uint64_t)r < (uint64_t)n ? r : 0; };
+    int f = s0, e = s0 + 1;  // this block's segments at the current level
+    for (int lev = 0; lev < sh.nlev; ++lev) {
+        int32_t *tab = sh.tab[lev];
+        const int m = sh.m[lev];
+        const int ns = e - f;
+        __syncthreads();  // the previous level is done with seg[], cur and sc
+        if (ns > kLocalSegs) {  // excluded by the host's choice of levels
+            if (t == 0) atomicAdd(err, 1);
+            return;
+        }
+        for (int u = t; u < ns; u += kLocalThreads) {
+            const int s = f + u;
+            LocalSeg r{tab[s] - lo, tab[m + s] - lo, tab[2 * m + s], 0, 0, 0, tab[6 * m + s] - tab[6 * m + f], 0};
+            const int k = r.k;
+            if (k > 0) {
+                // tight box from the ends of the three list segments (entry p of list a: rank
+                // along axis (a + 1) % 3 in column 0)
+                float blo[3], bhi[3];
+                double ext[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int32_t *S = o.S[(a + 1) % 3];
+                    blo[a] = cs[a][S[rk(cur[(2 * a) * kLocalCap + r.lo])]];
+                    bhi[a] = cs[a][S[rk(cur[(2 * a) * kLocalCap + r.hi - 1])]];
+                    ext[a] = __dsub_rn((double)bhi[a], (double)blo[a]);
+                }
+                int axis = 0;
+                if (ext[1] > ext[axis]) axis = 1;
+                if (ext[2] > ext[axis]) axis = 2;
+                r.axis = axis;
+                r.thr = o.R[axis][o.S[(axis + 1) % 3][rk(cur[(2 * axis) * kLocalCap + r.lo + k])]];
+                tab[5 * m + s] = axis;
+                float *nb = node_box + 6 * (int64_t)tab[4 * m + s];
+                for (int a = 0; a < 3; ++a) {
+                    nb[a] = blo[a];
+                    nb[3 + a] = bhi[a];
+                }
+            }
+            seg[u] = r;
+        }
+        // the next level's range of this block's segments
+        const int fn = tab[3 * m + f];
+        const int en = tab[3 * m + e - 1] + (tab[2 * m + e - 1] > 0 ? 2 : 1);
+        for (int u = t; u < ns; u += kLocalThreads) seg[u].child = tab[3 * m + f + u] - fn;
+        __syncthreads();
+        // left flags of this thread's kLocalItems consecutive positions (bit b: list b)
+        const int q0 = t * kLocalItems;
+        unsigned fl[kLocalItems];
+        int sg[kLocalItems];
+        uint64_t mine = 0;
+#pragma unroll
+        for (int i = 0; i < kLocalItems; ++i) {
+            const int q = q0 + i;
+            fl[i] = 0u;
+            sg[i] = 0;
+            if (q < cnt) {
+                sg[i] = sc[q];
+                const LocalSeg &r = seg[sg[i]];
+                if (r.k > 0) {
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        bool left;
+                        if (b == r.axis) {
+                            left = q - r.lo < r.k;
+                        } else {
+                            const int c = (r.axis - b + 2) % 3;  // column of list b holding ranks along the axis
+                            left = cur[(2 * b + c) * kLocalCap + q] < r.thr;
+                        }
+                        fl[i] |= (unsigned)left << b;
+                    }
+                }
+                mine += pack3(fl[i]);
+            }
+        }
+        // block exclusive scan of the three counters
+        uint64_t incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t v = __shfl_up_sync(CRK_FULL_MASK, incl, d);
+            if (lane >= d) incl += v;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            constexpr int kW = kLocalThreads / 32;
+            uint64_t v = lane < kW ? wsum[lane] : 0, iv = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t u = __shfl_up_sync(CRK_FULL_MASK, iv, d);
+                if (lane >= d) iv += u;
+            }
+            if (lane < kW) wsum[lane] = iv - v;
+        }
+        __syncthreads();
+        uint64_t run = wsum[w] + incl - mine;
+        // stable partition into nxt; the segment of each new position
+#pragma unroll
+        for (int i = 0; i < kLocalItems; ++i) {
+            const int q = q0 + i;
+            if (q >= cnt) break;
+            const LocalSeg &r = seg[sg[i]];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                int np = q;
+                if (r.k > 0) {
+                    const int lb = field3(run, b) - r.lb;  // left entries before q in its segment
+                    np = (fl[i] >> b) & 1u ? r.lo + lb : r.lo + r.k + (q - r.lo - lb);
+                    if (!(np >= r.lo && np < r.hi)) {
+                        bad = 1;  // inconsistent partition: reported, never written out of the segment
+                        continue;
+                    }
+                }
+                nxt[(2 * b) * kLocalCap + np] = cur[(2 * b) * kLocalCap + q];
+                nxt[(2 * b + 1) * kLocalCap + np] = cur[(2 * b + 1) * kLocalCap + q];
+            }
+            sn[q] = (int16_t)(r.child + ((r.k > 0 && q - r.lo >= r.k) ? 1 : 0));
+            run += pack3(fl[i]);
+        }
+        int32_t *tp = cur;
+        cur = nxt;
+        nxt = tp;
+        int16_t *ts = sc;
+        sc = sn;
+        sn = ts;
+        f = fn;
+        e = en;
+    }
+    __syncthreads();
+    if (t == 0 && bad) atomicAdd(err, 1);
+    for (int q = t; q < cnt; q += kLocalThreads) members[lo + q] = o.S[1][rk(cur[q])];  // list 0, column 0
 }
 
 // --- per-leaf data ------------------------------------------------------------
@@ -1114,6 +1337,9 @@ static int rcb_shape(crk_ctx *ctx, const std::vector<int64_t> &box_start, int ml
     for (auto &L : levels) {
         r->level_off.push_back(tot);
         r->level_size.push_back(L.size());
+        int32_t mx = 0;
+        for (auto &sg : L) mx = std::max(mx, sg.hi - sg.lo);
+        r->level_max.push_back(mx);
         tot += 7 * L.size();
     }
     std::vector<int32_t> packed(tot > 0 ? tot : 1);
@@ -1346,8 +1572,8 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
             ++ctx->launches;
         }
         if (n > 0) {
-            validate_kernel<<<crk_grid(n, 256), 256, 0, st>>>(p->x, p->y, p->z, p->species, h, n, box_of, box_L, flags,
-                                                              hbits);
+            validate_kernel<<<(unsigned)((n + kValTile - 1) / kValTile), 256, 0, st>>>(
+                p->x, p->y, p->z, p->species, h, n, box_of, box_L, flags, hbits);
             ++ctx->launches;
         }
         int32_t *members = nullptr;  // particle ids grouped by leaf
@@ -1448,7 +1674,17 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                     goto fail;
                 }
             }
-            for (size_t d = 0; d < shape->level_size.size(); ++d) {
+            // levels [0, d_local) stream through DRAM; the rest run in shared memory, one block per
+            // segment of level d_local (every segment there holds at most kLocalCap entries)
+            const int n_lev = (int)shape->level_size.size();
+            int d_local = n_lev;
+            for (int d = 0; d < n_lev; ++d)
+                if (shape->level_max[d] <= kLocalCap) {
+                    d_local = d;
+                    break;
+                }
+            if (n_lev - d_local > kLocalLevels) d_local = n_lev - kLocalLevels;
+            for (int d = 0; d < d_local; ++d) {
                 int m = (int)shape->level_size[d];
                 int32_t *tab = shape->dtab + shape->level_off[d];
                 LevelDev dv{tab, tab + m, tab + 2 * m, tab + 3 * m, tab + 4 * m, tab + 5 * m, tab + 6 * m};
@@ -1466,9 +1702,25 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                 std::swap(node_of, node_nx);
                 KCHECK("rcb level");
             }
-            if (n > 0) {
-                rank_members_kernel<<<crk_grid(n, 256), 256, 0, st>>>(
-                    n, RankLists{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}}, ord, mem);
+            const RankLists Lfin{{{Ac[0][0], Ac[0][1]}, {Ac[1][0], Ac[1][1]}, {Ac[2][0], Ac[2][1]}}};
+            if (n > 0 && d_local < n_lev) {
+                static bool smem_set = false;  // opt-in above 48 KB, once (never inside a capture: a
+                if (!smem_set) {               // rebuild always follows a fresh build)
+                    cudaFuncSetAttribute(rcb_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSmem);
+                    smem_set = true;
+                }
+                LocalShape ls{};
+                ls.nlev = n_lev - d_local;
+                for (int l = 0; l < ls.nlev; ++l) {
+                    ls.tab[l] = shape->dtab + shape->level_off[d_local + l];
+                    ls.m[l] = (int32_t)shape->level_size[d_local + l];
+                }
+                rcb_local_kernel<<<(unsigned)shape->level_size[d_local], kLocalThreads, kLocalSmem, st>>>(
+                    n, ls, Lfin, ord, p->x, p->y, p->z, node_box, mem, flags + 5);
+                ++ctx->launches;
+                KCHECK("rcb local levels");
+            } else if (n > 0) {
+                rank_members_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, Lfin, ord, mem);
                 ++ctx->launches;
             }
             tr.mark("rcb levels");

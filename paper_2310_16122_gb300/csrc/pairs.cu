@@ -540,11 +540,37 @@ struct CorrStage {
         float m0, c0;
         float m1[3], c1[3];
         float m2[6], c2[6];  // xx xy xz yy yz zz
+        // Gradient moments.  With w = V_j W and d_g(V_j W) = V_j dWr x_g, the g-derivatives of
+        // m1_a and m2_ab are delta_ag m0 + V_j dWr x_a x_g and delta_ag m1_b + delta_bg m1_a +
+        // V_j dWr x_a x_b x_g: only the symmetric dWr sums s2 (second order) and s3 (third
+        // order) are accumulated, the delta terms come from m0 and m1 in finish.
         float dm0[3];
-        float dm1[9];   // [g][a]
-        float dm2[18];  // [g][ab]
+        float s2[6];   // xx xy xz yy yz zz
+        float s3[10];  // xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
         int cnt;
     };
+    // packed index of (a <= b) among xx xy xz yy yz zz
+    __host__ __device__ static constexpr int idx2(int a, int b) { return a * (5 - a) / 2 + b; }
+    // packed index of (a <= b <= c) among xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+    __host__ __device__ static constexpr int idx3(int a, int b, int c) {
+        return a == 0 ? (b == 0 ? c : (b == 1 ? 2 + c : 5)) : (a == 1 ? (b == 1 ? 5 + c : 8) : 9);
+    }
+    // the full gradient moments dm1[g][a] and dm2[g][ab] (ab packed) from m0, m1, s2, s3
+    __device__ static void grad_moments(const I &s, double m0, const double m1[3], double dm1[3][3],
+                                        double dm2[3][6]) {
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+        for (int g = 0; g < 3; ++g) {
+            for (int a = 0; a < 3; ++a)
+                dm1[g][a] = (a == g ? m0 : 0.0) + (double)s.s2[a < g ? idx2(a, g) : idx2(g, a)];
+            for (int q = 0; q < 6; ++q) {
+                int t0 = ia[q], t1 = ib[q], t2 = g;  // sort (a, b, g); a <= b already
+                if (t2 < t1) { t2 = t1; t1 = g; }
+                if (t1 < t0) { int u = t0; t0 = t1; t1 = u; }
+                dm2[g][q] = (ia[q] == g ? m1[ib[q]] : 0.0) + (ib[q] == g ? m1[ia[q]] : 0.0) +
+                            (double)s.s3[idx3(t0, t1, t2)];
+            }
+        }
+    }
     __device__ static Rec gather(const P &p, int32_t o, float4 ps) { return {ps.x, ps.y, ps.z, ps.w, p.V[o], 0, 0, 0}; }
     __device__ static float box_cut(const P &, float hmax_i, const Rec &rj) { return hmax_i + rj.h; }
     __device__ static float leaf_cut(const P &, float hmax_i, float hmax_j) { return hmax_i + hmax_j; }
@@ -556,9 +582,9 @@ struct CorrStage {
 #pragma unroll
         for (int a = 0; a < 6; ++a) s.m2[a] = s.c2[a] = 0.f;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) s.dm1[a] = 0.f;
+        for (int a = 0; a < 6; ++a) s.s2[a] = 0.f;
 #pragma unroll
-        for (int a = 0; a < 18; ++a) s.dm2[a] = 0.f;
+        for (int a = 0; a < 10; ++a) s.s3[a] = 0.f;
         s.cnt = 0;
     }
     template <bool kCount>
@@ -582,18 +608,14 @@ struct CorrStage {
         for (int q = 0; q < 6; ++q) {
             xx[q] = x[ia[q]] * x[ib[q]];
             kahan_add(s.m2[q], s.c2[q], wx[ia[q]] * x[ib[q]]);
+            s.s2[q] = fmaf(xx[q], vd, s.s2[q]);
         }
 #pragma unroll
-        for (int g = 0; g < 3; ++g) {
-            s.dm0[g] += dW[g];
+        for (int g = 0; g < 3; ++g) s.dm0[g] += dW[g];
+        // s3[abc] += x_a x_b (V_j dWr x_c) for a <= b <= c
+        const int k3q[10] = {0, 0, 0, 1, 1, 2, 3, 3, 4, 5}, k3c[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
 #pragma unroll
-            for (int a = 0; a < 3; ++a) s.dm1[3 * g + a] = fmaf(x[a], dW[g], s.dm1[3 * g + a] + (a == g ? w : 0.0f));
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                float t = (ia[q] == g ? wx[ib[q]] : 0.0f) + (ib[q] == g ? wx[ia[q]] : 0.0f);
-                s.dm2[6 * g + q] = fmaf(xx[q], dW[g], s.dm2[6 * g + q] + t);
-            }
-        }
+        for (int k = 0; k < 10; ++k) s.s3[k] = fmaf(xx[k3q[k]], dW[k3c[k]], s.s3[k]);
         if (kCount) s.cnt += in;
     }
     __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
@@ -635,18 +657,20 @@ struct CorrStage {
         double A = 1.0 / (m0 + B[0] * m1[0] + B[1] * m1[1] + B[2] * m1[2]);
         p.A[o] = (float)A;
         for (int a = 0; a < 3; ++a) p.B[a * n + o] = (float)B[a];
+        double dm1[3][3], dm2[3][6];
+        grad_moments(s, m0, m1, dm1, dm2);
         for (int g = 0; g < 3; ++g) {
             double dM[3][3];
             for (int q = 0; q < 6; ++q) {
-                dM[ia[q]][ib[q]] = s.dm2[6 * g + q];
-                dM[ib[q]][ia[q]] = s.dm2[6 * g + q];
+                dM[ia[q]][ib[q]] = dm2[g][q];
+                dM[ib[q]][ia[q]] = dm2[g][q];
             }
             double t[3], BdMB = 0.0, Bdm1 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double dMB = dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2];
-                t[a] = (double)s.dm1[3 * g + a] + dMB;
+                t[a] = dm1[g][a] + dMB;
                 BdMB += B[a] * dMB;
-                Bdm1 += B[a] * (double)s.dm1[3 * g + a];
+                Bdm1 += B[a] * dm1[g][a];
             }
             p.gA[g * n + o] = (float)(-A * A * ((double)s.dm0[g] + 2.0 * Bdm1 + BdMB));
             for (int a = 0; a < 3; ++a)
@@ -719,15 +743,17 @@ struct CorrAdjPrepStage : CorrStage {
         double Ab = (double)p.Abar[o];
         // moment cotangents: dm1b[g][a], dm2b[g][ab] (symmetric in ab, packed as ia/ib)
         double m0b = 0.0, m1b[3] = {0, 0, 0}, dm0b[3], dm1b[3][3], dm2b[3][6];
+        double dm1[3][3], dm2[3][6];
+        grad_moments(s, m0, m1, dm1, dm2);
         for (int g = 0; g < 3; ++g) {
             double dM[3][3], t[3], tb[3], K = (double)s.dm0[g];
             for (int q = 0; q < 6; ++q) {
-                dM[ia[q]][ib[q]] = s.dm2[6 * g + q];
-                dM[ib[q]][ia[q]] = s.dm2[6 * g + q];
+                dM[ia[q]][ib[q]] = dm2[g][q];
+                dM[ib[q]][ia[q]] = dm2[g][q];
             }
             for (int a = 0; a < 3; ++a) {
-                t[a] = (double)s.dm1[3 * g + a] + dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2];
-                K += 2.0 * B[a] * (double)s.dm1[3 * g + a] + B[a] * (dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2]);
+                t[a] = dm1[g][a] + dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2];
+                K += 2.0 * B[a] * dm1[g][a] + B[a] * (dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2]);
             }
             double gb[3];
             for (int a = 0; a < 3; ++a) gb[a] = (double)p.gBbar[(3 * g + a) * n + o];
@@ -741,7 +767,7 @@ struct CorrAdjPrepStage : CorrStage {
             for (int a = 0; a < 3; ++a) {
                 dm1b[g][a] = tb[a] + 2.0 * B[a] * Kb;
                 Bb[a] += tb[0] * dM[0][a] + tb[1] * dM[1][a] + tb[2] * dM[2][a];  // dM symmetric
-                Bb[a] += 2.0 * (double)s.dm1[3 * g + a] * Kb + 2.0 * (dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2]) * Kb;
+                Bb[a] += 2.0 * dm1[g][a] * Kb + 2.0 * (dM[a][0] * B[0] + dM[a][1] * B[1] + dM[a][2] * B[2]) * Kb;
             }
             // dm2b[g][a][b] = tb_a B_b + B_a B_b Kb, summed over (a, b) and (b, a) for a packed
             // off-diagonal entry (the moment sums are symmetric in ab)
@@ -2603,8 +2629,21 @@ struct GasLists {
 // bytes; the hydro record is too large to stage, its lanes gather directly)
 template <class S>
 __host__ __device__ constexpr int table_cap() {
-    return sizeof(typename S::Rec) <= 32 ? 320 : (sizeof(typename S::Rec) <= 48 ? 224 : 0);
+    // corrections: 256, so that five blocks of 128 threads fit an SM (with list_min_blocks below)
+    return std::is_same<S, CorrStage>::value ? 256
+                                             : (sizeof(typename S::Rec) <= 32 ? 320 : (sizeof(typename S::Rec) <= 48 ? 224 : 0));
 }
+
+// resident blocks per SM that list_kernel<S> is compiled for (register cap): corrections at
+// five (96 registers, a few spilled outside the pair loop) is latency-bound at four
+template <class S>
+struct list_min_blocks {
+    static constexpr int value = 0;  // no register cap
+};
+template <>
+struct list_min_blocks<CorrStage> {
+    static constexpr int value = 5;
+};
 
 // index rows in flight in list_kernel<S>: 8 for the short pair terms (records of at most 32
 // bytes and few registers), 4 for the long ones
@@ -2619,7 +2658,7 @@ __host__ __device__ constexpr int list_ahead() {
 // indices.  Table entries beyond the staged capacity are gathered from global
 // memory through the leaf's image table.
 template <class S, bool kCount>
-__global__ void __launch_bounds__(kThreads) list_kernel(LeafView lv, typename S::P p,
+__global__ void __launch_bounds__(kThreads, list_min_blocks<S>::value) list_kernel(LeafView lv, typename S::P p,
                                                         const typename S::Rec *__restrict__ rec, GasLists gl,
                                                         double *__restrict__ cons_part) {
     using Rec = typename S::Rec;
@@ -2760,6 +2799,21 @@ size_t list_kernel_smem() {
     return bytes;
 }
 
+// resident blocks per SM of list_kernel<S> (registers and shared memory; once per kernel)
+template <class S, bool kCount>
+int list_kernel_resident() {
+    static int nb = 0;
+    if (!nb) {
+        const size_t smem = list_kernel_smem<S, kCount>();
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, list_kernel<S, kCount>, kThreads, smem) != cudaSuccess) {
+            cudaGetLastError();
+            nb = 4;
+        }
+        if (nb < 1) nb = 1;
+    }
+    return nb;
+}
+
 // fixed-capacity list and table offsets: goff[g] = g capr, uoff[g] = g capt
 __global__ void strided_offsets_kernel(int64_t m, int capr, int capt, int32_t *__restrict__ goff,
                                        int32_t *__restrict__ uoff) {
@@ -2827,8 +2881,11 @@ int run_stage(crk_ctx *ctx, const crk_leaves *lv, typename S::P p, bool gas_pair
     if (grid > 2147483647LL) grid = 2147483647LL;
     const bool persistent = ctx->persist[kernel_id] != 0;
     if (persistent) {
-        // persistent grid: resident blocks on every SM (4 blocks of 128 threads per SM is the design point)
-        int64_t g = (int64_t)ctx->num_sms * 4;
+        // persistent grid: resident blocks on every SM (lists: as many as fit; tiles: 4 blocks of
+        // 128 threads per SM, the design point)
+        int per_sm = 4;
+        if (lists) per_sm = p.count ? list_kernel_resident<S, true>() : list_kernel_resident<S, false>();
+        const int64_t g = (int64_t)ctx->num_sms * per_sm;
         if (g < grid) grid = g;
     }
     const bool halfwarp = !lists && ctx->variant[kernel_id] >= CRK_VARIANT_HALFWARP_SHFL &&
