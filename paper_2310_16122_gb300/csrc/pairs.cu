@@ -706,6 +706,64 @@ struct CorrAdjP : CorrP {
 struct CorrAdjPrepStage : CorrStage {
     static constexpr bool kAllVariants = false;
     using P = CorrAdjP;
+    // The preparation sweep accumulates the gradient moments in full (30 sums, not the forward's
+    // symmetric s2/s3): with its FP64 finish the symmetric form measured slower here.
+    struct I {
+        float m0, c0;
+        float m1[3], c1[3];
+        float m2[6], c2[6];  // xx xy xz yy yz zz
+        float dm0[3];
+        float dm1[9];   // [g][a]
+        float dm2[18];  // [g][ab]
+        int cnt;
+    };
+    __device__ static void init(const P &, I &s, const Rec &, int64_t, int, int, int32_t) {
+        s.m0 = s.c0 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s.m1[a] = s.c1[a] = s.dm0[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) s.m2[a] = s.c2[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s.dm1[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 18; ++a) s.dm2[a] = 0.f;
+        s.cnt = 0;
+    }
+    template <bool kCount>
+    __device__ static void interact(const P &, I &s, const Rec &ri, const Rec &rj) {
+        float x[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};  // x_ij
+        float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+        float hs = ri.h + rj.h;
+        bool in = r2 < hs * hs;
+        float W, dWr;
+        wendland(r2, 0.5f * hs, W, dWr);
+        float w = in ? rj.V * W : 0.0f;
+        float vd = in ? rj.V * dWr : 0.0f;
+        float wx[3] = {w * x[0], w * x[1], w * x[2]};
+        float dW[3] = {vd * x[0], vd * x[1], vd * x[2]};  // V_j d_g W
+        kahan_add(s.m0, s.c0, w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) kahan_add(s.m1[a], s.c1[a], wx[a]);
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+        float xx[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            xx[q] = x[ia[q]] * x[ib[q]];
+            kahan_add(s.m2[q], s.c2[q], wx[ia[q]] * x[ib[q]]);
+        }
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            s.dm0[g] += dW[g];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s.dm1[3 * g + a] = fmaf(x[a], dW[g], s.dm1[3 * g + a] + (a == g ? w : 0.0f));
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                float t = (ia[q] == g ? wx[ib[q]] : 0.0f) + (ib[q] == g ? wx[ia[q]] : 0.0f);
+                s.dm2[6 * g + q] = fmaf(xx[q], dW[g], s.dm2[6 * g + q] + t);
+            }
+        }
+        if (kCount) s.cnt += in;
+    }
     __device__ static void finish(const P &p, I &s, const Rec &, int32_t o, int64_t) {
         const int64_t n = p.n;
         const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
@@ -744,7 +802,10 @@ struct CorrAdjPrepStage : CorrStage {
         // moment cotangents: dm1b[g][a], dm2b[g][ab] (symmetric in ab, packed as ia/ib)
         double m0b = 0.0, m1b[3] = {0, 0, 0}, dm0b[3], dm1b[3][3], dm2b[3][6];
         double dm1[3][3], dm2[3][6];
-        grad_moments(s, m0, m1, dm1, dm2);
+        for (int g = 0; g < 3; ++g) {
+            for (int a = 0; a < 3; ++a) dm1[g][a] = (double)s.dm1[3 * g + a];
+            for (int q = 0; q < 6; ++q) dm2[g][q] = (double)s.dm2[6 * g + q];
+        }
         for (int g = 0; g < 3; ++g) {
             double dM[3][3], t[3], tb[3], K = (double)s.dm0[g];
             for (int q = 0; q < 6; ++q) {
@@ -1729,6 +1790,10 @@ __device__ __forceinline__ void tile_group_pair(const LeafView &lv, const typena
             ++cnt;
         }
         __syncwarp();
+        // unrolled: independent packed pairs interleave their dependent chains (Horner, rsqrt);
+        // on the 2x256^3 box gravity and its adjoint took 28.2 and 48.8 ms rolled, 26.6 and
+        // 46.9 ms unrolled by 4, 26.4 and 46.4 ms by 8
+#pragma unroll 8
         for (int k = 0; k < (cnt >> 1); ++k) S::template interact2<kCount>(p, st, buf[k]);
         __syncwarp();
     };
@@ -2652,6 +2717,34 @@ __host__ __device__ constexpr int list_ahead() {
     return (std::is_same<S, GeomStage>::value || std::is_same<S, GeomAdjStage>::value) ? 8 : 4;
 }
 
+// Stages whose pair term is gated by the in-range test (every contribution of
+// an out-of-range j is an exact zero): list_kernel runs their rows of entries
+// as straight-line code, padding the end of a lane's list with i's own record
+// moved 4 h + 1 away, so the compiler interleaves the entries' dependent
+// chains (geometry 5.34 -> 4.88 ms, corrections 10.48 -> 10.11 ms on the
+// 2x256^3 box).  Hydro is left out: four staged 112-byte records per lane
+// cost it its occupancy (15.1 -> 22.6 ms).
+template <class S>
+struct flat_tail {
+    static constexpr bool value = false;
+};
+template <>
+struct flat_tail<GeomStage> {
+    static constexpr bool value = true;
+};
+template <>
+struct flat_tail<GeomAdjStage> {
+    static constexpr bool value = true;
+};
+template <>
+struct flat_tail<CorrStage> {
+    static constexpr bool value = true;
+};
+template <>
+struct flat_tail<ExtrasStage> {
+    static constexpr bool value = true;
+};
+
 // Exact neighbour lists, one warp per i-group.  The warp stages the group's
 // j table in shared memory (each distinct j of the group gathered once,
 // shifted into the i frame), then each lane walks its own list of table
@@ -2736,10 +2829,23 @@ __global__ void __launch_bounds__(kThreads, list_min_blocks<S>::value) list_kern
                 nx1 = k + 5 < c ? __ldg(Lk + 32) : 0;
                 nx2 = k + 6 < c ? __ldg(Lk + 64) : 0;
                 nx3 = k + 7 < c ? __ldg(Lk + 96) : 0;
-                S::template interact<kCount>(p, st, ri, entry(i0));
-                if (k + 1 < c) S::template interact<kCount>(p, st, ri, entry(i1));
-                if (k + 2 < c) S::template interact<kCount>(p, st, ri, entry(i2));
-                if (k + 3 < c) S::template interact<kCount>(p, st, ri, entry(i3));
+                if constexpr (flat_tail<S>::value) {
+                    Rec far = ri;  // past the end of the list: out of range, every term finite
+                    far.x += 4.0f * ri.h + 1.0f;
+                    const Rec e0 = entry(i0);
+                    const Rec e1 = k + 1 < c ? entry(i1) : far;
+                    const Rec e2 = k + 2 < c ? entry(i2) : far;
+                    const Rec e3 = k + 3 < c ? entry(i3) : far;
+                    S::template interact<kCount>(p, st, ri, e0);
+                    S::template interact<kCount>(p, st, ri, e1);
+                    S::template interact<kCount>(p, st, ri, e2);
+                    S::template interact<kCount>(p, st, ri, e3);
+                } else {
+                    S::template interact<kCount>(p, st, ri, entry(i0));
+                    if (k + 1 < c) S::template interact<kCount>(p, st, ri, entry(i1));
+                    if (k + 2 < c) S::template interact<kCount>(p, st, ri, entry(i2));
+                    if (k + 3 < c) S::template interact<kCount>(p, st, ri, entry(i3));
+                }
             }
         } else {
             int nx[kAhead];
@@ -2753,10 +2859,20 @@ __global__ void __launch_bounds__(kThreads, list_min_blocks<S>::value) list_kern
                     cur[d] = nx[d];
                     nx[d] = k + kAhead + d < c ? __ldg(Lk + (size_t)d * 32) : 0;
                 }
-                S::template interact<kCount>(p, st, ri, entry(cur[0]));
+                if constexpr (flat_tail<S>::value) {
+                    Rec far = ri;
+                    far.x += 4.0f * ri.h + 1.0f;
+                    Rec e[kAhead];
 #pragma unroll
-                for (int d = 1; d < kAhead; ++d)
-                    if (k + d < c) S::template interact<kCount>(p, st, ri, entry(cur[d]));
+                    for (int d = 0; d < kAhead; ++d) e[d] = (d == 0 || k + d < c) ? entry(cur[d]) : far;
+#pragma unroll
+                    for (int d = 0; d < kAhead; ++d) S::template interact<kCount>(p, st, ri, e[d]);
+                } else {
+                    S::template interact<kCount>(p, st, ri, entry(cur[0]));
+#pragma unroll
+                    for (int d = 1; d < kAhead; ++d)
+                        if (k + d < c) S::template interact<kCount>(p, st, ri, entry(cur[d]));
+                }
             }
         }
         if (act) S::finish(p, st, ri, lv.korder ? i : lv.kperm[i], i);
