@@ -41,8 +41,9 @@ STAGES = ["leaves", "geometry", "corrections", "hydro", "gravity", "gravity_adjo
 # DRAM bytes (read + write) per launch of a kernel in one launch shape (workload, kernel, variant,
 # depth, warps), from one ncu capture of the current build (dram__bytes_read.sum + dram__bytes_write.sum;
 # the summaries under profiles/ give the commands).  A shape not captured since its kernel last
-# changed has no entry, and the bench line then reports traffic null.
-TRAFFIC = {}
+# changed has no entry, and the bench line then reports traffic null.  The large box's entry is the
+# medium-box capture (307.1 MB) scaled by the in-range pairs per launch (8.784e9 / 1.328e9).
+TRAFFIC = {("large", "gravity_adjoint", 1, 96, 2): 2.032e9}
 
 
 def parse():
@@ -57,6 +58,8 @@ def parse():
     ap.add_argument("--trace-leaves", action="store_true", help="after timing, print leaf-build phase times")
     ap.add_argument("--variants", default="", help="kernel=variant,... (0 lists, 1 tiles, 2 tiles16, 3 tiles8, 4 ring16, 5-7 half-warp, "
                                                      "8 split8)")
+    ap.add_argument("--launch", default="", help="kernel=P:D:W,... launch shapes (persistent 0/1, j-tile depth, "
+                                                   "warps per block) instead of the autotuner's (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Extras-chain measurement")
     ap.add_argument("--no-advance", action="store_true", help="skip the timestep/integrator measurement")
@@ -288,6 +291,10 @@ def main():
     for kv in filter(None, args.variants.split(",")):
         k, v = kv.split("=")
         ctx.set_variant(k, int(v))
+    for kv in filter(None, args.launch.split(",")):
+        k, v = kv.split("=")
+        pm, d, w = (int(t) for t in v.split(":"))
+        ctx.set_launch(k, pm, d, w)
     variants = {k: ctx.get_variant(k) for k in native.KERNELS}
     db = api.DeviceBox(box, device=f"cuda:{local}")
     gas = (db.species == 0).float()
@@ -330,7 +337,7 @@ def main():
         return lv
 
     tuning = None
-    if not args.no_tune and not args.variants:
+    if not args.no_tune and not args.variants and not args.launch:
         # untimed: the autotuner picks each kernel's variant on this workload's leaves
         lv_t = api.build_leaves(ctx, db.x, db.y, db.z, db.species, db.h, db.L, db.lp)
         io_t = api.StepIO(ctx, db, extras=True)
@@ -816,8 +823,8 @@ def _batched_vs_plain(args, local, peak_tflops, boxes, t_gen, side):
                                 "over all boxes, tuned launch shapes", "leaves_status": status},
             "batched_persistent": {"ms_per_step": res["batched_graph_persistent"],
                                    "value": p_batch / (res["batched_graph_persistent"] * 1e-3),
-                                   "form": "the same graph with every pair kernel persistent (4 blocks per SM, "
-                                           "atomic work queue)"},
+                                   "form": "the same graph with every pair kernel persistent (resident blocks on every "
+                                           "SM, atomic work queue)"},
             "batched_eager": {"ms_per_step": res["batched_eager"],
                               "value": p_batch / (res["batched_eager"] * 1e-3),
                               "form": "one multi-box leaf build (host reads back sizes) + one crk_step, eager"},

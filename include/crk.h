@@ -140,9 +140,10 @@ int crk_set_trace(crk_ctx *ctx, int on);
 #define CRK_N_VARIANTS 9
 int crk_set_variant(crk_ctx *ctx, int kernel, int variant);
 /* Launch mode of every pair kernel: 0 (default) one block per i-leaf (one warp
- * per group for the list kernels); 1 persistent: a grid of 4 blocks per SM
- * whose blocks (warps) take i-leaves (groups) from an atomic work queue (no
- * block ever waits on another).  Same results. */
+ * per group for the list kernels); 1 persistent: a grid of resident blocks on
+ * every SM (list kernels: as many as the kernel's registers and shared memory
+ * allow; tiles kernels: 4) whose blocks (warps) take i-leaves (groups) from an
+ * atomic work queue (no block ever waits on another).  Same results. */
 int crk_set_persistent(crk_ctx *ctx, int on);
 /* Launch shape of one pair kernel (CRK_K_*), as the autotuner sets it:
  * persistent as above; the j-tile depth of the packed tiles sweeps of the

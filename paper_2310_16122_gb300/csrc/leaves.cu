@@ -773,7 +773,8 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
                                  int32_t *__restrict__ perm, int32_t *__restrict__ kperm,
                                  int32_t *__restrict__ leaf_ngas, float *__restrict__ bbox,
                                  float *__restrict__ hmax, float4 *__restrict__ pos, int32_t *__restrict__ kperm_g,
-                                 float4 *__restrict__ pos_g, int32_t *__restrict__ err, int cells8) {
+                                 float4 *__restrict__ pos_g, int32_t *__restrict__ kinv, int32_t *__restrict__ kinv_g,
+                                 int32_t *__restrict__ err, int cells8) {
     __shared__ uint64_t key[kCap], zkey[kCap];
     __shared__ Bisect32<kCap> bs;
     __shared__ float4 pm[kCap];  // member position and h (0 for dark matter), gathered once
@@ -869,7 +870,9 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int t = gsrc[q];
         const float4 c = pm[t];
-        kperm[lo + q] = (int32_t)(uint32_t)key[t];
+        const int32_t id = (int32_t)(uint32_t)key[t];
+        kperm[lo + q] = id;
+        kinv[id] = lo + q;  // the inverse permutations, written here rather than by a pass of their own
         pos[lo + q] = make_float4(c.x - ox, c.y - oy, c.z - oz, c.w);
     }
     __syncthreads();
@@ -883,7 +886,9 @@ __global__ void leaf_data_kernel(int64_t n_leaves, const int32_t *__restrict__ l
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int t = src[q];
         const float4 c = pm[t];
-        kperm_g[lo + q] = (int32_t)(uint32_t)key[t];
+        const int32_t id = (int32_t)(uint32_t)key[t];
+        kperm_g[lo + q] = id;
+        kinv_g[id] = lo + q;
         pos_g[lo + q] = make_float4(c.x - ox, c.y - oy, c.z - oz, c.w);
     }
 }
@@ -1401,14 +1406,6 @@ struct Tracer {
 };
 }  // namespace
 
-__global__ void inverse_perm_kernel(int64_t n, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
-                                    int32_t *__restrict__ ainv, int32_t *__restrict__ binv) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    ainv[a[q]] = (int32_t)q;
-    binv[b[q]] = (int32_t)q;
-}
-
 __global__ void init_node_of_kernel(int64_t n, const int32_t *__restrict__ box_of, const int32_t *__restrict__ seg_of_box,
                                     int32_t *__restrict__ node_of) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1742,15 +1739,12 @@ static int build_leaves_impl(crk_ctx *ctx, const crk_particles *p, const float *
                 leaf_data_kernel<128><<<(unsigned)nl, 32, 0, st>>>(nl, lv->leaf_start, members, p->x, p->y, p->z,
                                                                    p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
                                                                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g,
-                                                                   lv->pos_g, flags + 4, lv->cells8 ? 1 : 0);
+                                                                   lv->pos_g, lv->kinv, lv->kinv_g, flags + 4,
+                                                                   lv->cells8 ? 1 : 0);
             else
                 leaf_data_kernel<kMaxLeafCap><<<(unsigned)nl, 128, 0, st>>>(
                     nl, lv->leaf_start, members, p->x, p->y, p->z, p->species, h, lv->perm, lv->kperm, lv->leaf_ngas,
-                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g, flags + 4, 0);
-            ++ctx->launches;
-        }
-        if (n > 0) {
-            inverse_perm_kernel<<<crk_grid(n, 256), 256, 0, st>>>(n, lv->kperm, lv->kperm_g, lv->kinv, lv->kinv_g);
+                    lv->bbox, lv->hmax, lv->pos, lv->kperm_g, lv->pos_g, lv->kinv, lv->kinv_g, flags + 4, 0);
             ++ctx->launches;
         }
         KCHECK("leaf data");
