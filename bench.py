@@ -41,9 +41,9 @@ STAGES = ["leaves", "geometry", "corrections", "hydro", "gravity", "gravity_adjo
 # DRAM bytes (read + write) per launch of a kernel in one launch shape (workload, kernel, variant,
 # depth, warps), from one ncu capture of the current build (dram__bytes_read.sum + dram__bytes_write.sum;
 # the summaries under profiles/ give the commands).  A shape not captured since its kernel last
-# changed has no entry, and the bench line then reports traffic null.  The large box's entry is the
-# medium-box capture (307.1 MB) scaled by the in-range pairs per launch (8.784e9 / 1.328e9).
-TRAFFIC = {("large", "gravity_adjoint", 1, 96, 2): 2.032e9}
+# changed has no entry, and the bench line then reports traffic null.  The large box's entries are the
+# medium-box captures (307.1 MB in both shapes) scaled by the in-range pairs per launch (8.784e9 / 1.328e9).
+TRAFFIC = {("large", "gravity_adjoint", 1, 96, 2): 2.032e9, ("large", "gravity_adjoint", 1, 96, 4): 2.032e9}
 
 
 def parse():

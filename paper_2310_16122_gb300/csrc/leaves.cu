@@ -324,10 +324,13 @@ __global__ void rcb_scan3_kernel(int32_t *__restrict__ bsum, int64_t nb) {
 // thread t is position base + k kPartThreads + t), so the left-going (and the
 // right-going) entries of one warp row land in consecutive output positions:
 // coalesced stores.  The tile-local prefix of an entry is the count over
-// earlier (row, warp) pairs plus the ballot rank inside its warp.
+// earlier (row, warp) pairs plus the ballot rank inside its warp.  The kernel
+// waits on its loads (segment record, rank columns): compiled for six
+// resident blocks per SM (40 registers) it ran the 14 streamed levels of the
+// 33.5M-particle build 2.0 ms faster than at four.
 constexpr int kPartWarps = kPartThreads / 32;
 
-__global__ void __launch_bounds__(kPartThreads, 4) rcb_scatter3_kernel(int64_t n, const SegRec *__restrict__ segs,
+__global__ void __launch_bounds__(kPartThreads, 6) rcb_scatter3_kernel(int64_t n, const SegRec *__restrict__ segs,
                                                                       const int32_t *__restrict__ node_of, RankLists L,
                                                                       const int32_t *__restrict__ bsum, int64_t nb,
                                                                       RankListsOut O, int32_t *__restrict__ node_of_next,
