@@ -1080,11 +1080,15 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
     int64_t n_leaves, const int32_t *__restrict__ leaf_start, const int32_t *__restrict__ leaf_ngas,
     const float *__restrict__ bbox, const float *__restrict__ hmax, TreeDev tree, double L0, double rc, PairOut o,
     const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ box_root, const float *__restrict__ box_L) {
-    __shared__ int32_t stack[kTravWarps][kStackCap];
-    __shared__ int32_t cand[kTravWarps][kCandCap];
-    __shared__ int32_t sorted[kTravWarps][kCandCap];
-    __shared__ uint8_t ng[kTravWarps][kCandCap], nh[kTravWarps][kCandCap];
+    // two per-warp buffers, each reused by a later phase (32 KB a block, five blocks per SM):
+    // the traversal stack, then the sorted candidates; the candidates, then the image counts
+    static_assert(kStackCap <= kCandCap, "stack inside the sorted-candidate buffer");
+    __shared__ int32_t buf_a[kTravWarps][kCandCap];
+    __shared__ int32_t buf_b[kTravWarps][kCandCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *const stack = buf_a[warp], *const sorted = buf_a[warp];
+    int32_t *const cand = buf_b[warp];
+    uint8_t *const ng = reinterpret_cast<uint8_t *>(buf_b[warp]), *const nh = ng + kCandCap;
     const unsigned below = (1u << lane) - 1u;
     const int64_t a = (int64_t)blockIdx.x * kTravWarps + warp;
     if (a >= n_leaves) return;  // whole warp leaves together; no block barrier below
@@ -1109,16 +1113,16 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
                 }
                 unsigned m = __ballot_sync(CRK_FULL_MASK, keep);
                 int pos = nc + __popc(m & below);
-                if (keep && pos < kCandCap) cand[warp][pos] = (int32_t)b;
+                if (keep && pos < kCandCap) cand[pos] = (int32_t)b;
                 nc += __popc(m);
             }
         } else {
             int top = 1;
-            if (lane == 0) stack[warp][0] = root;
+            if (lane == 0) stack[0] = root;
             __syncwarp();
             while (top > 0) {
                 const int take = top < 32 ? top : 32;
-                const int32_t nd = lane < take ? stack[warp][top - 1 - lane] : -1;
+                const int32_t nd = lane < take ? stack[top - 1 - lane] : -1;
                 top -= take;
                 __syncwarp();
                 bool pass = false;
@@ -1131,13 +1135,13 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
                 const bool is_leaf = pass && lf >= 0, inner = pass && lf < 0;
                 unsigned m = __ballot_sync(CRK_FULL_MASK, is_leaf);
                 int pos = nc + __popc(m & below);
-                if (is_leaf && pos < kCandCap) cand[warp][pos] = lf;
+                if (is_leaf && pos < kCandCap) cand[pos] = lf;
                 nc += __popc(m);
                 unsigned m2 = __ballot_sync(CRK_FULL_MASK, inner);
                 int sp = top + 2 * __popc(m2 & below);
                 if (inner && sp + 1 < kStackCap) {
-                    stack[warp][sp] = tree.node_right[nd];
-                    stack[warp][sp + 1] = tree.node_left[nd];
+                    stack[sp] = tree.node_right[nd];
+                    stack[sp + 1] = tree.node_left[nd];
                 }
                 top += 2 * __popc(m2);
                 if (top > kStackCap || nc > kCandCap) {
@@ -1156,16 +1160,16 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
     }
     // ascending j-leaf order (rank sort; leaf ids are unique)
     for (int t = lane; t < nc; t += 32) {
-        int32_t v = cand[warp][t];
+        int32_t v = cand[t];
         int r = 0;
-        for (int u = 0; u < nc; ++u) r += cand[warp][u] < v;
-        sorted[warp][r] = v;
+        for (int u = 0; u < nc; ++u) r += cand[u] < v;
+        sorted[r] = v;
     }
     __syncwarp();
     // exact image counts of both lists
     const double rc2 = __dmul_rn(rc, rc);
     for (int t = lane; t < nc; t += 32) {
-        int32_t b = sorted[warp][t];
+        int32_t b = sorted[t];
         int cg = leaf_images<false>(bbox, a, b, L, rc2, nullptr);
         int ch = 0;
         if (a_gas && leaf_ngas[b] > 0) {
@@ -1173,14 +1177,14 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
             double cut = __dmul_rn(2.0, hA > hb ? hA : hb);
             ch = leaf_images<false>(bbox, a, b, L, __dmul_rn(cut, cut), nullptr);
         }
-        ng[warp][t] = (uint8_t)cg;
-        nh[warp][t] = (uint8_t)ch;
+        ng[t] = (uint8_t)cg;
+        nh[t] = (uint8_t)ch;
     }
     __syncwarp();
     int tot[4] = {0, 0, 0, 0};
     for (int t0 = 0; t0 < nc; t0 += 32) {
         int t = t0 + lane;
-        int cg = t < nc ? ng[warp][t] : 0, ch = t < nc ? nh[warp][t] : 0;
+        int cg = t < nc ? ng[t] : 0, ch = t < nc ? nh[t] : 0;
         int v[4] = {cg, cg > 0, ch, ch > 0};
         for (int k = 0; k < 4; ++k) {
             int s;
@@ -1208,7 +1212,7 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
     int run[4] = {0, 0, 0, 0};
     for (int t0 = 0; t0 < nc; t0 += 32) {
         int t = t0 + lane;
-        int cg = t < nc ? ng[warp][t] : 0, ch = t < nc ? nh[warp][t] : 0;
+        int cg = t < nc ? ng[t] : 0, ch = t < nc ? nh[t] : 0;
         int v[4] = {cg, cg > 0, ch, ch > 0};
         int off[4];
         for (int k = 0; k < 4; ++k) {
@@ -1217,7 +1221,7 @@ __global__ void __launch_bounds__(kTravWarps * 32) leaf_pairs_warp_kernel(
             run[k] += s;
         }
         if (t < nc) {
-            int32_t b = sorted[warp][t];
+            int32_t b = sorted[t];
             if (cg > 0) {
                 o.gpair[base[1] + off[1]] = b;
                 leaf_images<true>(bbox, a, b, L, rc2, o.gimg + base[0] + off[0]);
